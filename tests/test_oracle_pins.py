@@ -1,0 +1,429 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: lattice
+isotropy (textbook), exact Taylor identities of the stencils on polynomials
+(Eqs. 8, 10, 11, 29), the moment constraints of Appendix A (Eqs. 33-35, 37)
+built from the pressure tensor of Eq. 1, conservation laws, symmetry, the 2D
+fold stated in Sec. VII, Maxwell residuals and the printed coexistence
+densities (Sec. IV).  Longer runs (Laplace law, spurious velocity) are in
+test_oracle_physics.py.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import sympy as sp
+
+from oracle import lb_oracle as O
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+A_VDW, B_VDW = 9.0 / 49.0, 2.0 / 21.0
+
+
+# ----------------------------------------------------------------- lattices
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+def test_velocity_set_isotropy(lat):
+    """w_i are 3x the textbook lattice weights: sum w e_a e_b = delta_ab,
+    sum w e_a e_b e_c e_d = (d_ab d_cd + d_ac d_bd + d_ad d_bc)/3, odd moments 0."""
+    e = O.velocities(lat).astype(float)
+    d = O.dim_of(lat)
+    w = (O.weights_d2q9() if d == 2 else O.weights_d3q19()).w
+    assert len({tuple(v) for v in e}) == len(e)
+    assert np.allclose(np.einsum("i,ia->a", w, e), 0)
+    I = np.eye(3)
+    I[d:, d:] = 0
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, e, e), I, atol=1e-15)
+    four = np.einsum("i,ia,ib,ic,id->abcd", w, e, e, e, e)
+    iso = (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+           + np.einsum("ad,bc->abcd", I, I)) / 3.0
+    assert np.allclose(four, iso, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, e, e, e), 0)
+
+
+def test_d2q9_optimal_weights_match_summary():
+    """Sec. VIII list: w^p = w^t = (1/3, 1/12), w^xx_{5-8} = -1/24,
+    w^xx_{1-2} = 1/3, w^xx_{3-4} = -1/6, w^xy_{1-4} = 0, |w^xy_{5-8}| = 1/4."""
+    w = O.weights_d2q9()
+    assert np.allclose(w.wp[1:], [1 / 3] * 4 + [1 / 12] * 4)
+    assert np.allclose(w.wt[1:], [1 / 3] * 4 + [1 / 12] * 4)
+    assert np.allclose(w.wm[(0, 0)][1:], [1 / 3, 1 / 3, -1 / 6, -1 / 6] + [-1 / 24] * 4)
+    assert np.allclose(w.wm[(1, 1)][1:], [-1 / 6, -1 / 6, 1 / 3, 1 / 3] + [-1 / 24] * 4)
+    assert np.allclose(np.abs(w.wm[(0, 1)][5:]), 0.25)
+    assert np.allclose(w.wm[(0, 1)][1:5], 0)
+
+
+def test_d3q19_table_entries():
+    """Eq. 31 entries that are used as printed (R4/R5 change only the 1/3s)."""
+    w = O.weights_d3q19()
+    assert np.allclose(w.w[7:], 1 / 12)
+    assert np.allclose(w.wm[(0, 0)][[7, 8, 9, 10, 15, 16, 17, 18]], -1 / 24)
+    assert np.allclose(w.wm[(0, 0)][11:15], 1 / 12)
+    assert np.allclose(w.wm[(1, 1)][15:19], 1 / 12)
+    assert np.allclose(w.wm[(2, 2)][7:11], 1 / 12)
+    assert np.allclose(w.wm[(0, 0)][3:7], -1 / 3)
+    lit = O.weights_d3q19(paper_literal=True)
+    assert np.allclose(lit.w[1:7], 1 / 3) and np.allclose(lit.wm[(0, 0)][1:3], 1 / 3)
+
+
+# ----------------------------------------------------------------- stencils
+
+X, Y, Z = sp.symbols("x y z")
+
+
+def _rand_poly(rng, deg, dim):
+    """Random integer polynomial of total degree <= deg."""
+    vars_ = [X, Y, Z][:dim]
+    p = 0
+    for px in range(deg + 1):
+        for py in range(deg + 1 - px):
+            for pz in range(deg + 1 - px - py if dim == 3 else 1):
+                p += int(rng.integers(-3, 4)) * X ** px * Y ** py * Z ** pz
+    return sp.expand(p), vars_
+
+
+def _eval_grid(expr, n, dim):
+    f = sp.lambdify((X, Y, Z), expr, "numpy")
+    nz = n if dim == 3 else 1
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(n), np.arange(n), indexing="ij")
+    out = f(x.astype(float), y.astype(float), z.astype(float))
+    return np.broadcast_to(np.asarray(out, dtype=float), (nz, n, n)).copy()
+
+
+def _interior(a, dim, m=2):
+    return a[m:-m, m:-m, m:-m] if dim == 3 else a[:, m:-m, m:-m]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("B", [1 / 12, 0.0, 0.05])
+def test_gradient_taylor_identity(dim, B):
+    """Eq. 10 (and Eq. 29): d_x = d_x + d_x^3/6 + 2B d_x (d_y^2 [+ d_z^2]),
+    exact on polynomials of degree <= 4 (fifth derivatives vanish)."""
+    rng = np.random.default_rng(7)
+    st = O.Stencils(dim=dim, B=B)
+    n = 9
+    for trial in range(2):
+        p, _ = _rand_poly(rng, 4, dim)
+        rho = _eval_grid(p, n, dim)
+        got = O.gradient(rho, st)
+        axes = [X, Y, Z][:dim]
+        for a_, va in enumerate(axes):
+            others = [v for v in axes if v != va]
+            expect = sp.diff(p, va) + sp.diff(p, va, 3) / 6 + 2 * sp.Rational(B).limit_denominator(10 ** 6) * sum(
+                sp.diff(p, va, ob, 2) for ob in others)
+            ref = _eval_grid(expect, n, dim)
+            assert np.allclose(_interior(got[a_], dim), _interior(ref, dim), rtol=1e-11, atol=1e-8)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("D", [1 / 6, 0.0, 0.3])
+def test_laplacian_taylor_identity(dim, D):
+    """Eq. 11: lap = lap + (d_x^4 + d_y^4)/12 + D d_x^2 d_y^2 (2D);
+    Eq. 29: lap + sum d^4/12 + D sum_{pairs} d_a^2 d_b^2 (3D, C + 4D = 1).
+    Exact on polynomials of degree <= 5."""
+    rng = np.random.default_rng(11)
+    st = O.Stencils(dim=dim, D=D)
+    n = 9
+    axes = [X, Y, Z][:dim]
+    Dq = sp.Rational(D).limit_denominator(10 ** 6)
+    for trial in range(2):
+        p, _ = _rand_poly(rng, 5, dim)
+        rho = _eval_grid(p, n, dim)
+        got = O.laplacian(rho, st)
+        expect = sum(sp.diff(p, v, 2) for v in axes) + sum(sp.diff(p, v, 4) for v in axes) / 12
+        for i in range(dim):
+            for k in range(i + 1, dim):
+                expect += Dq * sp.diff(p, axes[i], 2, axes[k], 2)
+        ref = _eval_grid(expect, n, dim)
+        assert np.allclose(_interior(got, dim), _interior(ref, dim), rtol=1e-11, atol=1e-8)
+
+
+def test_optimal_2d_stencils_are_eq32():
+    """Eq. 32: d_x = (1/12)[-1 0 1; -4 0 4; -1 0 1], lap = (1/6)[1 4 1; 4 -20 4; 1 4 1]."""
+    st = O.Stencils(dim=2)
+    gx = st.grad_offsets()[0]
+    want = {(-1, 1, 0): -1, (1, 1, 0): 1, (-1, 0, 0): -4, (1, 0, 0): 4, (-1, -1, 0): -1, (1, -1, 0): 1}
+    assert set(gx) == set(want)
+    for k, v in want.items():
+        assert abs(gx[k] - v / 12) < 1e-15
+    lap = st.laplacian_offsets()
+    expect = {(-1, 1, 0): 1, (0, 1, 0): 4, (1, 1, 0): 1, (-1, 0, 0): 4, (0, 0, 0): -20, (1, 0, 0): 4,
+              (-1, -1, 0): 1, (0, -1, 0): 4, (1, -1, 0): 1}
+    assert set(lap) == set(expect)
+    for k, v in expect.items():
+        assert abs(lap[k] - v / 6) < 1e-15
+
+
+def test_simple_stencil_is_central_difference():
+    """B = 0 gives Eq. 7: [rho(r+e1) - rho(r+e2)]/2 (the stencil of Eq. 9)."""
+    st = O.Stencils(dim=2, B=0.0)
+    assert st.grad_offsets()[0] == {(-1, 0, 0): -0.5, (1, 0, 0): 0.5}
+
+
+# ------------------------------------------------------- moments (App. A)
+
+def _random_state(lat, rng, shape=(3, 4, 5)):
+    d = O.dim_of(lat)
+    if d == 2:
+        shape = (1,) + shape[1:]
+    rho = rng.uniform(2.0, 5.0, shape)
+    u = [rng.uniform(-0.05, 0.05, shape) for _ in range(d)]
+    grad = [rng.uniform(-0.5, 0.5, shape) for _ in range(d)]
+    lap = rng.uniform(-0.5, 0.5, shape)
+    return rho, u, grad, lap
+
+
+def _pressure_tensor(rho, grad, lap, m, with_m=True):
+    """Eq. 1 with discrete derivatives: (p0 - k rho lap - k/2 |grad|^2) d_ab + k d_a d_b."""
+    d = m.dim
+    pr = O.p0(rho, m.a, m.b, m.T) - m.kappa * rho * lap
+    if with_m:
+        pr = pr - 0.5 * m.kappa * sum(g * g for g in grad)
+    P = {}
+    for a_ in range(d):
+        for b_ in range(d):
+            P[(a_, b_)] = (pr if a_ == b_ else 0.0) + (m.kappa * grad[a_] * grad[b_] if with_m else 0.0)
+    return P
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_equilibrium_moments(lat, scheme):
+    """Eqs. 33-35: sum f^eq = rho; sum f^eq e = rho u;
+    sum f^eq e e = P + rho u u + lambda(u d rho + d rho u + delta u.d rho);
+    sum f^eq e e e = rho c^2/3 (delta u + ...).  In the forcing scheme the M
+    part of P is moved into g (Sec. VI)."""
+    rng = np.random.default_rng(3)
+    m = O.Model(lat, A_VDW, B_VDW, 0.55, 0.01, 0.8, scheme=scheme)
+    rho, u, grad, lap = _random_state(lat, rng)
+    feq = O.equilibrium(rho, u, grad, lap, m, include_m_terms=(scheme == "equilibrium"))
+    e = m.e.astype(float)
+    d = m.dim
+    assert np.allclose(feq.sum(0), rho, rtol=1e-14)
+    for a_ in range(d):
+        assert np.allclose(np.einsum("i,i...->...", e[:, a_], feq), rho * u[a_], rtol=1e-12, atol=1e-14)
+    P = _pressure_tensor(rho, grad, lap, m, with_m=(scheme == "equilibrium"))
+    lam = (m.tau - 0.5) / 3 * (1 - 3 * O.cs2(rho, m.a, m.b, m.T))
+    udg = sum(u[k] * grad[k] for k in range(d))
+    for a_ in range(d):
+        for b_ in range(d):
+            got = np.einsum("i,i,i...->...", e[:, a_], e[:, b_], feq)
+            want = P[(a_, b_)] + rho * u[a_] * u[b_] + lam * (
+                u[a_] * grad[b_] + u[b_] * grad[a_] + (a_ == b_) * udg)
+            assert np.allclose(got, want, rtol=1e-12, atol=1e-13), (a_, b_)
+    for a_ in range(d):
+        for b_ in range(d):
+            for c_ in range(d):
+                got = np.einsum("i,i,i,i...->...", e[:, a_], e[:, b_], e[:, c_], feq)
+                want = rho / 3 * ((a_ == b_) * u[c_] + (a_ == c_) * u[b_] + (b_ == c_) * u[a_])
+                assert np.allclose(got, want, rtol=1e-12, atol=1e-13)
+
+
+def test_paper_literal_3d_table_fails_second_moment():
+    """With the printed 1/3 entries of Eq. 31 (R4, R5 not applied) the second
+    moment of Eq. 34 is not met: the readings are needed."""
+    rng = np.random.default_rng(5)
+    m = O.Model("D3Q19", A_VDW, B_VDW, 0.55, 0.01, 1.0, weights=O.weights_d3q19(paper_literal=True))
+    rho, u, grad, lap = _random_state("D3Q19", rng)
+    u = [0 * x for x in u]
+    feq = O.equilibrium(rho, u, grad, lap, m)
+    e = m.e.astype(float)
+    P = _pressure_tensor(rho, grad, lap, m)
+    got = np.einsum("i,i,i...->...", e[:, 0], e[:, 0], feq)
+    assert not np.allclose(got, P[(0, 0)], rtol=1e-6)
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+def test_force_population_moments(lat):
+    """Eq. 37: sum F = 0, sum F e = g, sum F e e = u g + g u."""
+    rng = np.random.default_rng(9)
+    m = O.Model(lat, A_VDW, B_VDW, 0.55, 0.01, 1.0, scheme="forcing")
+    d = m.dim
+    shape = (1, 4, 5) if d == 2 else (3, 4, 5)
+    u = [rng.uniform(-0.1, 0.1, shape) for _ in range(d)]
+    g = [rng.uniform(-0.1, 0.1, shape) for _ in range(d)]
+    F = O.force_populations(u, g, m)
+    e = m.e.astype(float)
+    assert np.allclose(F.sum(0), 0, atol=1e-16)
+    for a_ in range(d):
+        assert np.allclose(np.einsum("i,i...->...", e[:, a_], F), g[a_], rtol=1e-13, atol=1e-16)
+        for b_ in range(d):
+            got = np.einsum("i,i,i...->...", e[:, a_], e[:, b_], F)
+            assert np.allclose(got, u[a_] * g[b_] + u[b_] * g[a_], rtol=1e-12, atol=1e-16)
+
+
+def test_force_2d_matches_eq28_stencil_form():
+    """Eq. 28 written as the printed (E, F) stencils on (M_xx - M_yy)/2 and M_xy,
+    with E = 1/3, F = 1/12, evaluated directly with the matrices as printed."""
+    rng = np.random.default_rng(2)
+    m = O.Model("D2Q9", A_VDW, B_VDW, 0.55, 0.02, 1.0, scheme="forcing")
+    rho = rng.uniform(2, 5, (1, 6, 7))
+    g = O.body_force(rho, m)
+    gx_, gy_ = O.gradient(rho, m.stencils)
+    Mxx, Myy, Mxy = m.kappa * gx_ * gx_, m.kappa * gy_ * gy_, m.kappa * gx_ * gy_
+    E, F = 1 / 3, 1 / 12
+    s = lambda a, dx, dy: O.shift(a, (dx, dy, 0))
+    h = 0.5 * (Mxx - Myy)
+    first = (-F * s(h, -1, 1) + F * s(h, 1, 1) - E * s(h, -1, 0) + E * s(h, 1, 0)
+             - F * s(h, -1, -1) + F * s(h, 1, -1))
+    second = (F * s(Mxy, -1, 1) + E * s(Mxy, 0, 1) + F * s(Mxy, 1, 1)
+              - F * s(Mxy, -1, -1) - E * s(Mxy, 0, -1) - F * s(Mxy, 1, -1))
+    assert np.allclose(g[0], -first - second, rtol=1e-13, atol=1e-15)
+
+
+# ---------------------------------------------------------- dynamics pins
+
+def _drop_model(lat, scheme, T=0.55, kappa=0.01, tau=0.8):
+    return O.Model(lat, A_VDW, B_VDW, T, kappa, tau, scheme=scheme)
+
+
+def _drop_state(m, n, R, nz=None, perturb=0.0, seed=0):
+    rl, rg = O.coexistence(m.a, m.b, m.T)
+    nz = (n if m.dim == 3 else 1) if nz is None else nz
+    c = (n / 2, n / 2) if m.dim == 2 else (n / 2, n / 2, nz / 2)
+    rho0 = O.drop_density((nz, n, n), [c], [R], rl, rg)
+    f = O.init_equilibrium(rho0, m)
+    if perturb:
+        rng = np.random.default_rng(seed)
+        f = f * (1 + perturb * rng.standard_normal(f.shape))
+    return f
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_mass_and_momentum_conserved(lat, scheme):
+    """Collision conserves rho and rho u locally (Eq. 33, Eq. 37 sum F = 0) and
+    streaming permutes; with forcing, sum_r g = 0 because g is a discrete
+    divergence on the periodic lattice.  Random perturbation gives u != 0."""
+    m = _drop_model(lat, scheme)
+    n = 16 if lat == "D2Q9" else 10
+    f = _drop_state(m, n, 4.0, perturb=1e-3, seed=1)
+    rho0, j0, _ = O.moments(f, m)
+    mass0, mom0 = rho0.sum(), [x.sum() for x in j0]
+    f = O.run(f, m, 60)
+    rho1, j1, _ = O.moments(f, m)
+    assert abs(rho1.sum() - mass0) / mass0 < 1e-13
+    for a_ in range(m.dim):
+        assert abs(j1[a_].sum() - mom0[a_]) / mass0 < 1e-13
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+def test_uniform_rest_state_is_fixed_point(lat):
+    """Uniform density at rest: gradients vanish and f^eq = f, so f is unchanged."""
+    m = _drop_model(lat, "equilibrium")
+    shape = (1, 6, 6) if lat == "D2Q9" else (4, 5, 6)
+    rho0 = np.full(shape, 4.2)
+    f = O.init_equilibrium(rho0, m)
+    f1 = O.run(f, m, 5)
+    assert np.allclose(f1, f, rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_d2q9_drop_keeps_square_symmetry(scheme):
+    """A centred drop keeps the D4 symmetry of the square lattice: rho is
+    invariant under x -> n - x and x <-> y; u_x is odd under x -> n - x."""
+    m = _drop_model("D2Q9", scheme)
+    n = 24
+    f = _drop_state(m, n, 7.0)
+    f = O.run(f, m, 40)
+    rho, u, _ = O.observables(f, m)
+    r = rho[0]
+    refl = np.roll(r[:, ::-1], 1, axis=1)       # x -> n - x
+    assert np.allclose(r, refl, rtol=1e-13, atol=1e-13)
+    assert np.allclose(r, r.T, rtol=1e-13, atol=1e-13)
+    ux = u[0][0]
+    assert np.allclose(ux, -np.roll(ux[:, ::-1], 1, axis=1), rtol=0, atol=1e-12 * np.abs(ux).max())
+    assert np.abs(ux).max() > 1e-9            # the test is not vacuous
+
+
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_d3q19_drop_keeps_cubic_symmetry(scheme):
+    """A centred sphere keeps the cubic symmetry: rho is invariant under axis
+    permutations and reflections."""
+    m = _drop_model("D3Q19", scheme)
+    n = 12
+    f = _drop_state(m, n, 3.5)
+    f = O.run(f, m, 12)
+    rho, u, _ = O.observables(f, m)
+    assert np.allclose(rho, np.transpose(rho, (0, 2, 1)), rtol=1e-13, atol=1e-13)
+    assert np.allclose(rho, np.transpose(rho, (2, 1, 0)), rtol=1e-13, atol=1e-13)
+    assert np.allclose(rho, np.roll(rho[:, :, ::-1], 1, axis=2), rtol=1e-13, atol=1e-13)
+    assert np.abs(u[0]).max() > 1e-9
+
+
+def _fold(f3):
+    """Sum D3Q19 populations over e_z, mapping (e_x, e_y) onto the D2Q9 index."""
+    e2 = O.velocities("D2Q9")
+    e3 = O.velocities("D3Q19")
+    out = np.zeros((9,) + f3.shape[1:])
+    for i, v in enumerate(e3):
+        k = [j for j, w in enumerate(e2) if w[0] == v[0] and w[1] == v[1]][0]
+        out[k] += f3[i]
+    return out
+
+
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_d3q19_one_wide_reduces_to_d2q9(scheme):
+    """Sec. VII: for a system one lattice unit wide the 3D equilibrium reduces
+    to the 2D one.  Checked at rest (the pressure-tensor weights, incl. R4 and
+    R5) and after one step from rest.  Beyond that the Galilean term's
+    delta_ab u.grad(rho) has a dimension-dependent trace, so the runs separate
+    at O(lambda u.grad rho)."""
+    m2 = _drop_model("D2Q9", scheme)
+    m3 = _drop_model("D3Q19", scheme)
+    rl, rg = O.coexistence(m2.a, m2.b, m2.T)
+    rho0 = O.drop_density((1, 14, 16), [(8, 7)], [4.5], rl, rg)
+    f2 = O.init_equilibrium(rho0, m2)
+    f3 = O.init_equilibrium(rho0, m3)
+    assert np.allclose(_fold(f3), f2, rtol=1e-14, atol=1e-14)
+    f2 = O.step(f2, m2)
+    f3 = O.step(f3, m3)
+    assert np.allclose(_fold(f3), f2, rtol=1e-13, atol=1e-14)
+
+
+# --------------------------------------------------------------- Maxwell
+
+def test_coexistence_matches_paper_values():
+    """Sec. IV: T = 0.56 gives rho_l = 4.54, rho_g = 2.57 (printed to 3
+    figures; read as measured bulk values, so within 1%)."""
+    g = GOLDEN["coexistence_T056"]
+    rl, rg = O.coexistence(g["a"], g["b"], g["T"])
+    assert abs(rl - g["rho_l"]) / g["rho_l"] < 0.01
+    assert abs(rg - g["rho_g"]) / g["rho_g"] < 0.015
+
+
+@pytest.mark.parametrize("T", [0.50, 0.53, 0.55, 0.56, 0.57])
+def test_coexistence_residuals(T):
+    """Equal bulk pressure (Eq. 2) and equal chemical potential at coexistence."""
+    rl, rg = O.coexistence(A_VDW, B_VDW, T)
+    assert rl > 1 / (3 * B_VDW) > rg
+    assert abs(O.p0(rl, A_VDW, B_VDW, T) - O.p0(rg, A_VDW, B_VDW, T)) < 1e-12
+    assert abs(O.mu0(rl, A_VDW, B_VDW, T) - O.mu0(rg, A_VDW, B_VDW, T)) < 1e-11
+    assert O.cs2(rl, A_VDW, B_VDW, T) > 0 and O.cs2(rg, A_VDW, B_VDW, T) > 0
+
+
+def test_critical_point_closed_form():
+    """Eq. 2: dp0/drho = d2p0/drho2 = 0 at T_c = 8a/27b, rho_c = 1/3b (= 4/7, 3.5);
+    the two phases merge as T -> T_c with the textbook mean-field exponent 1/2,
+    and no coexistence exists above T_c."""
+    Tc, rc = O.critical_point(A_VDW, B_VDW)
+    assert abs(Tc - 4 / 7) < 1e-15 and abs(rc - 3.5) < 1e-14
+    assert abs(O.cs2(rc, A_VDW, B_VDW, Tc)) < 1e-14
+    h = 1e-4
+    d2 = (O.p0(rc + h, A_VDW, B_VDW, Tc) - 2 * O.p0(rc, A_VDW, B_VDW, Tc) + O.p0(rc - h, A_VDW, B_VDW, Tc)) / h ** 2
+    assert abs(d2) < 1e-6
+    gaps = [np.subtract(*O.coexistence(A_VDW, B_VDW, Tc * (1 - eps))) for eps in (1e-2, 1e-3, 1e-4)]
+    assert gaps[0] > gaps[1] > gaps[2] > 0
+    # mean-field (van der Waals) order parameter: rho_l - rho_g ~ (T_c - T)^(1/2)
+    assert abs(gaps[1] / gaps[2] - np.sqrt(10)) / np.sqrt(10) < 0.02
+    with pytest.raises(ValueError):
+        O.coexistence(A_VDW, B_VDW, Tc * 1.001)
+
+
+def test_mu0_is_derivative_of_free_energy():
+    """p0 = rho mu0 - psi with psi = rho T ln(rho/(1-b rho)) - a rho^2 - rho T (Eq. 2)."""
+    T = 0.55
+    r = np.linspace(1.0, 6.0, 11)
+    psi = r * T * np.log(r / (1 - B_VDW * r)) - A_VDW * r ** 2 - r * T
+    assert np.allclose(r * O.mu0(r, A_VDW, B_VDW, T) - psi, O.p0(r, A_VDW, B_VDW, T), rtol=1e-13)
