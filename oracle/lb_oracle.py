@@ -356,11 +356,15 @@ def coexistence(a, b, T):
     # spinodals: c_s^2 = 0 on either side of rho_c (c_s^2 < 0 between them)
     r_sp_g = _bisect(f, 1e-12, rc)
     r_sp_l = _bisect(f, rc, (1 - 1e-12) / b)
-    p_lo = max(float(p0(r_sp_l, a, b, T)), 1e-300)
     p_hi = float(p0(r_sp_g, a, b, T))
+    p_lo = float(p0(r_sp_l, a, b, T))
+    if p_lo <= 0.0:
+        # at low T the liquid spinodal pressure is negative; coexistence needs
+        # P > 0, and the gas branch then runs down to rho -> 0
+        p_lo = 1e-12 * p_hi
 
     def branches(P):
-        rg = _bisect(lambda r: float(p0(r, a, b, T)) - P, 1e-14, r_sp_g)
+        rg = _bisect(lambda r: float(p0(r, a, b, T)) - P, 0.0, r_sp_g)
         rl = _bisect(lambda r: float(p0(r, a, b, T)) - P, r_sp_l, (1 - 1e-14) / b)
         return rl, rg
 

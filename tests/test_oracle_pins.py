@@ -393,7 +393,7 @@ def test_coexistence_matches_paper_values():
     assert abs(rg - g["rho_g"]) / g["rho_g"] < 0.015
 
 
-@pytest.mark.parametrize("T", [0.50, 0.53, 0.55, 0.56, 0.57])
+@pytest.mark.parametrize("T", [0.30, 0.40, 0.45, 0.50, 0.53, 0.55, 0.56, 0.57])
 def test_coexistence_residuals(T):
     """Equal bulk pressure (Eq. 2) and equal chemical potential at coexistence."""
     rl, rg = O.coexistence(A_VDW, B_VDW, T)
