@@ -1,0 +1,302 @@
+#!/usr/bin/env python3
+"""Throughput of the fused free-energy lattice Boltzmann step on GB300.
+
+Workload: D3Q19, 128^3 periodic, one spherical drop R = 30 at the centre,
+forcing scheme (Sec. VI), van der Waals a = 9/49, b = 2/21, T = 0.55,
+kappa = 0.01, tau = 1.0 (synthetic drop, tanh profile of width 2).
+A step is one time step of the whole lattice (one fused kernel launch).
+
+Prints one JSON line: MLUPS (million lattice updates per second, whole job),
+the HBM roofline of the step kernel, an end-to-end number through the C ABI
+with host buffers, and the FP64 CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f16dev|bf16dev|f32|f64]
+  python bench.py --impl reference ...     (the oracle, timed on the host cores)
+Multi-GPU (N > 1, torchrun): independent replicas, one per GPU (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+A_VDW, B_VDW = 9.0 / 49.0, 2.0 / 21.0
+WORKLOAD = dict(lattice="D3Q19", n=128, R=30.0, scheme="forcing", T=0.55, kappa=0.01, tau=1.0, width=2.0)
+BYTES_POP = {"f64": (8, 8), "f32": (4, 4), "f16dev": (4, 2), "bf16dev": (4, 2)}   # (f_0, f_i) bytes
+
+
+def bytes_per_lu(storage: str, q: int = 19) -> int:
+    """Algorithmic HBM bytes per lattice update: one read and one write of
+    every stored population (rho is recomputed on chip, never stored)."""
+    b0, bi = BYTES_POP[storage]
+    return 2 * (b0 + (q - 1) * bi)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--storage", default="f16dev", choices=list(BYTES_POP))
+    p.add_argument("--n", type=int, default=WORKLOAD["n"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+def reduce_max(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def oracle_sample(n_edge: int, steps: int):
+    """FP64 oracle on an n_edge^3 periodic box holding the same drop scaled to
+    the box (R = 30/128 of the edge): returns (MLUPS, seconds, sites*steps)."""
+    from oracle import lb_oracle as O
+    m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme="forcing")
+    rl, rg = O.coexistence(A_VDW, B_VDW, WORKLOAD["T"])
+    R = WORKLOAD["R"] * n_edge / WORKLOAD["n"]
+    rho0 = O.drop_density((n_edge,) * 3, [(n_edge / 2,) * 3], [R], rl, rg, WORKLOAD["width"])
+    f = O.init_equilibrium(rho0, m)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = O.step(f, m)
+    dt = time.perf_counter() - t0
+    lu = n_edge ** 3 * steps
+    return lu / dt / 1e6, dt, lu
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args):
+    world, rank, local, dist = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    # each timed step: one oracle step on a sub-box sized so the whole run
+    # stays within about two minutes of host time
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rate = 0.25e6                                     # oracle LU/s, measured order of magnitude
+    edge = int(max(8, min(args.n, round((budget * rate) ** (1 / 3)))))
+    from oracle import lb_oracle as O
+    m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme="forcing")
+    rl, rg = O.coexistence(A_VDW, B_VDW, WORKLOAD["T"])
+    R = WORKLOAD["R"] * edge / WORKLOAD["n"]
+    f = O.init_equilibrium(O.drop_density((edge,) * 3, [(edge / 2,) * 3], [R], rl, rg, WORKLOAD["width"]), m)
+    for _ in range(args.warmup):
+        f = O.step(f, m)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = O.step(f, m)
+    dt = time.perf_counter() - t0
+    mlups = edge ** 3 * args.steps / dt / 1e6
+    sample = f"{args.steps} oracle steps on a {edge}^3 box (drop scaled to the box), FP64 numpy"
+    line = {"impl": "reference", "metric": "MLUPS (D3Q19 128^3 free-energy LB step, forcing scheme)",
+            "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"D3Q19 {WORKLOAD['n']}^3 drop R=30, forcing, T=0.55, kappa=0.01, tau=1",
+                       "sample_edge": edge},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    world, rank, local, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_0710_5470_gb300 import build, lb
+    if rank == 0:
+        build.build()
+    barrier(dist)
+    if rank != 0:
+        build.build()
+    lb.load_library()
+    storage = lb.STORAGE_NAMES[args.storage]
+    n = args.n
+    stream = torch.cuda.current_stream()
+    ctx = lb.Context(lb.D3Q19, (n, n, n), A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"],
+                     scheme=lb.FORCING, storage=storage, stream=stream.cuda_stream)
+    R = WORKLOAD["R"] * n / WORKLOAD["n"]
+    ctx.init_drops([(n / 2,) * 3], [R], WORKLOAD["width"])
+    ctx.step(args.warmup)
+    ctx.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms_local = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ctx.synchronize()
+    st = ctx.stats()
+    ms = reduce_max(dist, ms_local)
+    sites = n ** 3
+    mlups = sites * args.steps * world / (ms / 1e3) / 1e6
+
+    # roofline of the fused step kernel (the only kernel in the timed region)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    bpl = bytes_per_lu(args.storage)
+    t_launch = ms_local / args.steps / 1e3
+    achieved = bpl * sites / t_launch / 1e9
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        rl, rg = ctx.coexistence()
+        from paper_0710_5470_gb300 import inputs
+        rho_h = torch.empty(sites, dtype=torch.float64, pin_memory=True).numpy()
+        c, r = inputs.centred_drop((n, n, n), R)
+        z, y, x = np.meshgrid(*(np.arange(n, dtype=np.float64),) * 3, indexing="ij")
+        d = np.sqrt((x - c[0][0]) ** 2 + (y - c[0][1]) ** 2 + (z - c[0][2]) ** 2)
+        rho_h[:] = (rg + (rl - rg) * 0.5 * (1 + np.tanh((r[0] - d) / WORKLOAD["width"]))).reshape(-1)
+        out_rho = torch.empty(sites, dtype=torch.float64, pin_memory=True).numpy()
+        out_u = torch.empty(3 * sites, dtype=torch.float64, pin_memory=True).numpy()
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.init_fields(rho_h)
+        ctx.step(args.steps)
+        ctx.fields_into(out_rho, out_u)
+        dt = time.perf_counter() - t0
+        dt = reduce_max(dist, dt)
+        e2e = {"value": sites * args.steps * world / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": sites * 8 / args.steps, "d2h_bytes_per_step": sites * 8 * 4 / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        edge = 64
+        v, dt, lu = oracle_sample(edge, 2)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"2 FP64 oracle steps (numpy, single thread) on a {edge}^3 box with the drop scaled "
+                         f"to the box ({dt:.1f} s)"}
+
+    ctx.close()
+    if rank == 0:
+        line = {
+            "metric": "MLUPS (D3Q19 128^3 free-energy LB step, forcing scheme)",
+            "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage != "f64" else "f64", "data": "synthetic",
+            "config": {"workload": f"D3Q19 {n}^3 periodic, one drop R={R:g}, forcing scheme, T=0.55, "
+                                   f"kappa=0.01, tau=1.0", "storage": args.storage,
+                       "l2": "working set (two population buffers) larger than L2",
+                       "parallelism": f"{world} independent replica(s)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "bytes_per_lu": bpl,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "check": {"max_v": st["max_v"], "mass": st["mass"], "status": st["status"]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * lb.h - C ABI of the GB300 free-energy lattice Boltzmann library (liblb.so).
+ *
+ * The library advances the free-energy lattice Boltzmann scheme of Pooley &
+ * Furtado ("Eliminating spurious velocities in the free energy lattice
+ * Boltzmann method") for a van der Waals liquid-gas system on the D2Q9 and
+ * D3Q19 lattices:
+ *   - van der Waals bulk pressure p0 (Eq. 2) and lambda = nu (1 - 3 c_s^2) (Eq. 36);
+ *   - isotropic gradient / Laplacian stencils (Eq. 32 in 2D, Eq. 29 with the
+ *     coefficients of Eq. 31 in 3D);
+ *   - the tuned equilibrium distribution (Eqs. 5, 6 with the weights of
+ *     Sec. VIII / Eq. 31) - "equilibrium scheme";
+ *   - the momentum-conserving forcing variant (Sec. VI, Eqs. 27, 28), whose
+ *     update reads density two sites away - "forcing scheme";
+ *   - BGK collision and streaming (Eq. 4).
+ * Lattice units: dx = dt = c = 1.  Every domain is periodic in all directions.
+ *
+ * Conventions shared by every call
+ *   - Host arrays are owned by the caller and only read/written during the
+ *     call.  Fields are float64, structure of arrays, site index
+ *     x + nx*(y + ny*z), x fastest.  Vector fields are stored component by
+ *     component (all x components, then all y, then all z).
+ *   - Population arrays exchanged with the host are float64 with layout
+ *     [i][z][y][x], i the velocity index in the paper's order (Sec. II for
+ *     D2Q9, Sec. VII for D3Q19).  They hold f_i(r, t), the distribution after
+ *     streaming (the left-hand side of Eq. 4).
+ *   - Device memory belongs to the context and is released by lb_destroy.
+ *   - Every call returns an lb_status and never throws.  On error the
+ *     thread-local message of lb_last_error() says why.  A device error seen
+ *     by a context (a CUDA failure or a non-finite density) is sticky: every
+ *     later call on that context returns it until lb_destroy.
+ *   - Work is queued on the context's CUDA stream; calls that return host
+ *     data synchronise that stream.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,     /* invalid argument or parameter set */
+    LB_ENOMEM = 2,     /* device or host allocation failed */
+    LB_ECUDA = 3,      /* a CUDA runtime call failed */
+    LB_EUNSTABLE = 4,  /* a density became non-finite or non-positive */
+    LB_ETIMEOUT = 5,   /* a bounded device wait expired */
+    LB_ESTATE = 6      /* call made in the wrong order (e.g. step before init) */
+} lb_status;
+
+typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1 } lb_lattice;
+
+/* LB_SCHEME_EQUILIBRIUM: M_ab = kappa d_a rho d_b rho terms inside f^eq (Eq. 5).
+ * LB_SCHEME_FORCING: M_ab terms moved into the body force g (Sec. VI). */
+typedef enum { LB_SCHEME_EQUILIBRIUM = 0, LB_SCHEME_FORCING = 1 } lb_scheme;
+
+/* Storage of the populations in HBM.  Arithmetic is float64 for LB_F64 and
+ * float32 otherwise.  LB_F16DEV / LB_BF16DEV keep f_0 in float32 and store
+ * f_i - w_i p0(rho_ref) (i >= 1) in fp16 / bf16: w_i p0(rho_ref) is the rest
+ * equilibrium of Eq. 5 at u = 0 and zero gradients, the same in bulk liquid
+ * and gas at coexistence. */
+typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16DEV = 2, LB_BF16DEV = 3 } lb_storage;
+
+typedef struct {
+    int lattice;          /* lb_lattice */
+    int nx, ny, nz;       /* sites per direction, >= 1; nz must be 1 for D2Q9 */
+    double a, b, T;       /* van der Waals p0 = rho T/(1 - b rho) - a rho^2 (Eq. 2); 0 < T < 8a/27b */
+    double kappa;         /* gradient coefficient of Eq. 1, > 0 */
+    double tau;           /* BGK relaxation time of Eq. 4, > 1/2 */
+    int scheme;           /* lb_scheme */
+    int storage;          /* lb_storage */
+    double rho_ref;       /* reference density of the deviation storage; 0 => liquid coexistence density */
+} lb_params;
+
+typedef struct {
+    double mass;          /* sum_r rho (float64, fixed summation order) */
+    double momentum[3];   /* sum_r rho u (Eq. 3); unused components are 0 */
+    double max_u;         /* max_r |u|, u the lattice velocity of Eq. 3 */
+    double max_v;         /* max_r |v|, v = u + g/(2 rho) (Eq. 40); = max_u for the equilibrium scheme */
+    double min_rho, max_rho;
+    long long step;       /* time steps taken since the last init */
+    int status;           /* lb_status of the context */
+} lb_stats;
+
+/* Library version string (static storage). */
+const char* lb_version(void);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char* lb_last_error(void);
+
+/* Maxwell coexistence densities of the van der Waals fluid (Eq. 2, Sec. II):
+ * rho_l > rho_g with equal p0 and equal chemical potential
+ * mu0 = T ln(rho/(1 - b rho)) + T b rho/(1 - b rho) - 2 a rho.
+ * float64 Newton iteration on the host.  LB_EINVAL unless a, b > 0 and
+ * 0 < T < 8a/(27b) and both outputs are non-NULL. */
+lb_status lb_coexistence(double a, double b, double T, double* rho_l, double* rho_g);
+
+/* Create a context: validates *p, solves the coexistence densities and
+ * allocates the two population buffers on the current CUDA device.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream); it must
+ * outlive the context.  *out receives the context, or NULL on error. */
+lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out);
+
+/* Release every device allocation of the context.  NULL-safe. */
+lb_status lb_destroy(lb_ctx* ctx);
+
+/* Coexistence densities the context uses (liquid, gas). */
+lb_status lb_get_coexistence(const lb_ctx* ctx, double* rho_l, double* rho_g);
+
+/* Initialise drops (synthetic workload of Sec. IV): density
+ *   rho0 = rho_g + (rho_l - rho_g) * max_k 1/2 (1 + tanh((R_k - d_k)/width)),
+ * d_k the periodic minimum-image distance of integer site coordinates from
+ * centre k; then f = f^eq(rho0, u = 0) of the context's scheme (Eqs. 5, 6),
+ * gradients taken with the stencils.  centres: ndrops*dim doubles (x, y[, z]);
+ * radii: ndrops doubles > 0.  ndrops = 0 gives uniform gas.  Resets the step
+ * counter. */
+lb_status lb_init_drops(lb_ctx* ctx, int ndrops, const double* centres, const double* radii,
+                        double width);
+
+/* Initialise from a host density field rho (N doubles) and velocity u
+ * (dim*N doubles, NULL => 0): f = f^eq(rho, u) of the context's scheme. */
+lb_status lb_init_fields(lb_ctx* ctx, const double* rho, const double* u);
+
+/* Load / read the populations f_i(r, t) (Q*N float64, layout [i][z][y][x]).
+ * Loading converts to the context's storage (rounding for reduced storage)
+ * and resets the step counter. */
+lb_status lb_set_populations(lb_ctx* ctx, const double* f);
+lb_status lb_get_populations(lb_ctx* ctx, double* f);
+
+/* Advance nsteps >= 0 time steps of Eq. 4: one fused kernel per step
+ * (moments, stencils, equilibrium, force, BGK, streaming).  Asynchronous on
+ * the context's stream; a non-finite density raises the context's status,
+ * reported by the next synchronising call. */
+lb_status lb_step(lb_ctx* ctx, int nsteps);
+
+/* Wait for queued work; returns the context's status. */
+lb_status lb_synchronize(lb_ctx* ctx);
+
+/* Host copies of rho (N), u (dim*N) and v = u + g/(2 rho) (dim*N; Eq. 40,
+ * = u for the equilibrium scheme).  Any output may be NULL.  Synchronises. */
+lb_status lb_fields(lb_ctx* ctx, double* rho, double* u, double* v);
+
+/* float64 reductions of the current state (see lb_stats).  Synchronises. */
+lb_status lb_stats_get(lb_ctx* ctx, lb_stats* out);
+
+/* Number of sites N and populations Q of the context. */
+lb_status lb_shape(const lb_ctx* ctx, long long* n_sites, int* q);
+
+/* Device pointer of the current population buffer and its byte size, for
+ * callers that stage inputs in device memory themselves. */
+lb_status lb_device_state(lb_ctx* ctx, void** dptr, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,243 @@
+// Per-run and diagnostic kernels around the fused step: drop initialisation,
+// equilibrium initialisation, moments, the body force for v (Eq. 40),
+// population import/export and float64 reductions.  None of these is on the
+// per-step path; they read and write global memory directly.
+#pragma once
+#include "step_kernel.cuh"
+
+namespace lbk {
+
+struct PopPtrs {
+    char* p[MAXQ];
+    float fref[MAXQ];
+};
+
+struct Grid3 {
+    int nx, ny, nz;
+    __device__ __forceinline__ size_t n() const { return size_t(nx) * ny * nz; }
+    __device__ __forceinline__ void xyz(size_t idx, int& x, int& y, int& z) const {
+        x = int(idx % nx);
+        y = int((idx / nx) % ny);
+        z = int(idx / (size_t(nx) * ny));
+    }
+    __device__ __forceinline__ size_t at(int x, int y, int z) const {
+        return (size_t(wrapi(z, nz)) * ny + wrapi(y, ny)) * nx + wrapi(x, nx);
+    }
+};
+
+// Density of one or more drops: rho_g + (rho_l - rho_g) max_k 1/2 (1 + tanh((R_k - d_k)/w)),
+// d_k the periodic minimum-image distance of the site from centre k.
+static __global__ void drop_density_kernel(double* rho, Grid3 g, int dim, int ndrops, const double* centres,
+                                    const double* radii, double width, double rho_l, double rho_g) {
+    const size_t n = g.n();
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        g.xyz(idx, x, y, z);
+        const double c[3] = {double(x), double(y), double(z)};
+        const double sz[3] = {double(g.nx), double(g.ny), double(g.nz)};
+        double prof = 0.0;
+        for (int k = 0; k < ndrops; ++k) {
+            double d2 = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                double dd = fabs(c[a] - centres[k * dim + a]);
+                dd = fmin(dd, sz[a] - dd);
+                d2 += dd * dd;
+            }
+            const double pk = 0.5 * (1.0 + tanh((radii[k] - sqrt(d2)) / width));
+            prof = fmax(prof, pk);
+        }
+        rho[idx] = rho_g + (rho_l - rho_g) * prof;
+    }
+}
+
+// Gradient and Laplacian of a float64 field at one site (stencils of
+// Eq. 32 / Eq. 29 written as weighted sums over the velocity set).
+template <class L>
+__device__ __forceinline__ void stencils_global(const double* rho, Grid3 g, int x, int y, int z, double (&G)[3],
+                                                double& lap) {
+    G[0] = G[1] = G[2] = 0.0;
+    lap = 0.0;
+    const double r0 = rho[g.at(x, y, z)];
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const double rn = rho[g.at(x + L::ex(i), y + L::ey(i), z + L::ez(i))];
+        const double wi = w_vel<L>(i);
+#pragma unroll
+        for (int c = 0; c < L::D; ++c) {
+            if (e_comp<L>(i, c) == 1) G[c] += wi * rn;
+            if (e_comp<L>(i, c) == -1) G[c] -= wi * rn;
+        }
+        lap += wi * (rn - r0);
+    }
+    lap *= 2.0;
+}
+
+struct Phys {
+    double a, b, T, kappa, nu;
+};
+
+// f = f^eq(rho, u) of the chosen scheme (no force applied), float64 math.
+template <class L, bool FORCING, class S>
+__global__ void init_feq_kernel(const double* rho, const double* u, PopPtrs dst, Grid3 g, Phys ph) {
+    const size_t n = g.n();
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        g.xyz(idx, x, y, z);
+        double G[3], lap;
+        stencils_global<L>(rho, g, x, y, z, G, lap);
+        const double r = rho[idx];
+        double uu[3] = {0.0, 0.0, 0.0}, j[3] = {0.0, 0.0, 0.0};
+        if (u) {
+            for (int c = 0; c < L::D; ++c) {
+                uu[c] = u[c * n + idx];
+                j[c] = r * uu[c];
+            }
+        }
+        const double g0[3] = {0.0, 0.0, 0.0};
+        double feq[L::Q], F[L::Q];
+        equilibrium<L, FORCING, double>(r, j, uu, G, lap, g0, ph.a, ph.b, ph.T, ph.kappa, ph.nu, feq, F);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            S::store(i, dst.p[i], idx, typename S::real(feq[i]), dst.fref[i]);
+    }
+}
+
+// rho, u (Eq. 3) of the stored populations, float64 outputs.
+template <class L, class S>
+__global__ void moments_kernel(PopPtrs src, Grid3 g, double* rho, double* u) {
+    const size_t n = g.n();
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+        double f[L::Q];
+        double r = 0.0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            f[i] = double(S::load(i, src.p[i], idx, src.fref[i]));
+            r += f[i];
+        }
+        double j[3];
+        momentum<L, double>(f, j);
+        rho[idx] = r;
+        for (int c = 0; c < L::D; ++c) u[c * n + idx] = j[c] / r;
+    }
+}
+
+// M'_ab = kappa (G_a G_b - delta_ab |G|^2 / 2) of the density field.
+template <class L>
+__global__ void mprime_kernel(const double* rho, Grid3 g, double kappa, double* mp) {
+    const size_t n = g.n();
+    constexpr int NMC = L::D == 3 ? 6 : 3;
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        g.xyz(idx, x, y, z);
+        double G[3], lap;
+        stencils_global<L>(rho, g, x, y, z, G, lap);
+        double g2 = 0.0;
+        for (int c = 0; c < L::D; ++c) g2 += G[c] * G[c];
+        for (int c = 0; c < L::D; ++c)
+            for (int d = c; d < L::D; ++d) {
+                double v = kappa * G[c] * G[d];
+                if (c == d) v -= 0.5 * kappa * g2;
+                mp[size_t(mcomp<L::D>(c, d)) * n + idx] = v;
+            }
+        (void)NMC;
+    }
+}
+
+// g = -div M' (Eq. 28) and v = u + g/(2 rho) (Eq. 40).
+template <class L>
+__global__ void velocity_v_kernel(const double* rho, const double* u, const double* mp, Grid3 g, double* v) {
+    const size_t n = g.n();
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        g.xyz(idx, x, y, z);
+        double gf[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+            const size_t nb = g.at(x + L::ex(i), y + L::ey(i), z + L::ez(i));
+            const double wi = w_vel<L>(i);
+#pragma unroll
+            for (int c = 0; c < L::D; ++c)
+#pragma unroll
+                for (int d = 0; d < L::D; ++d) {
+                    const int ed = e_comp<L>(i, d);
+                    if (ed != 0) gf[c] -= wi * ed * mp[size_t(mcomp<L::D>(c, d)) * n + nb];
+                }
+        }
+        const double r = rho[idx];
+        for (int c = 0; c < L::D; ++c) v[c * n + idx] = u[c * n + idx] + gf[c] / (2.0 * r);
+    }
+}
+
+template <class L, class S>
+__global__ void get_pops_kernel(PopPtrs src, size_t n, double* out) {
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) out[i * n + idx] = double(S::load(i, src.p[i], idx, src.fref[i]));
+    }
+}
+
+template <class L, class S>
+__global__ void set_pops_kernel(PopPtrs dst, size_t n, const double* in) {
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            S::store(i, dst.p[i], idx, typename S::real(in[i * n + idx]), dst.fref[i]);
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+// Per-block partials of: mass, momentum[3], max|u|, max|v|, min rho, max rho.
+constexpr int NSTAT = 8;
+constexpr int STAT_THREADS = 256;
+
+static __global__ void __launch_bounds__(STAT_THREADS)
+    stats_partial_kernel(const double* rho, const double* u, const double* v, int dim, size_t n, double* partial) {
+    __shared__ double sh[NSTAT][STAT_THREADS];
+    double acc[NSTAT] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1e300, -1e300};
+    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
+        const double r = rho[idx];
+        acc[0] += r;
+        double u2 = 0.0, v2 = 0.0;
+        for (int c = 0; c < dim; ++c) {
+            const double uc = u[c * n + idx], vc = v[c * n + idx];
+            acc[1 + c] += r * uc;
+            u2 += uc * uc;
+            v2 += vc * vc;
+        }
+        acc[4] = fmax(acc[4], sqrt(u2));
+        acc[5] = fmax(acc[5], sqrt(v2));
+        acc[6] = fmin(acc[6], r);
+        acc[7] = fmax(acc[7], r);
+    }
+    for (int k = 0; k < NSTAT; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = STAT_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+            sh[4][threadIdx.x] = fmax(sh[4][threadIdx.x], sh[4][threadIdx.x + s]);
+            sh[5][threadIdx.x] = fmax(sh[5][threadIdx.x], sh[5][threadIdx.x + s]);
+            sh[6][threadIdx.x] = fmin(sh[6][threadIdx.x], sh[6][threadIdx.x + s]);
+            sh[7][threadIdx.x] = fmax(sh[7][threadIdx.x], sh[7][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NSTAT; ++k) partial[size_t(blockIdx.x) * NSTAT + k] = sh[k][0];
+}
+
+// Folds the per-block partials in block order (deterministic).
+static __global__ void stats_final_kernel(const double* partial, int nblocks, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double acc[NSTAT] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1e300, -1e300};
+    for (int b = 0; b < nblocks; ++b) {
+        const double* p = partial + size_t(b) * NSTAT;
+        for (int k = 0; k < 4; ++k) acc[k] += p[k];
+        acc[4] = fmax(acc[4], p[4]);
+        acc[5] = fmax(acc[5], p[5]);
+        acc[6] = fmin(acc[6], p[6]);
+        acc[7] = fmax(acc[7], p[7]);
+    }
+    for (int k = 0; k < NSTAT; ++k) out[k] = acc[k];
+}
+
+}  // namespace lbk

@@ -1,0 +1,19 @@
+// Kernel instantiations for the D2Q9 lattice.
+#include "kernels_impl.cuh"
+
+using namespace lbk;
+
+template <bool F>
+static LbKernelSet pick(int storage) {
+    switch (storage) {
+        case 0: return Launchers<D2Q9, F, StF64, 32, 8>::make();
+        case 1: return Launchers<D2Q9, F, StF32, 32, 16>::make();
+        case 2: return Launchers<D2Q9, F, StF16, 32, 16>::make();
+        case 3: return Launchers<D2Q9, F, StBF16, 32, 16>::make();
+    }
+    return LbKernelSet{};
+}
+
+LbKernelSet lbk_kernels_d2q9(int scheme, int storage) {
+    return scheme == 1 ? pick<true>(storage) : pick<false>(storage);
+}

@@ -1,0 +1,19 @@
+// Kernel instantiations for the D3Q19 lattice.
+#include "kernels_impl.cuh"
+
+using namespace lbk;
+
+template <bool F>
+static LbKernelSet pick(int storage) {
+    switch (storage) {
+        case 0: return Launchers<D3Q19, F, StF64, 32, 4>::make();
+        case 1: return Launchers<D3Q19, F, StF32, 32, 8>::make();
+        case 2: return Launchers<D3Q19, F, StF16, 32, 8>::make();
+        case 3: return Launchers<D3Q19, F, StBF16, 32, 8>::make();
+    }
+    return LbKernelSet{};
+}
+
+LbKernelSet lbk_kernels_d3q19(int scheme, int storage) {
+    return scheme == 1 ? pick<true>(storage) : pick<false>(storage);
+}

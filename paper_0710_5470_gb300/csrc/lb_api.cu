@@ -1,0 +1,511 @@
+// Host side of the C ABI declared in include/lb.h: parameter validation,
+// the Maxwell construction, device buffers, and kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "dispatch.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lb_status fail(lb_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+lb_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ thermodynamics
+// van der Waals bulk pressure (Eq. 2), its derivative and the chemical potential.
+double p0_vdw(double r, double a, double b, double T) { return r * T / (1.0 - b * r) - a * r * r; }
+double cs2_vdw(double r, double a, double b, double T) {
+    const double ib = 1.0 / (1.0 - b * r);
+    return T * ib * ib - 2.0 * a * r;
+}
+double mu_vdw(double r, double a, double b, double T) {
+    return T * std::log(r / (1.0 - b * r)) + T * b * r / (1.0 - b * r) - 2.0 * a * r;
+}
+
+// Safeguarded Newton for fn(x) = target on [lo, hi] with fn increasing.
+template <class F, class DF>
+double newton_bracketed(F fn, DF dfn, double target, double lo, double hi) {
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        const double r = fn(x) - target;
+        if (r > 0) hi = x; else lo = x;
+        const double d = dfn(x);
+        double xn = (d > 0) ? x - r / d : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (std::fabs(xn - x) <= 1e-15 * std::fabs(x)) return xn;
+        x = xn;
+    }
+    return x;
+}
+
+// Maxwell construction: pressure P such that mu(rho_l(P)) = mu(rho_g(P)),
+// where rho_g(P), rho_l(P) solve p0 = P on the gas and liquid branches.  Newton
+// on P with d(mu_l - mu_g)/dP = 1/rho_l - 1/rho_g (dmu = dp/rho on a branch).
+lb_status maxwell(double a, double b, double T, double* rl_out, double* rg_out) {
+    if (!(a > 0 && b > 0)) return fail(LB_EINVAL, "coexistence: a and b must be positive");
+    const double Tc = 8.0 * a / (27.0 * b);
+    if (!(T > 0 && T < Tc)) return fail(LB_EINVAL, "coexistence: T must lie in (0, 8a/27b)");
+    // c_s^2 decreases up to rho* = (1 - (bT/a)^(1/3))/b and increases beyond;
+    // the spinodals are its zeros on either side.
+    const double rstar = (1.0 - std::cbrt(b * T / a)) / b;
+    auto dcs2 = [&](double r) { return 2.0 * b * T / std::pow(1.0 - b * r, 3) - 2.0 * a; };
+    auto neg_cs2 = [&](double r) { return -cs2_vdw(r, a, b, T); };
+    auto neg_dcs2 = [&](double r) { return -dcs2(r); };
+    const double sp_g = newton_bracketed(neg_cs2, neg_dcs2, 0.0, 1e-300, rstar);
+    const double sp_l = newton_bracketed([&](double r) { return cs2_vdw(r, a, b, T); }, dcs2, 0.0, rstar,
+                                         (1.0 - 1e-15) / b);
+    auto p = [&](double r) { return p0_vdw(r, a, b, T); };
+    auto dp = [&](double r) { return cs2_vdw(r, a, b, T); };
+    double plo = std::max(p(sp_l), 1e-300), phi = p(sp_g);
+    double P = 0.5 * (plo + phi);
+    double rl = 0, rg = 0;
+    for (int it = 0; it < 200; ++it) {
+        rg = newton_bracketed(p, dp, P, 1e-300, sp_g);
+        rl = newton_bracketed(p, dp, P, sp_l, (1.0 - 1e-15) / b);
+        const double dmu = mu_vdw(rl, a, b, T) - mu_vdw(rg, a, b, T);
+        // mu_l - mu_g decreases with P (slope 1/rho_l - 1/rho_g < 0): keep the bracket
+        if (dmu > 0) plo = P; else phi = P;
+        const double slope = 1.0 / rl - 1.0 / rg;
+        double Pn = P - dmu / slope;
+        if (!(Pn > plo && Pn < phi)) Pn = 0.5 * (plo + phi);
+        if (std::fabs(Pn - P) <= 1e-16 * std::fabs(P)) { P = Pn; break; }
+        P = Pn;
+    }
+    rg = newton_bracketed(p, dp, P, 1e-300, sp_g);
+    rl = newton_bracketed(p, dp, P, sp_l, (1.0 - 1e-15) / b);
+    *rl_out = rl;
+    *rg_out = rg;
+    return LB_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct lb_ctx {
+    lb_params p{};
+    int D = 2, Q = 9;
+    size_t N = 0;
+    size_t pitch = 0;        // elements per population array (padded)
+    size_t buf_bytes = 0;    // bytes of one population buffer
+    char* fbuf = nullptr;    // two buffers back to back
+    int cur = 0;
+    double rho_l = 0, rho_g = 0;
+    float fref[lbk::MAXQ] = {};
+    cudaStream_t stream = nullptr;
+    unsigned* d_status = nullptr;
+    LbKernelSet ks;
+    int lz = 1;
+    dim3 grid;
+    bool initialised = false;
+    long long step = 0;
+    lb_status sticky = LB_OK;
+    // lazily allocated work arrays (fields, reductions)
+    double* w_rho = nullptr;
+    double* w_u = nullptr;
+    double* w_v = nullptr;
+    double* w_mp = nullptr;
+    double* w_part = nullptr;
+    int stat_blocks = 0;
+    double* w_io = nullptr;   // Q*N staging for population import/export
+};
+
+namespace {
+
+size_t pop_offset(const lb_ctx* c, int i, int buf) {
+    // buffer layout: population 0 first, then 1..Q-1; each array padded to `pitch`
+    size_t off = 0;
+    const int elem0 = (c->p.storage == LB_F64) ? 8 : 4;
+    const int elemi = (c->p.storage == LB_F64) ? 8 : (c->p.storage == LB_F32 ? 4 : 2);
+    if (i > 0) off = c->pitch * elem0 + size_t(i - 1) * c->pitch * elemi;
+    return size_t(buf) * c->buf_bytes + off;
+}
+
+lbk::PopPtrs pop_ptrs(const lb_ctx* c, int buf) {
+    lbk::PopPtrs pp{};
+    for (int i = 0; i < c->Q; ++i) {
+        pp.p[i] = c->fbuf + pop_offset(c, i, buf);
+        pp.fref[i] = c->fref[i];
+    }
+    return pp;
+}
+
+lbk::Grid3 grid3(const lb_ctx* c) { return lbk::Grid3{c->p.nx, c->p.ny, c->p.nz}; }
+
+lbk::Phys phys(const lb_ctx* c) {
+    return lbk::Phys{c->p.a, c->p.b, c->p.T, c->p.kappa, (c->p.tau - 0.5) / 3.0};
+}
+
+lb_status check_ctx(lb_ctx* c) {
+    if (!c) return fail(LB_EINVAL, "null context");
+    if (c->sticky != LB_OK) return fail(c->sticky, "context is in an error state: " + g_last_error);
+    return LB_OK;
+}
+
+lb_status record(lb_ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return LB_OK;
+    c->sticky = LB_ECUDA;
+    return cuda_fail(e, where);
+}
+
+lb_status ensure_work(lb_ctx* c) {
+    if (c->w_rho) return LB_OK;
+    const size_t n = c->N;
+    const int nmc = c->D == 3 ? 6 : 3;
+    c->stat_blocks = int(std::min<size_t>(1024, (n + lbk::STAT_THREADS - 1) / lbk::STAT_THREADS));
+    if (c->stat_blocks < 1) c->stat_blocks = 1;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->w_rho, n * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->w_u, 3 * n * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->w_v, 3 * n * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->w_mp, nmc * n * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->w_part, (size_t(c->stat_blocks) + 1) * lbk::NSTAT * sizeof(double))) != cudaSuccess)
+        return fail(LB_ENOMEM, std::string("work arrays: ") + cudaGetErrorString(e));
+    return LB_OK;
+}
+
+lb_status ensure_io(lb_ctx* c) {
+    if (c->w_io) return LB_OK;
+    cudaError_t e = cudaMalloc(&c->w_io, size_t(c->Q) * c->N * sizeof(double));
+    if (e != cudaSuccess) return fail(LB_ENOMEM, std::string("staging buffer: ") + cudaGetErrorString(e));
+    return LB_OK;
+}
+
+lb_status sync_status(lb_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return record(c, e, "cudaStreamSynchronize");
+    unsigned st = 0;
+    e = cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return record(c, e, "status read");
+    if (st) {
+        c->sticky = LB_EUNSTABLE;
+        return fail(LB_EUNSTABLE, "non-finite or non-positive density");
+    }
+    return LB_OK;
+}
+
+// rho, u (and v for the forcing scheme) of the current state in the work arrays.
+lb_status compute_fields(lb_ctx* c, bool need_v) {
+    lb_status s = ensure_work(c);
+    if (s != LB_OK) return s;
+    const lbk::PopPtrs src = pop_ptrs(c, c->cur);
+    cudaError_t e = c->ks.moments(src, grid3(c), c->w_rho, c->w_u, c->stream);
+    if (e != cudaSuccess) return record(c, e, "moments");
+    if (need_v && c->p.scheme == LB_SCHEME_FORCING) {
+        e = c->ks.mprime(c->w_rho, grid3(c), c->p.kappa, c->w_mp, c->stream);
+        if (e == cudaSuccess) e = c->ks.velocity_v(c->w_rho, c->w_u, c->w_mp, grid3(c), c->w_v, c->stream);
+        if (e != cudaSuccess) return record(c, e, "body force");
+    } else if (need_v) {
+        e = cudaMemcpyAsync(c->w_v, c->w_u, size_t(c->D) * c->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream);
+        if (e != cudaSuccess) return record(c, e, "copy u");
+    }
+    return LB_OK;
+}
+
+lb_status validate(const lb_params* p) {
+    if (!p) return fail(LB_EINVAL, "null parameters");
+    if (p->lattice != LB_D2Q9 && p->lattice != LB_D3Q19) return fail(LB_EINVAL, "unknown lattice");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LB_EINVAL, "grid sizes must be >= 1");
+    if (p->lattice == LB_D2Q9 && p->nz != 1) return fail(LB_EINVAL, "D2Q9 needs nz = 1");
+    if (double(p->nx) * p->ny > 2.0e9) return fail(LB_EINVAL, "nx*ny too large");
+    if (!(p->tau > 0.5)) return fail(LB_EINVAL, "tau must exceed 1/2");
+    if (!(p->kappa > 0)) return fail(LB_EINVAL, "kappa must be positive");
+    if (!(p->a > 0 && p->b > 0)) return fail(LB_EINVAL, "a and b must be positive");
+    const double Tc = 8.0 * p->a / (27.0 * p->b);
+    if (!(p->T > 0 && p->T < Tc)) return fail(LB_EINVAL, "T must lie in (0, 8a/27b)");
+    if (p->scheme != LB_SCHEME_EQUILIBRIUM && p->scheme != LB_SCHEME_FORCING) return fail(LB_EINVAL, "unknown scheme");
+    if (p->storage < LB_F64 || p->storage > LB_BF16DEV) return fail(LB_EINVAL, "unknown storage");
+    if (p->rho_ref < 0 || (p->rho_ref > 0 && p->rho_ref * p->b >= 1.0)) return fail(LB_EINVAL, "rho_ref out of range");
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_version(void) { return "lbgb 0.1 (sm_103a)"; }
+
+const char* lb_last_error(void) { return g_last_error.c_str(); }
+
+lb_status lb_coexistence(double a, double b, double T, double* rho_l, double* rho_g) {
+    if (!rho_l || !rho_g) return fail(LB_EINVAL, "null output");
+    return maxwell(a, b, T, rho_l, rho_g);
+}
+
+lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
+    if (!out) return fail(LB_EINVAL, "null output");
+    *out = nullptr;
+    lb_status s = validate(p);
+    if (s != LB_OK) return s;
+    lb_ctx* c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(LB_ENOMEM, "host allocation");
+    c->p = *p;
+    c->D = p->lattice == LB_D2Q9 ? 2 : 3;
+    c->Q = p->lattice == LB_D2Q9 ? 9 : 19;
+    c->N = size_t(p->nx) * p->ny * p->nz;
+    c->pitch = (c->N + 127) / 128 * 128;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    s = maxwell(p->a, p->b, p->T, &c->rho_l, &c->rho_g);
+    if (s != LB_OK) { delete c; return s; }
+    const double rref = p->rho_ref > 0 ? p->rho_ref : c->rho_l;
+    const double pref = p0_vdw(rref, p->a, p->b, p->T);
+    for (int i = 0; i < lbk::MAXQ; ++i) c->fref[i] = 0.0f;
+    if (p->storage == LB_F16DEV || p->storage == LB_BF16DEV) {
+        for (int i = 1; i < c->Q; ++i) {
+            const double w = c->D == 2 ? lbk::w_vel<lbk::D2Q9>(i) : lbk::w_vel<lbk::D3Q19>(i);
+            c->fref[i] = float(w * pref);
+        }
+    }
+    const int elem0 = p->storage == LB_F64 ? 8 : 4;
+    const int elemi = p->storage == LB_F64 ? 8 : (p->storage == LB_F32 ? 4 : 2);
+    c->buf_bytes = c->pitch * (elem0 + size_t(c->Q - 1) * elemi);
+    c->ks = c->D == 2 ? lbk_kernels_d2q9(p->scheme, p->storage) : lbk_kernels_d3q19(p->scheme, p->storage);
+    if (!c->ks.step) { delete c; return fail(LB_EINVAL, "no kernel for this combination"); }
+
+    cudaError_t e = cudaMalloc(&c->fbuf, 2 * c->buf_bytes);
+    if (e != cudaSuccess) { delete c; return fail(LB_ENOMEM, std::string("population buffers: ") + cudaGetErrorString(e)); }
+    e = cudaMalloc(&c->d_status, sizeof(unsigned));
+    if (e != cudaSuccess) { cudaFree(c->fbuf); delete c; return fail(LB_ENOMEM, "status word"); }
+    cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+
+    // launch geometry of the fused step: one CTA per TX x TY column tile and z chunk;
+    // the z chunk is sized so that all CTAs are resident at once where possible.
+    int dev = 0, sms = 0, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(c->ks.step_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c->ks.smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->ks.step_fn, c->ks.tx * c->ks.ty, c->ks.smem) !=
+            cudaSuccess || occ < 1)
+        occ = 1;
+    cudaGetLastError();
+    const int gx = (p->nx + c->ks.tx - 1) / c->ks.tx;
+    const int gy = (p->ny + c->ks.ty - 1) / c->ks.ty;
+    int gz = 1;
+    c->lz = 1;
+    if (c->D == 3) {
+        const long long slots = (long long)std::max(sms, 1) * occ;
+        long long chunks = slots / ((long long)gx * gy);
+        if (chunks < 1) chunks = 1;
+        int lz = int((p->nz + chunks - 1) / chunks);
+        if (lz < 4) lz = std::min(4, p->nz);
+        c->lz = lz;
+        gz = (p->nz + lz - 1) / lz;
+    }
+    c->grid = dim3(gx, gy, gz);
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx* c) {
+    if (!c) return LB_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    cudaFree(c->fbuf);
+    cudaFree(c->d_status);
+    cudaFree(c->w_rho);
+    cudaFree(c->w_u);
+    cudaFree(c->w_v);
+    cudaFree(c->w_mp);
+    cudaFree(c->w_part);
+    cudaFree(c->w_io);
+    delete c;
+    return LB_OK;
+}
+
+lb_status lb_get_coexistence(const lb_ctx* c, double* rho_l, double* rho_g) {
+    if (!c || !rho_l || !rho_g) return fail(LB_EINVAL, "null argument");
+    *rho_l = c->rho_l;
+    *rho_g = c->rho_g;
+    return LB_OK;
+}
+
+lb_status lb_shape(const lb_ctx* c, long long* n_sites, int* q) {
+    if (!c) return fail(LB_EINVAL, "null context");
+    if (n_sites) *n_sites = (long long)c->N;
+    if (q) *q = c->Q;
+    return LB_OK;
+}
+
+lb_status lb_device_state(lb_ctx* c, void** dptr, size_t* bytes) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (dptr) *dptr = c->fbuf + size_t(c->cur) * c->buf_bytes;
+    if (bytes) *bytes = c->buf_bytes;
+    return LB_OK;
+}
+
+static lb_status init_from_device_rho(lb_ctx* c, const double* d_rho, const double* d_u) {
+    const lbk::PopPtrs dst = pop_ptrs(c, c->cur);
+    cudaError_t e = c->ks.init_feq(d_rho, d_u, dst, grid3(c), phys(c), c->stream);
+    if (e != cudaSuccess) return record(c, e, "init_feq");
+    e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return record(c, e, "status reset");
+    c->initialised = true;
+    c->step = 0;
+    return sync_status(c);
+}
+
+lb_status lb_init_drops(lb_ctx* c, int ndrops, const double* centres, const double* radii, double width) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (ndrops < 0 || (ndrops > 0 && (!centres || !radii))) return fail(LB_EINVAL, "bad drop list");
+    if (!(width > 0)) return fail(LB_EINVAL, "width must be positive");
+    for (int k = 0; k < ndrops; ++k)
+        if (!(radii[k] > 0)) return fail(LB_EINVAL, "drop radii must be positive");
+    if ((s = ensure_work(c)) != LB_OK) return s;
+    double* d_drops = nullptr;
+    const size_t nd = size_t(ndrops) * (c->D + 1);
+    cudaError_t e = cudaSuccess;
+    if (ndrops > 0) {
+        e = cudaMalloc(&d_drops, nd * sizeof(double));
+        if (e != cudaSuccess) return fail(LB_ENOMEM, "drop list");
+        std::vector<double> h(nd);
+        std::memcpy(h.data(), centres, size_t(ndrops) * c->D * sizeof(double));
+        std::memcpy(h.data() + size_t(ndrops) * c->D, radii, size_t(ndrops) * sizeof(double));
+        e = cudaMemcpyAsync(d_drops, h.data(), nd * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e == cudaSuccess) {
+        lbk::drop_density_kernel<<<lbk_aux_blocks(c->N), 256, 0, c->stream>>>(
+            c->w_rho, grid3(c), c->D, ndrops, d_drops, d_drops ? d_drops + size_t(ndrops) * c->D : nullptr,
+            width, c->rho_l, c->rho_g);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) { cudaFree(d_drops); return record(c, e, "drop density"); }
+    s = init_from_device_rho(c, c->w_rho, nullptr);
+    cudaFree(d_drops);
+    return s;
+}
+
+lb_status lb_init_fields(lb_ctx* c, const double* rho, const double* u) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!rho) return fail(LB_EINVAL, "null density");
+    if ((s = ensure_work(c)) != LB_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(c->w_rho, rho, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && u)
+        e = cudaMemcpyAsync(c->w_u, u, size_t(c->D) * c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return record(c, e, "field upload");
+    return init_from_device_rho(c, c->w_rho, u ? c->w_u : nullptr);
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* f) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!f) return fail(LB_EINVAL, "null populations");
+    if ((s = ensure_io(c)) != LB_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(c->w_io, f, size_t(c->Q) * c->N * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = c->ks.set_pops(pop_ptrs(c, c->cur), c->N, c->w_io, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return record(c, e, "set populations");
+    c->initialised = true;
+    c->step = 0;
+    return sync_status(c);
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* f) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!f) return fail(LB_EINVAL, "null output");
+    if (!c->initialised) return fail(LB_ESTATE, "state not initialised");
+    if ((s = ensure_io(c)) != LB_OK) return s;
+    cudaError_t e = c->ks.get_pops(pop_ptrs(c, c->cur), c->N, c->w_io, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, c->w_io, size_t(c->Q) * c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return record(c, e, "get populations");
+    return sync_status(c);
+}
+
+lb_status lb_step(lb_ctx* c, int nsteps) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (nsteps < 0) return fail(LB_EINVAL, "nsteps must be >= 0");
+    if (!c->initialised) return fail(LB_ESTATE, "step before init");
+    lbk::StepArgs a{};
+    a.nx = c->p.nx;
+    a.ny = c->p.ny;
+    a.nz = c->p.nz;
+    a.lz = c->lz;
+    a.a = c->p.a;
+    a.b = c->p.b;
+    a.T = c->p.T;
+    a.kappa = c->p.kappa;
+    a.omega = 1.0 / c->p.tau;
+    a.nu = (c->p.tau - 0.5) / 3.0;
+    a.status = c->d_status;
+    for (int i = 0; i < lbk::MAXQ; ++i) a.fref[i] = c->fref[i];
+    for (int k = 0; k < nsteps; ++k) {
+        for (int i = 0; i < c->Q; ++i) {
+            a.src[i] = c->fbuf + pop_offset(c, i, c->cur);
+            a.dst[i] = c->fbuf + pop_offset(c, i, 1 - c->cur);
+        }
+        cudaError_t e = c->ks.step(a, c->grid, c->stream);
+        if (e != cudaSuccess) return record(c, e, "step kernel");
+        c->cur = 1 - c->cur;
+        ++c->step;
+    }
+    return LB_OK;
+}
+
+lb_status lb_synchronize(lb_ctx* c) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    return sync_status(c);
+}
+
+lb_status lb_fields(lb_ctx* c, double* rho, double* u, double* v) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!c->initialised) return fail(LB_ESTATE, "state not initialised");
+    if ((s = compute_fields(c, v != nullptr)) != LB_OK) return s;
+    cudaError_t e = cudaSuccess;
+    const size_t dn = size_t(c->D) * c->N * sizeof(double);
+    if (rho) e = cudaMemcpyAsync(rho, c->w_rho, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, c->w_u, dn, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, c->w_v, dn, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return record(c, e, "field download");
+    return sync_status(c);
+}
+
+lb_status lb_stats_get(lb_ctx* c, lb_stats* out) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!out) return fail(LB_EINVAL, "null output");
+    if (!c->initialised) return fail(LB_ESTATE, "state not initialised");
+    if ((s = compute_fields(c, true)) != LB_OK) return s;
+    double* part = c->w_part;
+    double* res = c->w_part + size_t(c->stat_blocks) * lbk::NSTAT;
+    lbk::stats_partial_kernel<<<c->stat_blocks, lbk::STAT_THREADS, 0, c->stream>>>(c->w_rho, c->w_u, c->w_v, c->D,
+                                                                                   c->N, part);
+    lbk::stats_final_kernel<<<1, 32, 0, c->stream>>>(part, c->stat_blocks, res);
+    double h[lbk::NSTAT];
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return record(c, e, "stats");
+    s = sync_status(c);
+    std::memset(out, 0, sizeof(*out));
+    out->mass = h[0];
+    out->momentum[0] = h[1];
+    out->momentum[1] = h[2];
+    out->momentum[2] = h[3];
+    out->max_u = h[4];
+    out->max_v = h[5];
+    out->min_rho = h[6];
+    out->max_rho = h[7];
+    out->step = c->step;
+    out->status = int(c->sticky);
+    return s;
+}
+
+}  // extern "C"

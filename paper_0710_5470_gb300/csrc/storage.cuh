@@ -1,0 +1,77 @@
+// Storage formats of the populations in HBM.
+//
+//   StF64   f_i in float64, arithmetic in float64;
+//   StF32   f_i in float32, arithmetic in float32;
+//   StF16   f_0 in float32, f_i - fref_i (i >= 1) in fp16, arithmetic float32;
+//   StBF16  f_0 in float32, f_i - fref_i (i >= 1) in bf16, arithmetic float32.
+// fref_i = w_i p0(rho_ref) is the rest equilibrium of Eq. 5 (u = 0, zero
+// gradients); bulk liquid and gas at coexistence share p0, so the stored
+// deviations are small away from interfaces.  f_0 carries the O(1) density
+// contrast between the phases and stays float32.
+//
+// Populations are separate arrays (structure of arrays), one pointer each.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace lbk {
+
+struct StF64 {
+    using real = double;
+    static constexpr int id = 0;
+    __host__ __device__ static constexpr int bytes(int) { return 8; }
+    __device__ __forceinline__ static real load(int, const char* p, size_t idx, float) {
+        return reinterpret_cast<const double*>(p)[idx];
+    }
+    __device__ __forceinline__ static void store(int, char* p, size_t idx, real v, float) {
+        reinterpret_cast<double*>(p)[idx] = v;
+    }
+};
+
+struct StF32 {
+    using real = float;
+    static constexpr int id = 1;
+    __host__ __device__ static constexpr int bytes(int) { return 4; }
+    __device__ __forceinline__ static real load(int, const char* p, size_t idx, float) {
+        return reinterpret_cast<const float*>(p)[idx];
+    }
+    __device__ __forceinline__ static void store(int, char* p, size_t idx, real v, float) {
+        reinterpret_cast<float*>(p)[idx] = v;
+    }
+};
+
+struct StF16 {
+    using real = float;
+    static constexpr int id = 2;
+    __host__ __device__ static constexpr int bytes(int i) { return i == 0 ? 4 : 2; }
+    __device__ __forceinline__ static real load(int i, const char* p, size_t idx, float ref) {
+        if (i == 0) return reinterpret_cast<const float*>(p)[idx];
+        return __half2float(reinterpret_cast<const __half*>(p)[idx]) + ref;
+    }
+    __device__ __forceinline__ static void store(int i, char* p, size_t idx, real v, float ref) {
+        if (i == 0) {
+            reinterpret_cast<float*>(p)[idx] = v;
+            return;
+        }
+        reinterpret_cast<__half*>(p)[idx] = __float2half_rn(v - ref);
+    }
+};
+
+struct StBF16 {
+    using real = float;
+    static constexpr int id = 3;
+    __host__ __device__ static constexpr int bytes(int i) { return i == 0 ? 4 : 2; }
+    __device__ __forceinline__ static real load(int i, const char* p, size_t idx, float ref) {
+        if (i == 0) return reinterpret_cast<const float*>(p)[idx];
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[idx]) + ref;
+    }
+    __device__ __forceinline__ static void store(int i, char* p, size_t idx, real v, float ref) {
+        if (i == 0) {
+            reinterpret_cast<float*>(p)[idx] = v;
+            return;
+        }
+        reinterpret_cast<__nv_bfloat16*>(p)[idx] = __float2bfloat16_rn(v - ref);
+    }
+};
+
+}  // namespace lbk

@@ -1,0 +1,197 @@
+"""Python binding of liblb.so (the C ABI of include/lb.h).
+
+Argument marshalling only: every step of the lattice Boltzmann update runs in
+the library's CUDA kernels.  There is no CPU fallback; importing this module
+without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblb.so")
+
+D2Q9, D3Q19 = 0, 1
+EQUILIBRIUM, FORCING = 0, 1
+F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
+STORAGE_NAMES = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV}
+STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_EUNSTABLE", 5: "LB_ETIMEOUT",
+          6: "LB_ESTATE"}
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lb_params(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("a", C.c_double), ("b", C.c_double), ("T", C.c_double), ("kappa", C.c_double),
+                ("tau", C.c_double), ("scheme", C.c_int), ("storage", C.c_int), ("rho_ref", C.c_double)]
+
+
+class lb_stats(C.Structure):
+    _fields_ = [("mass", C.c_double), ("momentum", C.c_double * 3), ("max_u", C.c_double),
+                ("max_v", C.c_double), ("min_rho", C.c_double), ("max_rho", C.c_double),
+                ("step", C.c_longlong), ("status", C.c_int)]
+
+
+_lib = None
+
+_DPTR = C.POINTER(C.c_double)
+_SIGNATURES = {
+    "lb_version": (C.c_char_p, []),
+    "lb_last_error": (C.c_char_p, []),
+    "lb_coexistence": (C.c_int, [C.c_double, C.c_double, C.c_double, _DPTR, _DPTR]),
+    "lb_create": (C.c_int, [C.POINTER(lb_params), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lb_destroy": (C.c_int, [C.c_void_p]),
+    "lb_get_coexistence": (C.c_int, [C.c_void_p, _DPTR, _DPTR]),
+    "lb_init_drops": (C.c_int, [C.c_void_p, C.c_int, _DPTR, _DPTR, C.c_double]),
+    "lb_init_fields": (C.c_int, [C.c_void_p, _DPTR, _DPTR]),
+    "lb_set_populations": (C.c_int, [C.c_void_p, _DPTR]),
+    "lb_get_populations": (C.c_int, [C.c_void_p, _DPTR]),
+    "lb_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lb_synchronize": (C.c_int, [C.c_void_p]),
+    "lb_fields": (C.c_int, [C.c_void_p, _DPTR, _DPTR, _DPTR]),
+    "lb_stats_get": (C.c_int, [C.c_void_p, C.POINTER(lb_stats)]),
+    "lb_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+    "lb_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+}
+
+
+def load_library(path: str | None = None):
+    """Load liblb.so (built by paper_0710_5470_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_0710_5470_gb300.build.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise LBError(status, load_library().lb_last_error().decode())
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DPTR)
+
+
+def coexistence(a: float, b: float, T: float):
+    """lb_coexistence: Maxwell densities (rho_l, rho_g) of the van der Waals fluid."""
+    rl, rg = C.c_double(), C.c_double()
+    _check(load_library().lb_coexistence(a, b, T, C.byref(rl), C.byref(rg)))
+    return rl.value, rg.value
+
+
+def version() -> str:
+    return load_library().lb_version().decode()
+
+
+class Context:
+    """One lattice (lb_create ... lb_destroy)."""
+
+    def __init__(self, lattice: int, shape, a: float, b: float, T: float, kappa: float, tau: float,
+                 scheme: int = EQUILIBRIUM, storage: int = F64, rho_ref: float = 0.0, stream=None):
+        lib = load_library()
+        nx, ny, nz = (tuple(shape) + (1,))[:3] if len(shape) == 2 else tuple(shape)
+        self.params = lb_params(lattice, nx, ny, nz, a, b, T, kappa, tau, scheme, storage, rho_ref)
+        self.dim = 2 if lattice == D2Q9 else 3
+        self.q = 9 if lattice == D2Q9 else 19
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        h = C.c_void_p()
+        st = C.c_void_p(int(stream)) if stream else None
+        _check(lib.lb_create(C.byref(self.params), st, C.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def coexistence(self):
+        rl, rg = C.c_double(), C.c_double()
+        _check(self._lib.lb_get_coexistence(self._h, C.byref(rl), C.byref(rg)))
+        return rl.value, rg.value
+
+    def init_drops(self, centres, radii, width: float = 2.0):
+        c = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(-1))
+        r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64).reshape(-1))
+        _check(self._lib.lb_init_drops(self._h, len(r), _dptr(c) if len(r) else None,
+                                       _dptr(r) if len(r) else None, width))
+
+    def init_fields(self, rho: np.ndarray, u: np.ndarray | None = None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        _check(self._lib.lb_init_fields(self._h, _dptr(rho), _dptr(uu)))
+
+    def set_populations(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.q * self.n
+        _check(self._lib.lb_set_populations(self._h, _dptr(f)))
+
+    def get_populations(self) -> np.ndarray:
+        out = np.empty((self.q,) + self.shape, dtype=np.float64)
+        _check(self._lib.lb_get_populations(self._h, _dptr(out)))
+        return out
+
+    def step(self, n: int = 1):
+        _check(self._lib.lb_step(self._h, int(n)))
+
+    def synchronize(self):
+        _check(self._lib.lb_synchronize(self._h))
+
+    def fields(self, want_v: bool = True):
+        rho = np.empty(self.shape, dtype=np.float64)
+        u = np.empty((self.dim,) + self.shape, dtype=np.float64)
+        v = np.empty((self.dim,) + self.shape, dtype=np.float64) if want_v else None
+        _check(self._lib.lb_fields(self._h, _dptr(rho), _dptr(u), _dptr(v)))
+        return rho, u, v
+
+    def fields_into(self, rho: np.ndarray, u: np.ndarray | None = None, v: np.ndarray | None = None):
+        """lb_fields into caller-provided float64 arrays (e.g. pinned host memory)."""
+        for a, k in ((rho, 1), (u, self.dim), (v, self.dim)):
+            assert a is None or (a.dtype == np.float64 and a.size == k * self.n and a.flags["C_CONTIGUOUS"])
+        _check(self._lib.lb_fields(self._h, _dptr(rho), _dptr(u), _dptr(v)))
+
+    def stats(self) -> dict:
+        s = lb_stats()
+        _check(self._lib.lb_stats_get(self._h, C.byref(s)))
+        return {"mass": s.mass, "momentum": list(s.momentum)[: self.dim], "max_u": s.max_u, "max_v": s.max_v,
+                "min_rho": s.min_rho, "max_rho": s.max_rho, "step": s.step, "status": s.status}
+
+    def device_state(self):
+        p, nb = C.c_void_p(), C.c_size_t()
+        _check(self._lib.lb_device_state(self._h, C.byref(p), C.byref(nb)))
+        return p.value, nb.value

@@ -1,0 +1,203 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+float64 storage: element-by-element agreement of every population, to the
+1e-12 relative bound, after up to 1000 steps, on ragged grids that span
+several CTA tiles.  Reduced storage: stated tolerances (see the test bodies).
+"""
+import numpy as np
+import pytest
+
+from oracle import lb_oracle as O
+from paper_0710_5470_gb300 import inputs
+from tests.helpers import drop_populations, library, make_ctx, oracle_model, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
+
+CASES = [
+    ("D2Q9", "equilibrium", (45, 37)),
+    ("D2Q9", "forcing", (45, 37)),
+    ("D3Q19", "equilibrium", (37, 13, 11)),
+    ("D3Q19", "forcing", (37, 13, 11)),
+]
+
+
+@pytest.mark.parametrize("lat,scheme,shape", CASES)
+def test_f64_step_parity_ragged(lat, scheme, shape):
+    """50 steps from a perturbed drop: every f_i within 1e-12 of the oracle."""
+    lb = library()
+    m = oracle_model(lat, scheme)
+    R = 0.3 * min(shape)
+    f0 = drop_populations(m, shape, R, perturb=1e-3, seed=3)
+    with make_ctx(lb, lat, scheme, shape) as ctx:
+        ctx.set_populations(f0)
+        assert np.array_equal(ctx.get_populations(), f0)
+        ctx.step(50)
+        got = ctx.get_populations()
+    want = O.run(f0, m, 50)
+    for i in range(len(f0)):
+        assert rel_inf(got[i], want[i]) < 1e-12, (i, rel_inf(got[i], want[i]))
+
+
+@pytest.mark.parametrize("lat,scheme,shape", [
+    ("D2Q9", "equilibrium", (40, 36)), ("D2Q9", "forcing", (40, 36)),
+    ("D3Q19", "equilibrium", (16, 12, 10)), ("D3Q19", "forcing", (16, 12, 10))])
+def test_f64_parity_1000_steps(lat, scheme, shape):
+    """Spec bound: 1e-12 relative per field after 1000 steps (rho, u
+    relative to max(|u|, 1e-4), every f_i), tau = 1, drop initial state."""
+    lb = library()
+    m = oracle_model(lat, scheme, tau=1.0)
+    f0 = drop_populations(m, shape, 0.3 * min(shape))
+    with make_ctx(lb, lat, scheme, shape, tau=1.0) as ctx:
+        ctx.set_populations(f0)
+        ctx.step(1000)
+        got = ctx.get_populations()
+        rho_g, u_g, v_g = ctx.fields()
+    want = O.run(f0, m, 1000)
+    for i in range(len(f0)):
+        assert rel_inf(got[i], want[i]) < 1e-12
+    rho, u, v = O.observables(want, m)
+    assert rel_inf(rho_g, rho) < 1e-12
+    umax = max(max(np.abs(x).max() for x in u), 1e-4)
+    for a in range(m.dim):
+        assert np.abs(u_g[a] - u[a]).max() / umax < 1e-12
+        assert np.abs(v_g[a] - v[a]).max() / umax < 1e-12
+
+
+@pytest.mark.parametrize("lat,scheme", [("D2Q9", "equilibrium"), ("D2Q9", "forcing"),
+                                        ("D3Q19", "equilibrium"), ("D3Q19", "forcing")])
+def test_init_drops_parity(lat, scheme):
+    """lb_init_drops: tanh drops (two, one wrapping the boundary) then f^eq."""
+    lb = library()
+    m = oracle_model(lat, scheme)
+    shape = (40, 34) if lat == "D2Q9" else (20, 18, 16)
+    if lat == "D2Q9":
+        centres, radii = [(20.0, 17.0), (2.0, 1.5)], [7.0, 5.0]
+    else:
+        centres, radii = [(10.0, 9.0, 8.0), (1.0, 17.0, 0.5)], [4.5, 3.0]
+    with make_ctx(lb, lat, scheme, shape) as ctx:
+        ctx.init_drops(centres, radii, width=2.0)
+        got = ctx.get_populations()
+        rl, rg = ctx.coexistence()
+    nx, ny, nz = (tuple(shape) + (1,))[:3]
+    orl, org = O.coexistence(m.a, m.b, m.T)
+    assert abs(rl - orl) < 1e-12 * orl
+    rho0 = O.drop_density((nz, ny, nx), centres, radii, orl, org, width=2.0)
+    want = O.init_equilibrium(rho0, m)
+    for i in range(len(want)):
+        assert rel_inf(got[i], want[i]) < 1e-13
+
+
+@pytest.mark.parametrize("lat,scheme", [("D2Q9", "forcing"), ("D3Q19", "forcing"), ("D3Q19", "equilibrium")])
+def test_fields_and_stats_parity(lat, scheme):
+    """lb_fields (rho, u, v of Eq. 40) and lb_stats_get against the oracle."""
+    lb = library()
+    m = oracle_model(lat, scheme)
+    shape = (33, 30) if lat == "D2Q9" else (17, 14, 12)
+    f0 = drop_populations(m, shape, 0.3 * min(shape), perturb=1e-4, seed=5)
+    with make_ctx(lb, lat, scheme, shape) as ctx:
+        ctx.set_populations(f0)
+        ctx.step(20)
+        rho_g, u_g, v_g = ctx.fields()
+        st = ctx.stats()
+    f = O.run(f0, m, 20)
+    rho, u, v = O.observables(f, m)
+    d = O.diagnostics(f, m)
+    assert rel_inf(rho_g, rho) < 1e-13
+    for a in range(m.dim):
+        assert np.abs(u_g[a] - u[a]).max() < 1e-13
+        assert np.abs(v_g[a] - v[a]).max() < 1e-13
+    assert abs(st["mass"] - d["mass"]) < 1e-12 * d["mass"]
+    for a in range(m.dim):
+        assert abs(st["momentum"][a] - d["momentum"][a]) < 1e-12 * d["mass"]
+    assert abs(st["max_u"] - d["max_u"]) < 1e-12
+    assert abs(st["max_v"] - d["max_v"]) < 1e-12
+    assert st["step"] == 20 and st["status"] == 0
+
+
+@pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 1)), ("D2Q9", (1, 7)), ("D2Q9", (5, 2)),
+                                       ("D3Q19", (1, 1, 1)), ("D3Q19", (3, 1, 2)), ("D3Q19", (2, 5, 1))])
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_degenerate_tiny_grids(lat, shape, scheme):
+    """Grids narrower than the stencil wrap onto themselves; still exact."""
+    lb = library()
+    m = oracle_model(lat, scheme)
+    nx, ny, nz = (tuple(shape) + (1,))[:3]
+    rng_f = drop_populations(m, shape, 1.0)
+    f0 = rng_f * (1.0 + 1e-2 * inputs.noise(11, rng_f.shape))
+    with make_ctx(lb, lat, scheme, shape) as ctx:
+        ctx.set_populations(f0)
+        ctx.step(7)
+        got = ctx.get_populations()
+    want = O.run(f0, m, 7)
+    assert rel_inf(got, want) < 1e-12
+
+
+def test_zero_steps_and_state_errors():
+    lb = library()
+    with make_ctx(lb, "D2Q9", "forcing", (16, 16)) as ctx:
+        with pytest.raises(lb.LBError) as e:
+            ctx.step(1)                     # step before init
+        assert e.value.status == 6
+        ctx.init_drops([(8.0, 8.0)], [4.0])
+        f = ctx.get_populations()
+        ctx.step(0)
+        assert np.array_equal(ctx.get_populations(), f)
+        with pytest.raises(lb.LBError):
+            ctx.step(-1)
+
+
+def test_nonfinite_density_is_reported_and_sticky():
+    """A NaN planted in the host state raises LB_EUNSTABLE at the next sync,
+    and the context keeps returning it (no GPU fault involved)."""
+    lb = library()
+    m = oracle_model("D2Q9", "equilibrium")
+    f0 = drop_populations(m, (16, 16), 4.0)
+    f0[0, 0, 3, 3] = np.nan
+    with make_ctx(lb, "D2Q9", "equilibrium", (16, 16)) as ctx:
+        ctx.set_populations(f0)
+        ctx.step(2)
+        with pytest.raises(lb.LBError) as e:
+            ctx.synchronize()
+        assert e.value.status == 4
+        with pytest.raises(lb.LBError) as e:
+            ctx.step(1)
+        assert e.value.status == 4
+
+
+# ------------------------------------------------------------ reduced storage
+
+def _reduced_case(lat, scheme, storage, shape, steps):
+    lb = library()
+    m = oracle_model(lat, scheme)
+    f0 = drop_populations(m, shape, 0.3 * min(shape))
+    with make_ctx(lb, lat, scheme, shape, storage=storage) as ctx:
+        ctx.set_populations(f0)
+        start = ctx.get_populations()          # f0 rounded to the storage
+        ctx.step(steps)
+        got = ctx.get_populations()
+        rho_g, u_g, v_g = ctx.fields()
+    want = O.run(start, m, steps)
+    rho, u, v = O.observables(want, m)
+    return got, want, rho_g, rho, v_g, v
+
+
+@pytest.mark.parametrize("lat,scheme,shape", CASES)
+def test_f32_storage_tolerance(lat, scheme, shape):
+    """float32 storage and arithmetic, 100 steps: rho within 1e-5 relative,
+    populations within 2e-5 of max|f|, v within 1e-6 absolute."""
+    got, want, rho_g, rho, v_g, v = _reduced_case(lat, scheme, F32, shape, 100)
+    assert rel_inf(rho_g, rho) < 1e-5
+    assert rel_inf(got, want) < 2e-5
+    assert max(np.abs(v_g[a] - v[a]).max() for a in range(len(v))) < 1e-6
+
+
+@pytest.mark.parametrize("storage,tol_rho,tol_v", [(F16DEV, 1e-4, 2e-5), (BF16DEV, 1e-3, 2e-4)])
+@pytest.mark.parametrize("lat,scheme,shape", CASES)
+def test_deviation_storage_tolerance(lat, scheme, shape, storage, tol_rho, tol_v):
+    """fp16 / bf16 deviation storage (f_0 float32), 100 steps from the rounded
+    start: rho within tol_rho relative, v within tol_v absolute."""
+    got, want, rho_g, rho, v_g, v = _reduced_case(lat, scheme, storage, shape, 100)
+    assert rel_inf(rho_g, rho) < tol_rho
+    assert max(np.abs(v_g[a] - v[a]).max() for a in range(len(v))) < tol_v

@@ -1,0 +1,61 @@
+"""The C ABI library loads and exports every symbol include/lb.h declares;
+host-only calls work without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from tests.helpers import A_VDW, B_VDW, library
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    lb = library()
+    lib = ctypes.CDLL(lb.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_coexistence_host_call_matches_oracle():
+    from oracle import lb_oracle as O
+    lb = library()
+    for T in (0.30, 0.45, 0.50, 0.55, 0.56):
+        rl, rg = lb.coexistence(A_VDW, B_VDW, T)
+        orl, org = O.coexistence(A_VDW, B_VDW, T)
+        assert abs(rl - orl) < 1e-12 * orl and abs(rg - org) < 1e-11 * org
+
+
+def test_invalid_parameters_rejected_before_device_work():
+    lb = library()
+    bad = [dict(tau=0.5), dict(tau=0.3), dict(T=0.6), dict(kappa=0.0), dict(shape=(0, 4))]
+    for b in bad:
+        kw = dict(shape=(8, 8), a=A_VDW, b=B_VDW, T=0.55, kappa=0.01, tau=0.8)
+        kw.update(b)
+        with pytest.raises(lb.LBError) as e:
+            lb.Context(0, kw["shape"], kw["a"], kw["b"], kw["T"], kw["kappa"], kw["tau"])
+        assert e.value.status == 1
+    with pytest.raises(lb.LBError):
+        lb.Context(0, (8, 8, 2), A_VDW, B_VDW, 0.55, 0.01, 0.8)   # D2Q9 needs nz = 1
+    with pytest.raises(lb.LBError):
+        lb.coexistence(A_VDW, B_VDW, 8 * A_VDW / (27 * B_VDW))
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_0710_5470_gb300 import lb
+    saved = lb._lib
+    lb._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            lb.load_library(str(tmp_path / "nope.so"))
+    finally:
+        lb._lib = saved
