@@ -93,9 +93,8 @@ __global__ void init_feq_kernel(const double* rho, const double* u, PopPtrs dst,
                 j[c] = r * uu[c];
             }
         }
-        const double g0[3] = {0.0, 0.0, 0.0};
-        double feq[L::Q], F[L::Q];
-        equilibrium<L, FORCING, double>(r, j, uu, G, lap, g0, ph.a, ph.b, ph.T, ph.kappa, ph.nu, feq, F);
+        double feq[L::Q];
+        equilibrium<L, FORCING, double>(r, j, uu, G, lap, ph.a, ph.b, ph.T, ph.kappa, ph.nu, feq);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
             S::store(i, dst.p[i], idx, typename S::real(feq[i]), dst.fref[i]);

@@ -2,23 +2,43 @@
 // combination; included by one translation unit per lattice.
 #pragma once
 #include "dispatch.h"
+#include "step3d.cuh"
 
 namespace lbk {
+
+// Fused step kernel of a lattice: the z-split kernel for D3Q19, the generic
+// single-plane kernel for D2Q9.
+template <class L, bool FORCING, class S, int TX, int TY>
+struct StepKernelOf {
+    using real = typename S::real;
+    static constexpr bool D3 = L::D == 3;
+    static constexpr size_t bytes() {
+        if constexpr (D3) return Layout3D<FORCING, TX, TY, real>::BYTES;
+        else return StepLayout<L, FORCING, TX, TY, real>::BYTES;
+    }
+    static const void* fn() {
+        if constexpr (D3) return reinterpret_cast<const void*>(step_kernel3d<FORCING, S, TX, TY>);
+        else return reinterpret_cast<const void*>(step_kernel<L, FORCING, S, TX, TY>);
+    }
+    static void launch(dim3 grid, cudaStream_t st, const StepArgs& a) {
+        if constexpr (D3) step_kernel3d<FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(a);
+        else step_kernel<L, FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(a);
+    }
+};
 
 template <class L, bool FORCING, class S, int TX, int TY>
 struct Launchers {
     using real = typename S::real;
-    using Lay = StepLayout<L, FORCING, TX, TY, real>;
+    using K = StepKernelOf<L, FORCING, S, TX, TY>;
 
     static cudaError_t step(const StepArgs& a, dim3 grid, cudaStream_t st) {
         static int attr_done = 0;
         if (!attr_done) {
-            cudaError_t e = cudaFuncSetAttribute(step_kernel<L, FORCING, S, TX, TY>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(Lay::BYTES));
+            cudaError_t e = cudaFuncSetAttribute(K::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::bytes()));
             if (e != cudaSuccess) return e;
             attr_done = 1;
         }
-        step_kernel<L, FORCING, S, TX, TY><<<grid, TX * TY, Lay::BYTES, st>>>(a);
+        K::launch(grid, st, a);
         return cudaGetLastError();
     }
     static cudaError_t init_feq(const double* rho, const double* u, const PopPtrs& p, Grid3 g, Phys ph,
@@ -55,8 +75,8 @@ struct Launchers {
         LbKernelSet k;
         k.tx = TX;
         k.ty = TY;
-        k.smem = Lay::BYTES;
-        k.step_fn = reinterpret_cast<const void*>(step_kernel<L, FORCING, S, TX, TY>);
+        k.smem = K::bytes();
+        k.step_fn = K::fn();
         k.step = &step;
         k.init_feq = &init_feq;
         k.moments = &moments;

@@ -21,8 +21,20 @@
 // Eq. 29 with A = 1/6, B = 1/12, C = 1/3, D = 1/6 (3D), so the kernels use
 // that form for both.
 #pragma once
+#include <type_traits>
 
 namespace lbk {
+
+// Compile-time loop: calls f(std::integral_constant<int, k>) for k in [B, E),
+// so that velocity components and weights are constant expressions inside f.
+template <int B, int E, class F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
 
 struct D2Q9 {
     static constexpr int D = 2;

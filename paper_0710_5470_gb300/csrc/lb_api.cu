@@ -102,6 +102,7 @@ struct lb_ctx {
     int cur = 0;
     double rho_l = 0, rho_g = 0;
     float fref[lbk::MAXQ] = {};
+    float pref = 0.0f, rsum = 0.0f;
     cudaStream_t stream = nullptr;
     unsigned* d_status = nullptr;
     LbKernelSet ks;
@@ -262,10 +263,14 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     const double pref = p0_vdw(rref, p->a, p->b, p->T);
     for (int i = 0; i < lbk::MAXQ; ++i) c->fref[i] = 0.0f;
     if (p->storage == LB_F16DEV || p->storage == LB_BF16DEV) {
+        double wsum = 0.0;
         for (int i = 1; i < c->Q; ++i) {
             const double w = c->D == 2 ? lbk::w_vel<lbk::D2Q9>(i) : lbk::w_vel<lbk::D3Q19>(i);
             c->fref[i] = float(w * pref);
+            wsum += w;
         }
+        c->pref = float(pref);
+        c->rsum = float(pref * wsum);
     }
     const int elem0 = p->storage == LB_F64 ? 8 : 4;
     const int elemi = p->storage == LB_F64 ? 8 : (p->storage == LB_F32 ? 4 : 2);
@@ -445,6 +450,8 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
     a.nu = (c->p.tau - 0.5) / 3.0;
     a.status = c->d_status;
     for (int i = 0; i < lbk::MAXQ; ++i) a.fref[i] = c->fref[i];
+    a.pref = c->pref;
+    a.rsum = c->rsum;
     for (int k = 0; k < nsteps; ++k) {
         for (int i = 0; i < c->Q; ++i) {
             a.src[i] = c->fbuf + pop_offset(c, i, c->cur);

@@ -1,0 +1,340 @@
+// Fused D3Q19 time step with the z-split stencils.
+//
+// Same plane pipeline as the generic kernel (step_kernel.cuh): a CTA owns a
+// TX x TY column of the lattice and marches through a chunk of z planes.  The
+// 3D stencils are split by the z component of the velocity: with the D3Q19
+// weights (1/6 on axes, 1/12 on diagonals) every stencil over the 18
+// neighbours of r is the sum of an in-plane part (e_z = 0) and one part from
+// each adjacent plane (e_z = +-1).  A plane's parts are computed once, from 9
+// values of that plane, and carried in registers along the march:
+//
+//   grad rho (Eq. 29, A = 1/6, B = 1/12), on a plane q' with
+//     Dx = rho(x+1) - rho(x-1), Dy = rho(y+1) - rho(y-1),
+//     S  = rho/6 + (rho(x+-1) + rho(y+-1))/12:
+//       d_x rho(q) = Dx(q)/6 + Ex(q)/12 + (Dx(q+1) + Dx(q-1))/12   (Ex: xy diagonals)
+//       d_z rho(q) = S(q+1) - S(q-1)
+//   lap rho (C = 1/3, D = 1/6) = 2 sum_i w_i rho(r + e_i) - 4 rho(r), with the
+//     same split of sum_i w_i rho(r + e_i).
+//   g = -div M' (Eq. 28, forcing scheme, reading for 3D: M'_ab = M_ab - delta_ab M_cc/2)
+//     = -(U+(q+1) + U0(q) + U-(q-1)), U+/0/- the contributions of one plane's
+//     M' e_i to the plane above / itself / below (43 values per site).
+#pragma once
+#include "step_kernel.cuh"
+
+namespace lbk {
+
+template <bool FORCING, int TX, int TY, class real>
+struct Layout3D {
+    static constexpr int Q = 19;
+    static constexpr int H = FORCING ? 2 : 1;
+    static constexpr int RX = TX + 2 * H, RY = TY + 2 * H, RN = RX * RY;
+    static constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY;
+    static constexpr int NT = TX * TY;
+    static constexpr int NA = (RN + NT - 1) / NT;
+    static constexpr int NB = FORCING ? (SN + NT - 1) / NT : 1;
+    static constexpr int NRHO = 3;
+    static constexpr int NSTASH = FORCING ? 3 : 2;
+    static constexpr int LAG_C = FORCING ? 2 : 1;
+    static constexpr int OFF_RHO = 0;
+    static constexpr int OFF_STASH = OFF_RHO + NRHO * RN;
+    static constexpr int OFF_MP = OFF_STASH + NSTASH * Q * NT;
+    static constexpr int OFF_G = OFF_MP + (FORCING ? 6 * SN : 0);
+    static constexpr int TOTAL = OFF_G + (FORCING ? 2 * 4 * NT : 0);
+    static constexpr size_t BYTES = size_t(TOTAL) * sizeof(real);
+};
+
+// Per-plane parts of the gradient / Laplacian stencil at one site.
+template <class real>
+struct PlaneParts {
+    real dx, dy, s;          // Dx, Dy, S of the plane (used by the planes above and below)
+    real gx, gy, lin, c;     // in-plane parts of d_x, d_y, sum w rho, and rho itself
+};
+
+template <class real>
+__device__ __forceinline__ PlaneParts<real> plane_parts(const real* rho, int rc, int RX) {
+    const real c = rho[rc];
+    const real xp = rho[rc + 1], xm = rho[rc - 1], yp = rho[rc + RX], ym = rho[rc - RX];
+    const real pp = rho[rc + RX + 1], pm = rho[rc - RX + 1], mp = rho[rc + RX - 1], mm = rho[rc - RX - 1];
+    const real sixth = real(1) / real(6), twelfth = real(1) / real(12);
+    PlaneParts<real> o;
+    o.dx = xp - xm;
+    o.dy = yp - ym;
+    const real f = (xp + xm) + (yp + ym);
+    o.s = sixth * c + twelfth * f;
+    o.gx = sixth * o.dx + twelfth * ((pp + pm) - (mp + mm));
+    o.gy = sixth * o.dy + twelfth * ((pp + mp) - (pm + mm));
+    o.lin = sixth * f + twelfth * ((pp + pm) + (mp + mm));
+    o.c = c;
+    return o;
+}
+
+// Gradient and Laplacian of plane q from the parts of planes q-1 (lo), q (mid), q+1 (hi).
+template <class real>
+__device__ __forceinline__ void assemble(const PlaneParts<real>& lo, const PlaneParts<real>& mid,
+                                         const PlaneParts<real>& hi, real (&G)[3], real& lap) {
+    const real twelfth = real(1) / real(12);
+    G[0] = mid.gx + twelfth * (hi.dx + lo.dx);
+    G[1] = mid.gy + twelfth * (hi.dy + lo.dy);
+    G[2] = hi.s - lo.s;
+    lap = real(2) * (mid.lin + hi.s + lo.s) - real(4) * mid.c;
+}
+
+template <bool FORCING, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, sizeof(typename S::real) == 4 ? 2 : 1) step_kernel3d(const StepArgs args) {
+    using L = D3Q19;
+    using real = typename S::real;
+    using Lay = Layout3D<FORCING, TX, TY, real>;
+    constexpr int Q = 19, H = Lay::H, NT = Lay::NT;
+    constexpr int RX = Lay::RX, RN = Lay::RN, SX = Lay::SX, SN = Lay::SN;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* sm = reinterpret_cast<real*>(smem_raw);
+    real* rho_s = sm + Lay::OFF_RHO;
+    real* stash = sm + Lay::OFF_STASH;
+    real* mp_s = sm + Lay::OFF_MP;     // M' of one plane on the tile + 1 ring: [comp][SN]
+    real* gl_s = sm + Lay::OFF_G;      // G, lap of the tile for two planes: [slot][4][NT]
+
+    const int nx = args.nx, ny = args.ny, nz = args.nz;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * args.lz;
+    const int z1 = min(z0 + args.lz, nz);
+    const int plane = nx * ny;
+
+    const real pa = real(args.a), pb = real(args.b), pT = real(args.T), pk = real(args.kappa);
+    const real om = real(args.omega), nu = real(args.nu);
+    const real pref = real(args.pref), rsum = real(args.rsum);
+
+    int a_in[Lay::NA], a_st[Lay::NA];
+#pragma unroll
+    for (int m = 0; m < Lay::NA; ++m) {
+        const int k = tid + m * NT;
+        a_in[m] = -1;
+        a_st[m] = -1;
+        if (k < RN) {
+            const int rx = k % RX, ry = k / RX;
+            a_in[m] = wrapi(y0 - H + ry, ny) * nx + wrapi(x0 - H + rx, nx);
+            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY) a_st[m] = (ry - H) * TX + (rx - H);
+        }
+    }
+    // stage-B items: the tile + 1 ring (forcing) or the thread's own site
+    int b_rc[Lay::NB], b_k[Lay::NB], b_r0[Lay::NB];
+#pragma unroll
+    for (int m = 0; m < Lay::NB; ++m) {
+        if (FORCING) {
+            const int k = tid + m * NT;
+            const int sx = k % SX, sy = k / SX;
+            b_k[m] = k < SN ? k : -1;
+            b_rc[m] = (sy + H - 1) * RX + (sx + H - 1);
+            b_r0[m] = (k < SN && sx >= 1 && sx <= TX && sy >= 1 && sy <= TY) ? (sy - 1) * TX + (sx - 1) : -1;
+        } else {
+            b_k[m] = tid;
+            b_rc[m] = (ty + H) * RX + (tx + H);
+            b_r0[m] = tid;
+        }
+    }
+    const int xs = x0 + tx, ys = y0 + ty;
+    const bool own = xs < nx && ys < ny;
+    const int xw[3] = {wrapi(xs - 1, nx), wrapi(xs, nx), wrapi(xs + 1, nx)};
+    const int yr[3] = {wrapi(ys - 1, ny) * nx, wrapi(ys, ny) * nx, wrapi(ys + 1, ny) * nx};
+
+    const int pstart = z0 - Lay::LAG_C;
+    const int pend = z1 + Lay::LAG_C;
+
+    typename S::raw0 r0[Lay::NA];
+    typename S::rawi ri[Lay::NA][Q - 1];
+    auto issue = [&](int p) {
+        const int poff = wrapi(p, nz) * plane;
+#pragma unroll
+        for (int m = 0; m < Lay::NA; ++m) {
+            if (a_in[m] >= 0) {
+                const size_t q = size_t(poff + a_in[m]);
+                r0[m] = S::ld0(args.src[0], q);
+                static_for<1, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    ri[m][i - 1] = S::ldi(args.src[i], q);
+                });
+            }
+        }
+    };
+    constexpr bool PREFETCH = sizeof(real) == 4;
+    if (PREFETCH) issue(pstart);
+
+    // carried stencil parts of the stage-B items: planes p-2 (lo) and p-1 (mid)
+    PlaneParts<real> pl_lo[Lay::NB], pl_mid[Lay::NB];
+    // carried body-force parts of the tile site: U0(q-1), U-(q-1), U-(q-2)
+    real u0_1[3] = {0, 0, 0}, um_1[3] = {0, 0, 0}, um_2[3] = {0, 0, 0};
+    // equilibrium scheme: G, lap of plane p-1 assembled in stage B
+    real Geq[3] = {0, 0, 0}, lapeq = 0;
+
+    for (int p = pstart; p < pend; ++p) {
+        const int it = p - pstart;
+        // ---------------- stage A: density of plane p on the halo region
+        {
+            if (!PREFETCH) issue(p);
+            real* rho_w = rho_s + (it % Lay::NRHO) * RN;
+            real* st_w = stash + (it % Lay::NSTASH) * Q * NT;
+            const bool keep = p >= z0 && p < z1;
+#pragma unroll
+            for (int m = 0; m < Lay::NA; ++m) {
+                if (a_in[m] >= 0) {
+                    real f[Q];               // f_0 and the deviations d_i
+                    f[0] = S::dec0(r0[m]);
+                    static_for<1, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        f[i] = S::devi(ri[m][i - 1]);
+                    });
+                    real r = rsum;
+                    static_for<1, Q>([&](auto I) { r += f[decltype(I)::value]; });
+                    r += f[0];
+                    rho_w[tid + m * NT] = r;
+                    if (keep && a_st[m] >= 0) {
+                        static_for<0, Q>([&](auto I) {
+                            constexpr int i = decltype(I)::value;
+                            st_w[i * NT + a_st[m]] = f[i];
+                        });
+                    }
+                }
+            }
+            if (PREFETCH && p + 1 < pend) issue(p + 1);
+        }
+        __syncthreads();
+
+        // ---------------- stage B: stencil parts of plane p; G, lap (and M') of plane q = p-1
+        const int q = p - 1;
+        const bool assemble_q = q >= z0 - (FORCING ? 1 : 0) && it >= 2;
+        {
+            const real* rho_p = rho_s + (it % Lay::NRHO) * RN;
+#pragma unroll
+            for (int m = 0; m < Lay::NB; ++m) {
+                if (b_k[m] < 0) continue;
+                const PlaneParts<real> cur = plane_parts(rho_p, b_rc[m], RX);
+                if (assemble_q) {
+                    real G[3], lap;
+                    assemble(pl_lo[m], pl_mid[m], cur, G, lap);
+                    if constexpr (FORCING) {
+                        const real g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+                        const real hk = real(0.5) * pk * g2;
+                        const int k = b_k[m];
+                        mp_s[0 * SN + k] = pk * G[0] * G[0] - hk;
+                        mp_s[1 * SN + k] = pk * G[1] * G[1] - hk;
+                        mp_s[2 * SN + k] = pk * G[2] * G[2] - hk;
+                        mp_s[3 * SN + k] = pk * G[0] * G[1];
+                        mp_s[4 * SN + k] = pk * G[1] * G[2];
+                        mp_s[5 * SN + k] = pk * G[0] * G[2];
+                        if (b_r0[m] >= 0) {
+                            real* gl = gl_s + ((q - pstart) & 1) * 4 * NT;
+                            gl[0 * NT + b_r0[m]] = G[0];
+                            gl[1 * NT + b_r0[m]] = G[1];
+                            gl[2 * NT + b_r0[m]] = G[2];
+                            gl[3 * NT + b_r0[m]] = lap;
+                        }
+                    } else {
+                        Geq[0] = G[0];
+                        Geq[1] = G[1];
+                        Geq[2] = G[2];
+                        lapeq = lap;
+                    }
+                }
+                pl_lo[m] = pl_mid[m];
+                pl_mid[m] = cur;
+            }
+        }
+        if constexpr (FORCING) __syncthreads();
+
+        // ---------------- body-force parts of plane q (forcing)
+        real gf[3] = {0, 0, 0};
+        if constexpr (FORCING) {
+            if (assemble_q) {
+                const int kc = (ty + 1) * SX + (tx + 1);
+                const real* Mxx = mp_s;
+                const real* Myy = mp_s + SN;
+                const real* Mzz = mp_s + 2 * SN;
+                const real* Mxy = mp_s + 3 * SN;
+                const real* Myz = mp_s + 4 * SN;
+                const real* Mxz = mp_s + 5 * SN;
+                real sp[3] = {0, 0, 0}, sz[3] = {0, 0, 0}, se[3] = {0, 0, 0};
+#pragma unroll
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    const int kx = kc + sgn, ky = kc + sgn * SX;
+                    const real s = real(sgn);
+                    // x faces: s (Mxx, Mxy, Mxz); z parts (Mxz, Myz, Mzz)
+                    const real axx = Mxx[kx], axy = Mxy[kx], axz = Mxz[kx], ayz = Myz[kx], azz = Mzz[kx];
+                    sp[0] += s * axx; sp[1] += s * axy; sp[2] += s * axz;
+                    sz[0] += axz; sz[1] += ayz; sz[2] += azz;
+                    // y faces: s (Mxy, Myy, Myz)
+                    const real bxy = Mxy[ky], byy = Myy[ky], byz = Myz[ky], bxz = Mxz[ky], bzz = Mzz[ky];
+                    sp[0] += s * bxy; sp[1] += s * byy; sp[2] += s * byz;
+                    sz[0] += bxz; sz[1] += byz; sz[2] += bzz;
+                    // xy diagonals (sx = sgn, sy = +-1)
+#pragma unroll
+                    for (int sgy = -1; sgy <= 1; sgy += 2) {
+                        const int ke = kc + sgn + sgy * SX;
+                        const real ty_ = real(sgy);
+                        const real exx = Mxx[ke], exy = Mxy[ke], eyy = Myy[ke], exz = Mxz[ke], eyz = Myz[ke];
+                        se[0] += s * exx + ty_ * exy;
+                        se[1] += s * exy + ty_ * eyy;
+                        se[2] += s * exz + ty_ * eyz;
+                    }
+                }
+                const real zc[3] = {Mxz[kc], Myz[kc], Mzz[kc]};
+                const real sixth = real(1) / real(6), twelfth = real(1) / real(12);
+                real up[3], u0[3], um[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    u0[c] = sixth * sp[c] + twelfth * se[c];
+                    up[c] = twelfth * (sp[c] + sz[c]) + sixth * zc[c];
+                    um[c] = twelfth * (sp[c] - sz[c]) - sixth * zc[c];
+                }
+                // g(q-1) = -(U+(q) + U0(q-1) + U-(q-2))   (Eq. 28)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    gf[c] = -(up[c] + u0_1[c] + um_2[c]);
+                    um_2[c] = um_1[c];
+                    um_1[c] = um[c];
+                    u0_1[c] = u0[c];
+                }
+            }
+        }
+
+        // ---------------- stage C: collide and push plane s
+        const int s = p - Lay::LAG_C;
+        if (s >= z0 && own) {
+            const int is = s - pstart;
+            const real* st_r = stash + (is % Lay::NSTASH) * Q * NT;
+            real f[Q];
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                f[i] = st_r[i * NT + tid];
+            });
+            const real rho = rho_s[(is % Lay::NRHO) * RN + (ty + H) * RX + (tx + H)];
+            real G[3], lap;
+            if constexpr (FORCING) {
+                const real* gl = gl_s + ((s - pstart) & 1) * 4 * NT;
+                G[0] = gl[tid];
+                G[1] = gl[NT + tid];
+                G[2] = gl[2 * NT + tid];
+                lap = gl[3 * NT + tid];
+            } else {
+                G[0] = Geq[0];
+                G[1] = Geq[1];
+                G[2] = Geq[2];
+                lap = lapeq;
+            }
+            if (!(rho > real(0)) || !(rho < real(1e30))) atomicOr(args.status, 1u);
+            real out[Q];
+            collide<L, FORCING, real>(f, rho, G, lap, gf, pa, pb, pT, pk, om, nu, pref, rsum, out);
+            const int zr[3] = {wrapi(s - 1, nz) * plane, wrapi(s, nz) * plane, wrapi(s + 1, nz) * plane};
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const int idx = zr[1 + L::ez(i)] + yr[1 + L::ey(i)] + xw[1 + L::ex(i)];
+                if constexpr (i == 0) S::st0(args.dst[0], size_t(idx), out[0]);
+                else S::sti(args.dst[i], size_t(idx), out[i]);
+            });
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace lbk

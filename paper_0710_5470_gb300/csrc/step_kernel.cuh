@@ -20,7 +20,9 @@
 // HBM traffic is one read and one write of every population per step; the
 // density halo is recomputed from populations that neighbouring CTAs read at
 // the same time (served by L2).  2D lattices use the same code with a single
-// plane and no lag between the stages.
+// plane and no lag between the stages.  Every loop over velocities is
+// expanded at compile time (static_for), so velocity components and weights
+// are literals in the generated code.
 #pragma once
 #include "lattice.cuh"
 #include "storage.cuh"
@@ -33,6 +35,7 @@ struct StepArgs {
     const char* src[MAXQ];
     char* dst[MAXQ];
     float fref[MAXQ];
+    float pref, rsum;  // deviation storage: fref_i = w_i pref, rsum = pref sum_{i>=1} w_i
     int nx, ny, nz;
     int lz;  // z planes per CTA (3D)
     double a, b, T, kappa, omega, nu;
@@ -76,27 +79,41 @@ __host__ __device__ constexpr int mcomp(int a, int b) {
     return a == b ? a : (D == 2 ? 2 : ((a + b == 1) ? 3 : ((a + b == 3) ? 4 : 5)));
 }
 
-// Tuned equilibrium (Eqs. 5, 6) and force populations (Eq. 27) of one site,
-// from its density rho, momentum j = rho u, velocity u, gradient G and
-// Laplacian lap of rho, and (forcing scheme) body force g.  feq[0] and F[0]
-// close the sums: sum_i feq_i = rho, sum_i F_i = 0.
+template <int E, class real>
+__device__ __forceinline__ void add_signed(real& acc, real v) {
+    if constexpr (E == 1) acc += v;
+    if constexpr (E == -1) acc -= v;
+}
+
+// Momentum j = sum_i f_i e_i (Eq. 3).
+template <class L, class real>
+__device__ __forceinline__ void momentum(const real (&f)[L::Q], real (&j)[3]) {
+    j[0] = j[1] = j[2] = real(0);
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        add_signed<L::ex(i)>(j[0], f[i]);
+        add_signed<L::ey(i)>(j[1], f[i]);
+        if constexpr (L::D == 3) add_signed<L::ez(i)>(j[2], f[i]);
+    });
+}
+
+// Tuned equilibrium (Eqs. 5, 6) of one site from rho, j = rho u, u, the
+// gradient G and Laplacian lap of rho.  The M_ab = kappa d_a rho d_b rho terms
+// are included in the equilibrium scheme only (Sec. VI).  feq[0] closes the
+// sum: sum_i feq_i = rho.  Used to initialise populations.
 template <class L, bool FORCING, class real>
 __device__ __forceinline__ void equilibrium(real rho, const real (&j)[3], const real (&u)[3],
-                                            const real (&G)[3], real lap, const real (&g)[3],
-                                            real a, real b, real T, real kappa, real nu,
-                                            real (&feq)[L::Q], real (&F)[L::Q]) {
-    constexpr int Q = L::Q, D = L::D;
+                                            const real (&G)[3], real lap, real a, real b, real T,
+                                            real kappa, real nu, real (&feq)[L::Q]) {
+    constexpr int D = L::D;
     const real ib = real(1) / (real(1) - b * rho);
     const real p0 = rho * T * ib - a * rho * rho;            // Eq. 2
     const real cs2 = T * ib * ib - real(2) * a * rho;        // dp0/drho
     const real lam = nu * (real(1) - real(3) * cs2);         // Eq. 36
     real udg = real(0);
-#pragma unroll
     for (int c = 0; c < D; ++c) udg += u[c] * G[c];
     real Qt[3][3];
-#pragma unroll
     for (int c = 0; c < D; ++c)
-#pragma unroll
         for (int d = c; d < D; ++d) {
             real v = rho * u[c] * u[d] + lam * (u[c] * G[d] + u[d] * G[c]);
             if (c == d) v += lam * udg;
@@ -104,97 +121,152 @@ __device__ __forceinline__ void equilibrium(real rho, const real (&j)[3], const 
             Qt[d][c] = v;
         }
     real trQ = real(0);
-#pragma unroll
     for (int c = 0; c < D; ++c) trQ += Qt[c][c];
-    // w_i (e.j + 3/2 (e e - 1/3) : Q) + w_i (p0 - kappa rho lap), with w^p = w^t = w
     const real A0 = (p0 - kappa * rho * lap) - real(0.5) * trQ;
-    real M[3][3];
-    if (!FORCING) {
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-#pragma unroll
-            for (int d = c; d < D; ++d) M[c][d] = kappa * G[c] * G[d];
-    }
-    real ug = real(0);
-    if (FORCING) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) ug += u[c] * g[c];
-    }
-    real sum_eq = real(0), sum_F = real(0);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        real ej = real(0), eqe = real(0);
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const int ec = e_comp<L>(i, c);
-            if (ec == 1) ej += j[c];
-            if (ec == -1) ej -= j[c];
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int ed = e_comp<L>(i, d);
-                if (ec * ed == 1) eqe += Qt[c][d];
-                if (ec * ed == -1) eqe -= Qt[c][d];
-            }
-        }
-        const real wi = real(w_vel<L>(i));
-        real fe = wi * (ej + real(1.5) * eqe + A0);
-        if (!FORCING) {
-#pragma unroll
-            for (int c = 0; c < D; ++c)
-#pragma unroll
-                for (int d = c; d < D; ++d) {
-                    const double wm = w_m<L>(i, c, d);
-                    if (wm != 0.0) fe += real(wm) * M[c][d];
-                }
+    real sum = real(0);
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        real s = A0;
+        real qe = real(0);
+        static_for<0, D>([&](auto C) {
+            constexpr int c = decltype(C)::value;
+            add_signed<e_comp<L>(i, c)>(s, j[c]);
+            static_for<0, D>([&](auto Dd) {
+                constexpr int d = decltype(Dd)::value;
+                add_signed<e_comp<L>(i, c) * e_comp<L>(i, d)>(qe, Qt[c][d]);
+            });
+        });
+        real fe = real(w_vel<L>(i)) * (s + real(1.5) * qe);
+        if constexpr (!FORCING) {
+            static_for<0, D>([&](auto C) {
+                constexpr int c = decltype(C)::value;
+                static_for<c, D>([&](auto Dd) {
+                    constexpr int d = decltype(Dd)::value;
+                    constexpr double wm = w_m<L>(i, c, d);
+                    if constexpr (wm != 0.0) fe += real(wm) * kappa * G[c] * G[d];
+                });
+            });
         }
         feq[i] = fe;
-        sum_eq += fe;
-        real Fi = real(0);
-        if (FORCING) {
-            real eg = real(0), eu = real(0);
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const int ec = e_comp<L>(i, c);
-                if (ec == 1) { eg += g[c]; eu += u[c]; }
-                if (ec == -1) { eg -= g[c]; eu -= u[c]; }
-            }
-            Fi = wi * (eg + real(3) * eu * eg - ug);          // Eq. 27
-            sum_F += Fi;
-        }
-        F[i] = Fi;
-    }
-    feq[0] = rho - sum_eq;                                    // Eq. 6
-    F[0] = -sum_F;                                            // sum_i F_i = 0
+        sum += fe;
+    });
+    feq[0] = rho - sum;                                       // Eq. 6
 }
 
-// Momentum j = sum_i f_i e_i (Eq. 3).
-template <class L, class real>
-__device__ __forceinline__ void momentum(const real (&f)[L::Q], real (&j)[3]) {
-    j[0] = j[1] = j[2] = real(0);
-#pragma unroll
-    for (int i = 1; i < L::Q; ++i) {
-#pragma unroll
-        for (int c = 0; c < L::D; ++c) {
-            if (e_comp<L>(i, c) == 1) j[c] += f[i];
-            if (e_comp<L>(i, c) == -1) j[c] -= f[i];
-        }
-    }
+template <class real>
+__device__ __forceinline__ real fast_rcp(real x) {
+    if constexpr (sizeof(real) == 4) return __fdividef(1.0f, x);
+    else return real(1) / x;
 }
 
-// BGK collision with force (Eq. 4): f*_i = f_i + omega (f^eq_i - f_i) + F_i.
+// BGK collision with force, Eq. 4: f*_i = (1 - omega) f_i + omega f^eq_i + F_i,
+// with f^eq of Eqs. 5, 6 and, for the forcing scheme, F_i of Eq. 27 and
+// F_0 = -sum F_i.  Written as one quadratic form in e_i per site:
+//   omega f^eq_i + F_i = w_i [e.(omega j + g) + e.T.e + omega A0 - u.g] (+ omega M-part)
+//   T_cd = 3/2 (omega Q_cd + u_c g_d + u_d g_c),  A0 = p0 - kappa rho lap - trQ/2,
+//   Q_cd = rho u_c u_d + lambda (u_c G_d + u_d G_c + delta_cd u.G).
+// Populations i >= 1 are deviations d_i = f_i - w_i pref from the rest state
+// w_i pref (pref = 0 stores f_i itself); since sum_i w_i e_i = 0 the momentum
+// is sum_i d_i e_i, and the collided deviation is (1 - omega) d_i + v_i with
+// v_i = w_i [... - omega pref].  rsum = pref sum_{i>=1} w_i.  Opposite
+// velocities i, -i share the even part of v and differ in the sign of e.J.
 template <class L, bool FORCING, class real>
 __device__ __forceinline__ void collide(const real (&f)[L::Q], real rho, const real (&G)[3], real lap,
                                         const real (&g)[3], real a, real b, real T, real kappa,
-                                        real omega, real nu, real (&out)[L::Q]) {
-    constexpr int Q = L::Q, D = L::D;
-    real j[3];
-    momentum<L, real>(f, j);
-    const real irho = real(1) / rho;
+                                        real omega, real nu, real pref, real rsum, real (&out)[L::Q]) {
+    constexpr int D = L::D;
+    real j[3] = {real(0), real(0), real(0)};
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int o = opposite<L>(i);
+        if constexpr (i < o) {
+            const real df = f[i] - f[o];
+            add_signed<L::ex(i)>(j[0], df);
+            add_signed<L::ey(i)>(j[1], df);
+            if constexpr (D == 3) add_signed<L::ez(i)>(j[2], df);
+        }
+    });
+    const real irho = fast_rcp(rho);
     real u[3] = {j[0] * irho, j[1] * irho, D == 3 ? j[2] * irho : real(0)};
-    real feq[Q], F[Q];
-    equilibrium<L, FORCING, real>(rho, j, u, G, lap, g, a, b, T, kappa, nu, feq, F);
+    const real ib = fast_rcp(real(1) - b * rho);
+    const real p0 = rho * T * ib - a * rho * rho;            // Eq. 2
+    const real cs2 = T * ib * ib - real(2) * a * rho;        // dp0/drho
+    const real lam = nu * (real(1) - real(3) * cs2);         // Eq. 36
+    real lu[3], udg = real(0), ug = real(0), g3[3];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[i] = f[i] + omega * (feq[i] - f[i]) + F[i];
+    for (int c = 0; c < 3; ++c) {
+        lu[c] = lam * u[c];
+        g3[c] = FORCING ? real(3) * g[c] : real(0);
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        udg += u[c] * G[c];
+        if (FORCING) ug += u[c] * g[c];
+    }
+    const real w15 = real(1.5) * omega, w3 = real(3) * omega;
+    real Tq[3][3];          // T_cd (diagonal) and 2 T_cd (off-diagonal)
+    real trQ = real(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int d = c; d < D; ++d) {
+            if (c == d) {
+                const real q = j[c] * u[c] + real(2) * lu[c] * G[c] + lam * udg;
+                trQ += q;
+                Tq[c][c] = w15 * q + (FORCING ? u[c] * g3[c] : real(0));
+            } else {
+                const real q = j[c] * u[d] + lu[c] * G[d] + lu[d] * G[c];
+                Tq[c][d] = w3 * q + (FORCING ? u[c] * g3[d] + u[d] * g3[c] : real(0));
+            }
+        }
+    const real A0 = (p0 - kappa * rho * lap) - real(0.5) * trQ;
+    const real Aw = omega * (A0 - pref) - ug;
+    real Jw[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Jw[c] = omega * j[c] + (FORCING ? g[c] : real(0));
+    real Mw[3][3];
+    if constexpr (!FORCING) {
+        const real ok = omega * kappa;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int d = c; d < D; ++d) Mw[c][d] = ok * G[c] * G[d];
+    }
+    const real omw = real(1) - omega;
+    real sum = real(0);
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int o = opposite<L>(i);
+        if constexpr (i < o) {
+            real even = Aw, odd = real(0);
+            static_for<0, D>([&](auto C) {
+                constexpr int c = decltype(C)::value;
+                constexpr int ec = e_comp<L>(i, c);
+                add_signed<ec>(odd, Jw[c]);
+                if constexpr (ec != 0) even += Tq[c][c];
+                static_for<c + 1, D>([&](auto Dd) {
+                    constexpr int d = decltype(Dd)::value;
+                    add_signed<ec * e_comp<L>(i, d)>(even, Tq[c][d]);
+                });
+            });
+            constexpr real wi = real(w_vel<L>(i));
+            real ev = wi * even;
+            if constexpr (!FORCING) {
+                static_for<0, D>([&](auto C) {
+                    constexpr int c = decltype(C)::value;
+                    static_for<c, D>([&](auto Dd) {
+                        constexpr int d = decltype(Dd)::value;
+                        constexpr double wm = w_m<L>(i, c, d);
+                        if constexpr (wm != 0.0) ev += real(wm) * Mw[c][d];
+                    });
+                });
+            }
+            sum += ev;
+            out[i] = omw * f[i] + (ev + wi * odd);
+            out[o] = omw * f[o] + (ev - wi * odd);
+        }
+    });
+    out[0] = omw * f[0] + (omega * (rho - rsum) - real(2) * sum);  // Eq. 6 and sum_i F_i = 0
 }
 
 template <class L, bool FORCING, class S, int TX, int TY>
@@ -218,10 +290,11 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs args) {
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = Lay::D3 ? blockIdx.z * args.lz : 0;
     const int z1 = Lay::D3 ? min(z0 + args.lz, nz) : 1;
-    const size_t plane = size_t(nx) * ny;
+    const int plane = nx * ny;
 
     const real pa = real(args.a), pb = real(args.b), pT = real(args.T), pk = real(args.kappa);
     const real om = real(args.omega), nu = real(args.nu);
+    const real pref = real(args.pref), rsum = real(args.rsum);
 
     // stage-A work items: wrapped in-plane index of each halo-region site
     int a_in[Lay::NA], a_st[Lay::NA];
@@ -239,65 +312,93 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs args) {
     const int xs = x0 + tx, ys = y0 + ty;
     const bool own = xs < nx && ys < ny;
     const int xw[3] = {wrapi(xs - 1, nx), wrapi(xs, nx), wrapi(xs + 1, nx)};
-    const int yw[3] = {wrapi(ys - 1, ny), wrapi(ys, ny), wrapi(ys + 1, ny)};
+    const int yr[3] = {wrapi(ys - 1, ny) * nx, wrapi(ys, ny) * nx, wrapi(ys + 1, ny) * nx};
 
     const int pstart = z0 - Lay::LAG_C;
     const int pend = z1 + Lay::LAG_C;
+
+    // Populations of the halo region of one plane, held in registers.  In 3D
+    // with 32-bit arithmetic the loads of plane p+1 are issued before stages
+    // B and C of plane p, so their latency overlaps that work.
+    constexpr bool PREFETCH = Lay::D3 && sizeof(real) == 4;
+    typename S::raw0 r0[Lay::NA];
+    typename S::rawi ri[Lay::NA][Q - 1];
+    auto issue = [&](int p) {
+        const int poff = Lay::D3 ? wrapi(p, nz) * plane : 0;
+#pragma unroll
+        for (int m = 0; m < Lay::NA; ++m) {
+            if (a_in[m] >= 0) {
+                const size_t q = size_t(poff + a_in[m]);
+                r0[m] = S::ld0(args.src[0], q);
+                static_for<1, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    ri[m][i - 1] = S::ldi(args.src[i], q);
+                });
+            }
+        }
+    };
+    if (PREFETCH) issue(pstart);
+
     for (int p = pstart; p < pend; ++p) {
+        const int it = p - pstart;
         // ---------------- stage A: density of plane p on the halo region
         {
-            const size_t poff = Lay::D3 ? size_t(wrapi(p, nz)) * plane : 0;
-            const int rs = (p - pstart) % Lay::NRHO;
-            const int ss = (p - pstart) % Lay::NSTASH;
+            if (!PREFETCH) issue(p);
+            real* rho_w = rho_s + (it % Lay::NRHO) * RN;
+            real* st_w = stash + (it % Lay::NSTASH) * Q * NT;
             const bool keep = p >= z0 && p < z1;
 #pragma unroll
             for (int m = 0; m < Lay::NA; ++m) {
                 if (a_in[m] >= 0) {
-                    const size_t q = poff + size_t(a_in[m]);
-                    real f[Q];
-                    real r = real(0);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        f[i] = S::load(i, args.src[i], q, args.fref[i]);
-                        r += f[i];
-                    }
-                    rho_s[rs * RN + tid + m * NT] = r;
+                    real f[Q];               // f_0 and the deviations d_i
+                    f[0] = S::dec0(r0[m]);
+                    static_for<1, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        f[i] = S::devi(ri[m][i - 1]);
+                    });
+                    real r = rsum;
+                    static_for<1, Q>([&](auto I) { r += f[decltype(I)::value]; });
+                    r += f[0];
+                    rho_w[tid + m * NT] = r;
                     if (keep && a_st[m] >= 0) {
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) stash[(ss * Q + i) * NT + a_st[m]] = f[i];
+                        static_for<0, Q>([&](auto I) {
+                            constexpr int i = decltype(I)::value;
+                            st_w[i * NT + a_st[m]] = f[i];
+                        });
                     }
                 }
             }
+            if (PREFETCH && p + 1 < pend) issue(p + 1);
         }
         __syncthreads();
 
         // ---------------- stage B (forcing): G, M' on the tile + 1 ring of plane q
         if constexpr (FORCING) {
             const int q = p - Lay::LAG_B;
+            const int iq = q - pstart;
             if (!Lay::D3 || q >= z0 - 1) {
-                const int ms = (q - pstart) % (Lay::NMP > 0 ? Lay::NMP : 1);
-                const int gs = (q - pstart) % (Lay::NGL > 0 ? Lay::NGL : 1);
+                const real* rho_p[3] = {rho_s + ((iq + 2) % Lay::NRHO) * RN, rho_s + (iq % Lay::NRHO) * RN,
+                                        rho_s + ((iq + 1) % Lay::NRHO) * RN};   // planes q-1, q, q+1
+                real* mp_w = mp_s + (iq % Lay::NMP) * Lay::NMC * SN;
+                const int gs = iq % Lay::NGL;
 #pragma unroll
                 for (int m = 0; m < Lay::NB; ++m) {
                     const int k = tid + m * NT;
                     if (k < SN) {
                         const int sx = k % SX, sy = k / SX;
                         const int rc = (sy + H - 1) * RX + (sx + H - 1);
-                        const real r0 = rho_s[((q - pstart) % Lay::NRHO) * RN + rc];
+                        const real r0 = rho_p[1][rc];
                         real G[3] = {real(0), real(0), real(0)};
                         real lap = real(0);
-#pragma unroll
-                        for (int i = 1; i < Q; ++i) {
-                            const int pl = (q + L::ez(i) - pstart) % Lay::NRHO;
-                            const real rn = rho_s[pl * RN + rc + L::ey(i) * RX + L::ex(i)];
-                            const real wi = real(w_vel<L>(i));
-#pragma unroll
-                            for (int c = 0; c < D; ++c) {
-                                if (e_comp<L>(i, c) == 1) G[c] += wi * rn;
-                                if (e_comp<L>(i, c) == -1) G[c] -= wi * rn;
-                            }
+                        static_for<1, Q>([&](auto I) {
+                            constexpr int i = decltype(I)::value;
+                            const real rn = rho_p[1 + L::ez(i)][rc + L::ey(i) * RX + L::ex(i)];
+                            constexpr real wi = real(w_vel<L>(i));
+                            add_signed<L::ex(i)>(G[0], wi * rn);
+                            add_signed<L::ey(i)>(G[1], wi * rn);
+                            if constexpr (D == 3) add_signed<L::ez(i)>(G[2], wi * rn);
                             lap += wi * (rn - r0);
-                        }
+                        });
                         real g2 = real(0);
 #pragma unroll
                         for (int c = 0; c < D; ++c) g2 += G[c] * G[c];
@@ -307,7 +408,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs args) {
                             for (int d = c; d < D; ++d) {
                                 real v = pk * G[c] * G[d];
                                 if (c == d) v -= real(0.5) * pk * g2;
-                                mp_s[(ms * Lay::NMC + mcomp<D>(c, d)) * SN + k] = v;
+                                mp_w[mcomp<D>(c, d) * SN + k] = v;
                             }
                         if (sx >= 1 && sx <= TX && sy >= 1 && sy <= TY) {
                             const int r0i = (sy - 1) * TX + (sx - 1);
@@ -324,71 +425,73 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs args) {
         // ---------------- stage C: collide and push plane s
         const int s = p - Lay::LAG_C;
         if (s >= z0 && own) {
-            const int ss = (s - pstart) % Lay::NSTASH;
-            const int rsl = (s - pstart) % Lay::NRHO;
+            const int is = s - pstart;
+            const real* st_r = stash + (is % Lay::NSTASH) * Q * NT;
             real f[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = stash[(ss * Q + i) * NT + tid];
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                f[i] = st_r[i * NT + tid];
+            });
             const int rc = (ty + H) * RX + (tx + H);
-            const real rho = rho_s[rsl * RN + rc];
+            const real rho = rho_s[(is % Lay::NRHO) * RN + rc];
             real G[3] = {real(0), real(0), real(0)};
             real g[3] = {real(0), real(0), real(0)};
             real lap = real(0);
             if constexpr (FORCING) {
-                const int gs = (s - pstart) % Lay::NGL;
+                const int gs = is % Lay::NGL;
 #pragma unroll
                 for (int c = 0; c < D; ++c) G[c] = g0_s[(gs * D + c) * NT + tid];
                 lap = l0_s[gs * NT + tid];
                 // g_a = -sum_i w_i sum_b e_ib M'_ab(r + e_i)   (Eq. 28)
+                const real* mp_p[3] = {mp_s + ((is + 2) % Lay::NMP) * Lay::NMC * SN,
+                                       mp_s + (is % Lay::NMP) * Lay::NMC * SN,
+                                       mp_s + ((is + 1) % Lay::NMP) * Lay::NMC * SN};   // planes s-1, s, s+1
                 const int kc = (ty + 1) * SX + (tx + 1);
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const int pl = (s + L::ez(i) - pstart) % Lay::NMP;
-                    const int kn = kc + L::ey(i) * SX + L::ex(i);
-                    const real wi = real(w_vel<L>(i));
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
+                static_for<1, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    const real* mp = mp_p[1 + L::ez(i)] + kc + L::ey(i) * SX + L::ex(i);
+                    constexpr real wi = real(w_vel<L>(i));
+                    static_for<0, D>([&](auto C) {
+                        constexpr int c = decltype(C)::value;
                         real acc = real(0);
                         bool any = false;
-#pragma unroll
-                        for (int d = 0; d < D; ++d) {
-                            const int ed = e_comp<L>(i, d);
-                            if (ed != 0) {
-                                const real mv = mp_s[(pl * Lay::NMC + mcomp<D>(c, d)) * SN + kn];
-                                if (ed == 1) acc += mv;
-                                else acc -= mv;
+                        static_for<0, D>([&](auto Dd) {
+                            constexpr int d = decltype(Dd)::value;
+                            constexpr int ed = e_comp<L>(i, d);
+                            if constexpr (ed != 0) {
+                                add_signed<ed>(acc, mp[mcomp<D>(c, d) * SN]);
                                 any = true;
                             }
-                        }
+                        });
                         if (any) g[c] -= wi * acc;
-                    }
-                }
+                    });
+                });
             } else {
-                const real r0 = rho;
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const int pl = (s + L::ez(i) - pstart) % Lay::NRHO;
-                    const real rn = rho_s[pl * RN + rc + L::ey(i) * RX + L::ex(i)];
-                    const real wi = real(w_vel<L>(i));
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        if (e_comp<L>(i, c) == 1) G[c] += wi * rn;
-                        if (e_comp<L>(i, c) == -1) G[c] -= wi * rn;
-                    }
-                    lap += wi * (rn - r0);
-                }
+                const real* rho_p[3] = {rho_s + ((is + 2) % Lay::NRHO) * RN, rho_s + (is % Lay::NRHO) * RN,
+                                        rho_s + ((is + 1) % Lay::NRHO) * RN};
+                static_for<1, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    const real rn = rho_p[1 + L::ez(i)][rc + L::ey(i) * RX + L::ex(i)];
+                    constexpr real wi = real(w_vel<L>(i));
+                    add_signed<L::ex(i)>(G[0], wi * rn);
+                    add_signed<L::ey(i)>(G[1], wi * rn);
+                    if constexpr (D == 3) add_signed<L::ez(i)>(G[2], wi * rn);
+                    lap += wi * (rn - rho);
+                });
                 lap *= real(2);
             }
             if (!(rho > real(0)) || !(rho < real(1e30))) atomicOr(args.status, 1u);
             real out[Q];
-            collide<L, FORCING, real>(f, rho, G, lap, g, pa, pb, pT, pk, om, nu, out);
+            collide<L, FORCING, real>(f, rho, G, lap, g, pa, pb, pT, pk, om, nu, pref, rsum, out);
             const int zc = Lay::D3 ? wrapi(s, nz) : 0;
-            const int zw[3] = {Lay::D3 ? wrapi(s - 1, nz) : 0, zc, Lay::D3 ? wrapi(s + 1, nz) : 0};
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const size_t idx = (size_t(zw[1 + L::ez(i)]) * ny + yw[1 + L::ey(i)]) * nx + xw[1 + L::ex(i)];
-                S::store(i, args.dst[i], idx, out[i], args.fref[i]);
-            }
+            const int zr[3] = {Lay::D3 ? wrapi(s - 1, nz) * plane : 0, zc * plane,
+                               Lay::D3 ? wrapi(s + 1, nz) * plane : 0};
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const int idx = zr[1 + L::ez(i)] + yr[1 + L::ey(i)] + xw[1 + L::ex(i)];
+                if constexpr (i == 0) S::st0(args.dst[0], size_t(idx), out[0]);
+                else S::sti(args.dst[i], size_t(idx), out[i]);
+            });
         }
         if (Lay::D3) __syncthreads();
     }

@@ -10,6 +10,9 @@
 // contrast between the phases and stays float32.
 //
 // Populations are separate arrays (structure of arrays), one pointer each.
+// The step kernels work on deviations d_i = f_i - fref_i (i >= 1; fref = 0
+// for StF64 / StF32): devi / sti read and write the stored deviation, f_0 is
+// stored as is.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -18,7 +21,16 @@ namespace lbk {
 
 struct StF64 {
     using real = double;
+    using raw0 = double;   // stored type of f_0
+    using rawi = double;   // stored type of f_i, i >= 1
     static constexpr int id = 0;
+    __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const double*>(p)[idx]; }
+    __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) { return reinterpret_cast<const double*>(p)[idx]; }
+    __device__ __forceinline__ static real dec0(raw0 v) { return v; }
+    __device__ __forceinline__ static real deci(rawi v, float) { return v; }
+    __device__ __forceinline__ static real devi(rawi v) { return v; }
+    __device__ __forceinline__ static void st0(char* p, size_t idx, real v) { reinterpret_cast<double*>(p)[idx] = v; }
+    __device__ __forceinline__ static void sti(char* p, size_t idx, real d) { reinterpret_cast<double*>(p)[idx] = d; }
     __host__ __device__ static constexpr int bytes(int) { return 8; }
     __device__ __forceinline__ static real load(int, const char* p, size_t idx, float) {
         return reinterpret_cast<const double*>(p)[idx];
@@ -30,7 +42,16 @@ struct StF64 {
 
 struct StF32 {
     using real = float;
+    using raw0 = float;
+    using rawi = float;
     static constexpr int id = 1;
+    __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
+    __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
+    __device__ __forceinline__ static real dec0(raw0 v) { return v; }
+    __device__ __forceinline__ static real deci(rawi v, float) { return v; }
+    __device__ __forceinline__ static real devi(rawi v) { return v; }
+    __device__ __forceinline__ static void st0(char* p, size_t idx, real v) { reinterpret_cast<float*>(p)[idx] = v; }
+    __device__ __forceinline__ static void sti(char* p, size_t idx, real d) { reinterpret_cast<float*>(p)[idx] = d; }
     __host__ __device__ static constexpr int bytes(int) { return 4; }
     __device__ __forceinline__ static real load(int, const char* p, size_t idx, float) {
         return reinterpret_cast<const float*>(p)[idx];
@@ -42,7 +63,18 @@ struct StF32 {
 
 struct StF16 {
     using real = float;
+    using raw0 = float;
+    using rawi = __half;
     static constexpr int id = 2;
+    __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
+    __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) { return reinterpret_cast<const __half*>(p)[idx]; }
+    __device__ __forceinline__ static real dec0(raw0 v) { return v; }
+    __device__ __forceinline__ static real deci(rawi v, float ref) { return __half2float(v) + ref; }
+    __device__ __forceinline__ static real devi(rawi v) { return __half2float(v); }
+    __device__ __forceinline__ static void st0(char* p, size_t idx, real v) { reinterpret_cast<float*>(p)[idx] = v; }
+    __device__ __forceinline__ static void sti(char* p, size_t idx, real d) {
+        reinterpret_cast<__half*>(p)[idx] = __float2half_rn(d);
+    }
     __host__ __device__ static constexpr int bytes(int i) { return i == 0 ? 4 : 2; }
     __device__ __forceinline__ static real load(int i, const char* p, size_t idx, float ref) {
         if (i == 0) return reinterpret_cast<const float*>(p)[idx];
@@ -59,7 +91,20 @@ struct StF16 {
 
 struct StBF16 {
     using real = float;
+    using raw0 = float;
+    using rawi = __nv_bfloat16;
     static constexpr int id = 3;
+    __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
+    __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) {
+        return reinterpret_cast<const __nv_bfloat16*>(p)[idx];
+    }
+    __device__ __forceinline__ static real dec0(raw0 v) { return v; }
+    __device__ __forceinline__ static real deci(rawi v, float ref) { return __bfloat162float(v) + ref; }
+    __device__ __forceinline__ static real devi(rawi v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static void st0(char* p, size_t idx, real v) { reinterpret_cast<float*>(p)[idx] = v; }
+    __device__ __forceinline__ static void sti(char* p, size_t idx, real d) {
+        reinterpret_cast<__nv_bfloat16*>(p)[idx] = __float2bfloat16_rn(d);
+    }
     __host__ __device__ static constexpr int bytes(int i) { return i == 0 ? 4 : 2; }
     __device__ __forceinline__ static real load(int i, const char* p, size_t idx, float ref) {
         if (i == 0) return reinterpret_cast<const float*>(p)[idx];
