@@ -156,6 +156,37 @@ lb_status lb_shape(const lb_ctx* ctx, long long* n_sites, int* q);
  * callers that stage inputs in device memory themselves. */
 lb_status lb_device_state(lb_ctx* ctx, void** dptr, size_t* bytes);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free reductions.  The paper has no counterpart: this is a
+ * library service for callers that cannot allocate device memory when they
+ * need the numbers, e.g. an application whose allocator has already reserved
+ * the device memory it may use, or a stepping loop that must not pay for
+ * cudaMalloc/cudaFree (which can synchronise the device) or risk running out
+ * of memory mid-run.
+ *
+ * lb_field_stats_noalloc computes the same float64 reductions as
+ * lb_stats_get, but from caller-provided device fields, writing 8 doubles to
+ * the caller's device buffer out: {mass, momentum x, y, z, max|u|, max|v|,
+ * min rho, max rho} (momentum components beyond dim are 0).
+ *   rho: n doubles; u, v: dim*n doubles (component-major, as lb_fields);
+ *   all device pointers owned by the caller; dim in 1..3;
+ *   1 <= n <= LB_NOALLOC_MAX_SITES, larger n returns LB_EINVAL;
+ *   asynchronous on cuda_stream (a cudaStream_t, NULL = legacy stream).
+ * It calls no cudaMalloc/cudaFree and no allocating routine: its per-block
+ * partial sums live in a file-scope device array of LB_NOALLOC_MAX_BLOCKS*8
+ * doubles (256 KiB), present on every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array; each call rewrites the
+ * partials it reads, but calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race on it.
+ */
+#define LB_NOALLOC_MAX_BLOCKS 4096
+#define LB_NOALLOC_SITES_PER_BLOCK 4096
+#define LB_NOALLOC_MAX_SITES ((long long)LB_NOALLOC_MAX_BLOCKS * LB_NOALLOC_SITES_PER_BLOCK)
+lb_status lb_field_stats_noalloc(const double* rho, const double* u, const double* v, int dim, long long n,
+                                 double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

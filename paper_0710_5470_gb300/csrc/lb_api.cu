@@ -91,6 +91,10 @@ lb_status maxwell(double a, double b, double T, double* rl_out, double* rg_out) 
 
 }  // namespace
 
+// Sets the thread-local message returned by lb_last_error; used by the other
+// translation units of the library (not exported through the C ABI).
+__attribute__((visibility("hidden"))) void lb_internal_set_error(const char* msg) { g_last_error = msg; }
+
 // ------------------------------------------------------------------ context
 struct lb_ctx {
     lb_params p{};

@@ -60,6 +60,8 @@ _SIGNATURES = {
     "lb_stats_get": (C.c_int, [C.c_void_p, C.POINTER(lb_stats)]),
     "lb_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "lb_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    "lb_field_stats_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_longlong,
+                                         C.c_void_p, C.c_void_p]),
 }
 
 
@@ -97,6 +99,15 @@ def coexistence(a: float, b: float, T: float):
     rl, rg = C.c_double(), C.c_double()
     _check(load_library().lb_coexistence(a, b, T, C.byref(rl), C.byref(rg)))
     return rl.value, rg.value
+
+
+def field_stats_noalloc(rho_ptr: int, u_ptr: int, v_ptr: int, dim: int, n: int, out_ptr: int,
+                        stream: int = 0):
+    """lb_field_stats_noalloc on caller-owned device buffers (raw device
+    pointers as ints); allocates nothing.  Writes 8 doubles at out_ptr."""
+    _check(load_library().lb_field_stats_noalloc(C.c_void_p(rho_ptr), C.c_void_p(u_ptr), C.c_void_p(v_ptr),
+                                                 int(dim), int(n), C.c_void_p(out_ptr),
+                                                 C.c_void_p(stream) if stream else None))
 
 
 def version() -> str:
