@@ -32,6 +32,26 @@ WORKLOAD = dict(lattice="D3Q19", n=128, R=30.0, scheme="forcing", T=0.55, kappa=
 BYTES_POP = {"f64": (8, 8), "f32": (4, 4), "f16dev": (4, 2), "bf16dev": (4, 2)}   # (f_0, f_i) bytes
 
 
+KERNEL_SOURCES = ["step3d.cuh", "step_kernel.cuh", "storage.cuh", "lattice.cuh"]
+# DRAM bytes (read + write) per launch of the D3Q19 forcing step kernel at
+# 128^3, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
+# fingerprint of the kernel sources they were measured on and the storage.
+# A changed kernel has a new fingerprint and reports traffic = null.
+NCU_TRAFFIC = {
+    ("1b80c15f4bca", "f16dev", 128): 133.43e6,   # 94.22 MB read + 39.21 MB written
+    ("1b80c15f4bca", "f32", 128): 291.95e6,      # 179.50 MB read + 112.46 MB written
+}
+
+
+def kernel_fingerprint() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_0710_5470_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def bytes_per_lu(storage: str, q: int = 19) -> int:
     """Algorithmic HBM bytes per lattice update: one read and one write of
     every stored population (rho is recomputed on chip, never stored)."""
@@ -49,6 +69,7 @@ def parse():
     p.add_argument("--n", type=int, default=WORKLOAD["n"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-variants", action="store_true")
     return p.parse_args()
 
 
@@ -184,6 +205,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(ctx, stream, steps, dist=None):
+    """CUDA-event time (ms) of exactly `steps` launches on the context's stream."""
+    import torch
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        ctx.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    return ev0.elapsed_time(ev1)
+
+
+def make_ctx(lb, storage: str, n: int, stream):
+    ctx = lb.Context(lb.D3Q19, (n, n, n), A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"],
+                     scheme=lb.FORCING, storage=lb.STORAGE_NAMES[storage], stream=stream.cuda_stream)
+    R = WORKLOAD["R"] * n / WORKLOAD["n"]
+    ctx.init_drops([(n / 2,) * 3], [R], WORKLOAD["width"])
+    return ctx, R
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -197,53 +241,42 @@ def run_native(args):
     if rank != 0:
         build.build()
     lb.load_library()
-    storage = lb.STORAGE_NAMES[args.storage]
     n = args.n
+    sites = n ** 3
     stream = torch.cuda.current_stream()
-    ctx = lb.Context(lb.D3Q19, (n, n, n), A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"],
-                     scheme=lb.FORCING, storage=storage, stream=stream.cuda_stream)
-    R = WORKLOAD["R"] * n / WORKLOAD["n"]
-    ctx.init_drops([(n / 2,) * 3], [R], WORKLOAD["width"])
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    fp = kernel_fingerprint()
+
+    ctx, R = make_ctx(lb, args.storage, n, stream)
     ctx.step(args.warmup)
     ctx.synchronize()
-
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    barrier(dist)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        ctx.step(1)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(dist)
-    ms_local = ev0.elapsed_time(ev1)
+    ms_local = time_steps(ctx, stream, args.steps, dist)
     clk = clocks.stop()
     ctx.synchronize()
     st = ctx.stats()
     ms = reduce_max(dist, ms_local)
-    sites = n ** 3
     mlups = sites * args.steps * world / (ms / 1e3) / 1e6
 
-    # roofline of the fused step kernel (the only kernel in the timed region)
-    peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    # roofline of the fused step kernel (the only kernel in the timed region):
+    # algorithmic bytes per launch / average launch duration
     bpl = bytes_per_lu(args.storage)
     t_launch = ms_local / args.steps / 1e3
     achieved = bpl * sites / t_launch / 1e9
+    traffic = NCU_TRAFFIC.get((fp, args.storage, n))
 
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned): upload the initial
+    # density, run the steps, download rho and u
     e2e = None
     if not args.no_e2e:
         rl, rg = ctx.coexistence()
-        from paper_0710_5470_gb300 import inputs
         rho_h = torch.empty(sites, dtype=torch.float64, pin_memory=True).numpy()
-        c, r = inputs.centred_drop((n, n, n), R)
         z, y, x = np.meshgrid(*(np.arange(n, dtype=np.float64),) * 3, indexing="ij")
-        d = np.sqrt((x - c[0][0]) ** 2 + (y - c[0][1]) ** 2 + (z - c[0][2]) ** 2)
-        rho_h[:] = (rg + (rl - rg) * 0.5 * (1 + np.tanh((r[0] - d) / WORKLOAD["width"]))).reshape(-1)
+        d = np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - n / 2) ** 2)
+        rho_h[:] = (rg + (rl - rg) * 0.5 * (1 + np.tanh((R - d) / WORKLOAD["width"]))).reshape(-1)
         out_rho = torch.empty(sites, dtype=torch.float64, pin_memory=True).numpy()
         out_u = torch.empty(3 * sites, dtype=torch.float64, pin_memory=True).numpy()
         barrier(dist)
@@ -252,20 +285,40 @@ def run_native(args):
         ctx.init_fields(rho_h)
         ctx.step(args.steps)
         ctx.fields_into(out_rho, out_u)
-        dt = time.perf_counter() - t0
-        dt = reduce_max(dist, dt)
+        dt = reduce_max(dist, time.perf_counter() - t0)
         e2e = {"value": sites * args.steps * world / dt / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": sites * 8 / args.steps, "d2h_bytes_per_step": sites * 8 * 4 / args.steps}
+               "h2d_bytes_per_step": sites * 8 / args.steps, "d2h_bytes_per_step": sites * 8 * 4 / args.steps,
+               "note": "init from a host density field, K steps, rho and u back to the host"}
+    ctx.close()
+
+    variants = {}
+    if not args.no_variants:
+        for sname in BYTES_POP:
+            if sname == args.storage:
+                continue
+            vctx, _ = make_ctx(lb, sname, n, stream)
+            vsteps = max(1, args.steps // (20 if sname == "f64" else 1))
+            vctx.step(min(args.warmup, 5) if sname == "f64" else args.warmup)
+            vctx.synchronize()
+            vms = reduce_max(dist, time_steps(vctx, stream, vsteps, dist))
+            vst = vctx.stats()
+            vctx.close()
+            vb = bytes_per_lu(sname)
+            vach = vb * sites / (vms / vsteps / 1e3) / 1e9
+            variants[sname] = {"value": sites * vsteps * world / (vms / 1e3) / 1e6, "steps": vsteps,
+                               "ms_per_step": vms / vsteps,
+                               "roofline": {"bound": "hbm", "achieved": vach, "peak": peak, "unit": "GB/s",
+                                            "frac": vach / peak, "bytes_per_lu": vb,
+                                            "traffic": NCU_TRAFFIC.get((fp, sname, n))},
+                               "max_v": vst["max_v"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        edge = 64
+        edge = n
         v, dt, lu = oracle_sample(edge, 2)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"2 FP64 oracle steps (numpy, single thread) on a {edge}^3 box with the drop scaled "
-                         f"to the box ({dt:.1f} s)"}
+               "sample": f"2 FP64 oracle steps (numpy, one thread) on the full {edge}^3 drop workload ({dt:.1f} s)"}
 
-    ctx.close()
     if rank == 0:
         line = {
             "metric": "MLUPS (D3Q19 128^3 free-energy LB step, forcing scheme)",
@@ -274,15 +327,17 @@ def run_native(args):
             "dtype": "f32" if args.storage != "f64" else "f64", "data": "synthetic",
             "config": {"workload": f"D3Q19 {n}^3 periodic, one drop R={R:g}, forcing scheme, T=0.55, "
                                    f"kappa=0.01, tau=1.0", "storage": args.storage,
-                       "l2": "working set (two population buffers) larger than L2",
+                       "l2": "inputs larger than L2: the two population buffers exceed the 126 MB L2",
                        "parallelism": f"{world} independent replica(s)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "bytes_per_lu": bpl,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+                         "frac": achieved / peak, "traffic": traffic, "bytes_per_lu": bpl,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                         "kernel_fingerprint": fp},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clk,
+            "variants": variants,
             "check": {"max_v": st["max_v"], "mass": st["mass"], "status": st["status"]},
         }
         print(json.dumps(line), flush=True)
