@@ -157,6 +157,46 @@ lb_status lb_shape(const lb_ctx* ctx, long long* n_sites, int* q);
 lb_status lb_device_state(lb_ctx* ctx, void** dptr, size_t* bytes);
 
 /* ------------------------------------------------------------------------
+ * Batched sweeps of independent D2Q9 drop runs (parameter sweeps of the
+ * Sec. IV test problem).  Every instance has its own lattice size, T, kappa
+ * and tau and one centred drop; all share a, b, the scheme and the storage.
+ * One kernel launch advances every active instance by one time step (work
+ * items = (instance, tile)); lb_batch_run_to_steady replays a CUDA graph of
+ * `every` steps plus a float64 convergence check and retires instances whose
+ * max_r |u(t) - u(t - every)| < tol (u of Eq. 3).  Tile shapes (32x8, 32x16,
+ * 64x8) are chosen by lb_batch_autotune, which times each on the live state
+ * and restores it.
+ */
+typedef struct lb_batch lb_batch;
+typedef struct {
+    int nx, ny;            /* lattice of the instance, >= 1 */
+    double T, kappa, tau;  /* van der Waals temperature, gradient coefficient, relaxation time */
+    double radius;         /* radius of its centred drop (lb_batch_init_drops); <= 0: no drop */
+} lb_instance;
+
+/* n in 1..4096 instances; cuda_stream NULL => the batch creates its own stream. */
+lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, const lb_instance* inst,
+                          void* cuda_stream, lb_batch** out);
+lb_status lb_batch_destroy(lb_batch* batch);   /* NULL-safe */
+/* f = f^eq of a tanh drop (same profile as lb_init_drops) in every instance; resets the run state. */
+lb_status lb_batch_init_drops(lb_batch* batch, double width);
+/* f = f^eq(rho, u) for instance k from host fields (u may be NULL). */
+lb_status lb_batch_init_fields(lb_batch* batch, int k, const double* rho, const double* u);
+/* Advance every active instance nsteps time steps. */
+lb_status lb_batch_step(lb_batch* batch, int nsteps);
+/* Time each tile variant for `steps` steps on a copy of the state and keep the fastest. */
+lb_status lb_batch_autotune(lb_batch* batch, int steps, int* tile_x, int* tile_y);
+/* Run until every instance is retired or max_steps: steps_out[k] = steps at retirement (-1: not
+ * converged), status_out[k] = LB_OK (converged), LB_ETIMEOUT (not converged within max_steps) or
+ * LB_EUNSTABLE (non-finite density).  every must be even; no instance retires before min_steps. */
+lb_status lb_batch_run_to_steady(lb_batch* batch, double tol, int every, long long min_steps, long long max_steps,
+                                 long long* steps_out, int* status_out, long long* total_steps);
+/* Host copies of rho (N) and u (2N) of instance k, and of its populations (9N, layout as lb_get_populations). */
+lb_status lb_batch_fields(lb_batch* batch, int k, double* rho, double* u);
+lb_status lb_batch_populations(lb_batch* batch, int k, double* f);
+lb_status lb_batch_info(const lb_batch* batch, int* tile_x, int* tile_y, long long* sites, long long* steps);
+
+/* ------------------------------------------------------------------------
  * Allocation-free reductions.  The paper has no counterpart: this is a
  * library service for callers that cannot allocate device memory when they
  * need the numbers, e.g. an application whose allocator has already reserved

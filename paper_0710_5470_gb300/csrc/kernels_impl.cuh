@@ -21,8 +21,13 @@ struct StepKernelOf {
         else return reinterpret_cast<const void*>(step_kernel<L, FORCING, S, TX, TY>);
     }
     static void launch(dim3 grid, cudaStream_t st, const StepArgs& a) {
-        if constexpr (D3) step_kernel3d<FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(a);
-        else step_kernel<L, FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(a);
+        if constexpr (D3) {
+            step_kernel3d<FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(a);
+        } else {
+            Tile2DArgs t{a.src_base, a.dst_base, a.pitch, a.nx, a.ny, a.a, a.b, a.T, a.kappa, a.omega, a.nu,
+                         a.pref, a.rsum, a.status};
+            step_kernel<L, FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(t);
+        }
     }
 };
 

@@ -461,6 +461,9 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
             a.src[i] = c->fbuf + pop_offset(c, i, c->cur);
             a.dst[i] = c->fbuf + pop_offset(c, i, 1 - c->cur);
         }
+        a.src_base = a.src[0];
+        a.dst_base = a.dst[0];
+        a.pitch = (long long)c->pitch;
         cudaError_t e = c->ks.step(a, c->grid, c->stream);
         if (e != cudaSuccess) return record(c, e, "step kernel");
         c->cur = 1 - c->cur;

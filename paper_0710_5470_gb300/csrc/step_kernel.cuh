@@ -34,6 +34,9 @@ constexpr int MAXQ = 19;
 struct StepArgs {
     const char* src[MAXQ];
     char* dst[MAXQ];
+    const char* src_base;   // population 0 of src; population i at pop_offset(i, pitch)
+    char* dst_base;
+    long long pitch;        // elements per population array
     float fref[MAXQ];
     float pref, rsum;  // deviation storage: fref_i = w_i pref, rsum = pref sum_{i>=1} w_i
     int nx, ny, nz;
@@ -269,232 +272,170 @@ __device__ __forceinline__ void collide(const real (&f)[L::Q], real rho, const r
     out[0] = omw * f[0] + (omega * (rho - rsum) - real(2) * sum);  // Eq. 6 and sum_i F_i = 0
 }
 
+// Per-tile arguments of the 2D step: population buffers as one base pointer
+// each (population i at byte offset S::pop_offset(i, pitch)), grid size and
+// physical parameters.
+struct Tile2DArgs {
+    const char* src;
+    char* dst;
+    long long pitch;
+    int nx, ny;
+    double a, b, T, kappa, omega, nu;
+    float pref, rsum;
+    unsigned int* status;
+};
+
+// One D2Q9 time step of the TX x TY tile at (x0, y0) (Eq. 4): stage A sums
+// rho on the tile plus a halo of H sites, stage B (forcing) computes the
+// gradient and M' on the tile plus one ring, stage C collides and pushes the
+// tile's sites.  smem holds StepLayout<L, FORCING, TX, TY, real>::TOTAL reals.
 template <class L, bool FORCING, class S, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs args) {
+__device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int y0, typename S::real* sm) {
+    static_assert(L::D == 2, "2D tile step");
     using real = typename S::real;
     using Lay = StepLayout<L, FORCING, TX, TY, real>;
-    constexpr int Q = L::Q, D = L::D, H = Lay::H, NT = Lay::NT;
+    constexpr int Q = L::Q, D = 2, H = Lay::H, NT = Lay::NT;
     constexpr int RX = Lay::RX, RN = Lay::RN, SX = Lay::SX, SN = Lay::SN;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real* sm = reinterpret_cast<real*>(smem_raw);
     real* rho_s = sm + Lay::OFF_RHO;
     real* stash = sm + Lay::OFF_STASH;
     real* mp_s = sm + Lay::OFF_MP;
     real* g0_s = sm + Lay::OFF_G;
     real* l0_s = sm + Lay::OFF_L;
 
-    const int nx = args.nx, ny = args.ny, nz = args.nz;
+    const int nx = args.nx, ny = args.ny;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = Lay::D3 ? blockIdx.z * args.lz : 0;
-    const int z1 = Lay::D3 ? min(z0 + args.lz, nz) : 1;
-    const int plane = nx * ny;
-
     const real pa = real(args.a), pb = real(args.b), pT = real(args.T), pk = real(args.kappa);
     const real om = real(args.omega), nu = real(args.nu);
     const real pref = real(args.pref), rsum = real(args.rsum);
+    const long long pitch = args.pitch;
 
-    // stage-A work items: wrapped in-plane index of each halo-region site
-    int a_in[Lay::NA], a_st[Lay::NA];
+    // ---------------- stage A: density on the halo region
 #pragma unroll
     for (int m = 0; m < Lay::NA; ++m) {
         const int k = tid + m * NT;
-        a_in[m] = -1;
-        a_st[m] = -1;
         if (k < RN) {
             const int rx = k % RX, ry = k / RX;
-            a_in[m] = wrapi(y0 - H + ry, ny) * nx + wrapi(x0 - H + rx, nx);
-            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY) a_st[m] = (ry - H) * TX + (rx - H);
+            const size_t q = size_t(wrapi(y0 - H + ry, ny)) * nx + wrapi(x0 - H + rx, nx);
+            real f[Q];
+            f[0] = S::dec0(S::ld0(args.src, q));
+            static_for<1, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                f[i] = S::devi(S::ldi(args.src + S::pop_offset(i, pitch), q));
+            });
+            real r = rsum;
+            static_for<1, Q>([&](auto I) { r += f[decltype(I)::value]; });
+            r += f[0];
+            rho_s[k] = r;
+            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY) {
+                const int st = (ry - H) * TX + (rx - H);
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    stash[i * NT + st] = f[i];
+                });
+            }
         }
     }
-    const int xs = x0 + tx, ys = y0 + ty;
-    const bool own = xs < nx && ys < ny;
-    const int xw[3] = {wrapi(xs - 1, nx), wrapi(xs, nx), wrapi(xs + 1, nx)};
-    const int yr[3] = {wrapi(ys - 1, ny) * nx, wrapi(ys, ny) * nx, wrapi(ys + 1, ny) * nx};
+    __syncthreads();
 
-    const int pstart = z0 - Lay::LAG_C;
-    const int pend = z1 + Lay::LAG_C;
-
-    // Populations of the halo region of one plane, held in registers.  In 3D
-    // with 32-bit arithmetic the loads of plane p+1 are issued before stages
-    // B and C of plane p, so their latency overlaps that work.
-    constexpr bool PREFETCH = Lay::D3 && sizeof(real) == 4;
-    typename S::raw0 r0[Lay::NA];
-    typename S::rawi ri[Lay::NA][Q - 1];
-    auto issue = [&](int p) {
-        const int poff = Lay::D3 ? wrapi(p, nz) * plane : 0;
+    // ---------------- stage B (forcing): G, M' on the tile + 1 ring
+    if constexpr (FORCING) {
 #pragma unroll
-        for (int m = 0; m < Lay::NA; ++m) {
-            if (a_in[m] >= 0) {
-                const size_t q = size_t(poff + a_in[m]);
-                r0[m] = S::ld0(args.src[0], q);
+        for (int m = 0; m < Lay::NB; ++m) {
+            const int k = tid + m * NT;
+            if (k < SN) {
+                const int sx = k % SX, sy = k / SX;
+                const int rc = (sy + H - 1) * RX + (sx + H - 1);
+                const real r0 = rho_s[rc];
+                real G[2] = {real(0), real(0)};
+                real lap = real(0);
                 static_for<1, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    ri[m][i - 1] = S::ldi(args.src[i], q);
-                });
-            }
-        }
-    };
-    if (PREFETCH) issue(pstart);
-
-    for (int p = pstart; p < pend; ++p) {
-        const int it = p - pstart;
-        // ---------------- stage A: density of plane p on the halo region
-        {
-            if (!PREFETCH) issue(p);
-            real* rho_w = rho_s + (it % Lay::NRHO) * RN;
-            real* st_w = stash + (it % Lay::NSTASH) * Q * NT;
-            const bool keep = p >= z0 && p < z1;
-#pragma unroll
-            for (int m = 0; m < Lay::NA; ++m) {
-                if (a_in[m] >= 0) {
-                    real f[Q];               // f_0 and the deviations d_i
-                    f[0] = S::dec0(r0[m]);
-                    static_for<1, Q>([&](auto I) {
-                        constexpr int i = decltype(I)::value;
-                        f[i] = S::devi(ri[m][i - 1]);
-                    });
-                    real r = rsum;
-                    static_for<1, Q>([&](auto I) { r += f[decltype(I)::value]; });
-                    r += f[0];
-                    rho_w[tid + m * NT] = r;
-                    if (keep && a_st[m] >= 0) {
-                        static_for<0, Q>([&](auto I) {
-                            constexpr int i = decltype(I)::value;
-                            st_w[i * NT + a_st[m]] = f[i];
-                        });
-                    }
-                }
-            }
-            if (PREFETCH && p + 1 < pend) issue(p + 1);
-        }
-        __syncthreads();
-
-        // ---------------- stage B (forcing): G, M' on the tile + 1 ring of plane q
-        if constexpr (FORCING) {
-            const int q = p - Lay::LAG_B;
-            const int iq = q - pstart;
-            if (!Lay::D3 || q >= z0 - 1) {
-                const real* rho_p[3] = {rho_s + ((iq + 2) % Lay::NRHO) * RN, rho_s + (iq % Lay::NRHO) * RN,
-                                        rho_s + ((iq + 1) % Lay::NRHO) * RN};   // planes q-1, q, q+1
-                real* mp_w = mp_s + (iq % Lay::NMP) * Lay::NMC * SN;
-                const int gs = iq % Lay::NGL;
-#pragma unroll
-                for (int m = 0; m < Lay::NB; ++m) {
-                    const int k = tid + m * NT;
-                    if (k < SN) {
-                        const int sx = k % SX, sy = k / SX;
-                        const int rc = (sy + H - 1) * RX + (sx + H - 1);
-                        const real r0 = rho_p[1][rc];
-                        real G[3] = {real(0), real(0), real(0)};
-                        real lap = real(0);
-                        static_for<1, Q>([&](auto I) {
-                            constexpr int i = decltype(I)::value;
-                            const real rn = rho_p[1 + L::ez(i)][rc + L::ey(i) * RX + L::ex(i)];
-                            constexpr real wi = real(w_vel<L>(i));
-                            add_signed<L::ex(i)>(G[0], wi * rn);
-                            add_signed<L::ey(i)>(G[1], wi * rn);
-                            if constexpr (D == 3) add_signed<L::ez(i)>(G[2], wi * rn);
-                            lap += wi * (rn - r0);
-                        });
-                        real g2 = real(0);
-#pragma unroll
-                        for (int c = 0; c < D; ++c) g2 += G[c] * G[c];
-#pragma unroll
-                        for (int c = 0; c < D; ++c)
-#pragma unroll
-                            for (int d = c; d < D; ++d) {
-                                real v = pk * G[c] * G[d];
-                                if (c == d) v -= real(0.5) * pk * g2;
-                                mp_w[mcomp<D>(c, d) * SN + k] = v;
-                            }
-                        if (sx >= 1 && sx <= TX && sy >= 1 && sy <= TY) {
-                            const int r0i = (sy - 1) * TX + (sx - 1);
-#pragma unroll
-                            for (int c = 0; c < D; ++c) g0_s[(gs * D + c) * NT + r0i] = G[c];
-                            l0_s[gs * NT + r0i] = real(2) * lap;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-
-        // ---------------- stage C: collide and push plane s
-        const int s = p - Lay::LAG_C;
-        if (s >= z0 && own) {
-            const int is = s - pstart;
-            const real* st_r = stash + (is % Lay::NSTASH) * Q * NT;
-            real f[Q];
-            static_for<0, Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                f[i] = st_r[i * NT + tid];
-            });
-            const int rc = (ty + H) * RX + (tx + H);
-            const real rho = rho_s[(is % Lay::NRHO) * RN + rc];
-            real G[3] = {real(0), real(0), real(0)};
-            real g[3] = {real(0), real(0), real(0)};
-            real lap = real(0);
-            if constexpr (FORCING) {
-                const int gs = is % Lay::NGL;
-#pragma unroll
-                for (int c = 0; c < D; ++c) G[c] = g0_s[(gs * D + c) * NT + tid];
-                lap = l0_s[gs * NT + tid];
-                // g_a = -sum_i w_i sum_b e_ib M'_ab(r + e_i)   (Eq. 28)
-                const real* mp_p[3] = {mp_s + ((is + 2) % Lay::NMP) * Lay::NMC * SN,
-                                       mp_s + (is % Lay::NMP) * Lay::NMC * SN,
-                                       mp_s + ((is + 1) % Lay::NMP) * Lay::NMC * SN};   // planes s-1, s, s+1
-                const int kc = (ty + 1) * SX + (tx + 1);
-                static_for<1, Q>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    const real* mp = mp_p[1 + L::ez(i)] + kc + L::ey(i) * SX + L::ex(i);
-                    constexpr real wi = real(w_vel<L>(i));
-                    static_for<0, D>([&](auto C) {
-                        constexpr int c = decltype(C)::value;
-                        real acc = real(0);
-                        bool any = false;
-                        static_for<0, D>([&](auto Dd) {
-                            constexpr int d = decltype(Dd)::value;
-                            constexpr int ed = e_comp<L>(i, d);
-                            if constexpr (ed != 0) {
-                                add_signed<ed>(acc, mp[mcomp<D>(c, d) * SN]);
-                                any = true;
-                            }
-                        });
-                        if (any) g[c] -= wi * acc;
-                    });
-                });
-            } else {
-                const real* rho_p[3] = {rho_s + ((is + 2) % Lay::NRHO) * RN, rho_s + (is % Lay::NRHO) * RN,
-                                        rho_s + ((is + 1) % Lay::NRHO) * RN};
-                static_for<1, Q>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    const real rn = rho_p[1 + L::ez(i)][rc + L::ey(i) * RX + L::ex(i)];
+                    const real rn = rho_s[rc + L::ey(i) * RX + L::ex(i)];
                     constexpr real wi = real(w_vel<L>(i));
                     add_signed<L::ex(i)>(G[0], wi * rn);
                     add_signed<L::ey(i)>(G[1], wi * rn);
-                    if constexpr (D == 3) add_signed<L::ez(i)>(G[2], wi * rn);
-                    lap += wi * (rn - rho);
+                    lap += wi * (rn - r0);
                 });
-                lap *= real(2);
+                const real hk = real(0.5) * pk * (G[0] * G[0] + G[1] * G[1]);
+                mp_s[0 * SN + k] = pk * G[0] * G[0] - hk;
+                mp_s[1 * SN + k] = pk * G[1] * G[1] - hk;
+                mp_s[2 * SN + k] = pk * G[0] * G[1];
+                if (sx >= 1 && sx <= TX && sy >= 1 && sy <= TY) {
+                    const int r0i = (sy - 1) * TX + (sx - 1);
+                    g0_s[r0i] = G[0];
+                    g0_s[NT + r0i] = G[1];
+                    l0_s[r0i] = real(2) * lap;
+                }
             }
-            if (!(rho > real(0)) || !(rho < real(1e30))) atomicOr(args.status, 1u);
-            real out[Q];
-            collide<L, FORCING, real>(f, rho, G, lap, g, pa, pb, pT, pk, om, nu, pref, rsum, out);
-            const int zc = Lay::D3 ? wrapi(s, nz) : 0;
-            const int zr[3] = {Lay::D3 ? wrapi(s - 1, nz) * plane : 0, zc * plane,
-                               Lay::D3 ? wrapi(s + 1, nz) * plane : 0};
-            static_for<0, Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                const int idx = zr[1 + L::ez(i)] + yr[1 + L::ey(i)] + xw[1 + L::ex(i)];
-                if constexpr (i == 0) S::st0(args.dst[0], size_t(idx), out[0]);
-                else S::sti(args.dst[i], size_t(idx), out[i]);
-            });
         }
-        if (Lay::D3) __syncthreads();
+        __syncthreads();
     }
+
+    // ---------------- stage C: collide and push
+    const int xs = x0 + tx, ys = y0 + ty;
+    if (xs < nx && ys < ny) {
+        real f[Q];
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            f[i] = stash[i * NT + tid];
+        });
+        const int rc = (ty + H) * RX + (tx + H);
+        const real rho = rho_s[rc];
+        real G[3] = {real(0), real(0), real(0)};
+        real g[3] = {real(0), real(0), real(0)};
+        real lap = real(0);
+        if constexpr (FORCING) {
+            G[0] = g0_s[tid];
+            G[1] = g0_s[NT + tid];
+            lap = l0_s[tid];
+            // g_a = -sum_i w_i sum_b e_ib M'_ab(r + e_i)   (Eq. 28)
+            const int kc = (ty + 1) * SX + (tx + 1);
+            static_for<1, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const real* mp = mp_s + kc + L::ey(i) * SX + L::ex(i);
+                constexpr real wi = real(w_vel<L>(i));
+                static_for<0, D>([&](auto C) {
+                    constexpr int c = decltype(C)::value;
+                    real acc = real(0);
+                    static_for<0, D>([&](auto Dd) {
+                        constexpr int d = decltype(Dd)::value;
+                        add_signed<e_comp<L>(i, d)>(acc, mp[mcomp<D>(c, d) * SN]);
+                    });
+                    g[c] -= wi * acc;
+                });
+            });
+        } else {
+            static_for<1, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const real rn = rho_s[rc + L::ey(i) * RX + L::ex(i)];
+                constexpr real wi = real(w_vel<L>(i));
+                add_signed<L::ex(i)>(G[0], wi * rn);
+                add_signed<L::ey(i)>(G[1], wi * rn);
+                lap += wi * (rn - rho);
+            });
+            lap *= real(2);
+        }
+        if (!(rho > real(0)) || !(rho < real(1e30))) atomicOr(args.status, 1u);
+        real out[Q];
+        collide<L, FORCING, real>(f, rho, G, lap, g, pa, pb, pT, pk, om, nu, pref, rsum, out);
+        const int xw[3] = {wrapi(xs - 1, nx), xs, wrapi(xs + 1, nx)};
+        const int yr[3] = {wrapi(ys - 1, ny) * nx, ys * nx, wrapi(ys + 1, ny) * nx};
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const size_t idx = size_t(yr[1 + L::ey(i)] + xw[1 + L::ex(i)]);
+            if constexpr (i == 0) S::st0(args.dst, idx, out[0]);
+            else S::sti(args.dst + S::pop_offset(i, pitch), idx, out[i]);
+        });
+    }
+}
+
+// One step of a single D2Q9 lattice: one CTA per tile.
+template <class L, bool FORCING, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) step_kernel(const Tile2DArgs args) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step2d_tile<L, FORCING, S, TX, TY>(args, blockIdx.x * TX, blockIdx.y * TY,
+                                       reinterpret_cast<typename S::real*>(smem_raw));
 }
 
 }  // namespace lbk

@@ -32,6 +32,7 @@ struct StF64 {
     __device__ __forceinline__ static void st0(char* p, size_t idx, real v) { reinterpret_cast<double*>(p)[idx] = v; }
     __device__ __forceinline__ static void sti(char* p, size_t idx, real d) { reinterpret_cast<double*>(p)[idx] = d; }
     __host__ __device__ static constexpr int bytes(int) { return 8; }
+    __host__ __device__ static constexpr long long pop_offset(int i, long long pitch) { return i * pitch * 8; }
     __device__ __forceinline__ static real load(int, const char* p, size_t idx, float) {
         return reinterpret_cast<const double*>(p)[idx];
     }
@@ -53,6 +54,7 @@ struct StF32 {
     __device__ __forceinline__ static void st0(char* p, size_t idx, real v) { reinterpret_cast<float*>(p)[idx] = v; }
     __device__ __forceinline__ static void sti(char* p, size_t idx, real d) { reinterpret_cast<float*>(p)[idx] = d; }
     __host__ __device__ static constexpr int bytes(int) { return 4; }
+    __host__ __device__ static constexpr long long pop_offset(int i, long long pitch) { return i * pitch * 4; }
     __device__ __forceinline__ static real load(int, const char* p, size_t idx, float) {
         return reinterpret_cast<const float*>(p)[idx];
     }
@@ -76,6 +78,9 @@ struct StF16 {
         reinterpret_cast<__half*>(p)[idx] = __float2half_rn(d);
     }
     __host__ __device__ static constexpr int bytes(int i) { return i == 0 ? 4 : 2; }
+    __host__ __device__ static constexpr long long pop_offset(int i, long long pitch) {
+        return i == 0 ? 0 : pitch * 4 + (i - 1) * pitch * 2;
+    }
     __device__ __forceinline__ static real load(int i, const char* p, size_t idx, float ref) {
         if (i == 0) return reinterpret_cast<const float*>(p)[idx];
         return __half2float(reinterpret_cast<const __half*>(p)[idx]) + ref;
@@ -106,6 +111,9 @@ struct StBF16 {
         reinterpret_cast<__nv_bfloat16*>(p)[idx] = __float2bfloat16_rn(d);
     }
     __host__ __device__ static constexpr int bytes(int i) { return i == 0 ? 4 : 2; }
+    __host__ __device__ static constexpr long long pop_offset(int i, long long pitch) {
+        return i == 0 ? 0 : pitch * 4 + (i - 1) * pitch * 2;
+    }
     __device__ __forceinline__ static real load(int i, const char* p, size_t idx, float ref) {
         if (i == 0) return reinterpret_cast<const float*>(p)[idx];
         return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[idx]) + ref;

@@ -40,6 +40,11 @@ class lb_stats(C.Structure):
                 ("step", C.c_longlong), ("status", C.c_int)]
 
 
+class lb_instance(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("T", C.c_double), ("kappa", C.c_double), ("tau", C.c_double),
+                ("radius", C.c_double)]
+
+
 _lib = None
 
 _DPTR = C.POINTER(C.c_double)
@@ -60,6 +65,19 @@ _SIGNATURES = {
     "lb_stats_get": (C.c_int, [C.c_void_p, C.POINTER(lb_stats)]),
     "lb_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "lb_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    "lb_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(lb_instance),
+                                  C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lb_batch_destroy": (C.c_int, [C.c_void_p]),
+    "lb_batch_init_drops": (C.c_int, [C.c_void_p, C.c_double]),
+    "lb_batch_init_fields": (C.c_int, [C.c_void_p, C.c_int, _DPTR, _DPTR]),
+    "lb_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lb_batch_run_to_steady": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_longlong, C.c_longlong,
+                                         C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "lb_batch_fields": (C.c_int, [C.c_void_p, C.c_int, _DPTR, _DPTR]),
+    "lb_batch_populations": (C.c_int, [C.c_void_p, C.c_int, _DPTR]),
+    "lb_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                C.POINTER(C.c_longlong)]),
     "lb_field_stats_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_longlong,
                                          C.c_void_p, C.c_void_p]),
 }
@@ -206,3 +224,76 @@ class Context:
         p, nb = C.c_void_p(), C.c_size_t()
         _check(self._lib.lb_device_state(self._h, C.byref(p), C.byref(nb)))
         return p.value, nb.value
+
+
+class Batch:
+    """Independent D2Q9 drop runs advanced together (lb_batch_*)."""
+
+    def __init__(self, instances, a: float, b: float, scheme: int = EQUILIBRIUM, storage: int = F64, stream=None):
+        lib = load_library()
+        self.instances = [dict(d) for d in instances]
+        arr = (lb_instance * len(instances))(*[lb_instance(d["nx"], d["ny"], d["T"], d["kappa"], d["tau"],
+                                                              d.get("radius", 0.0)) for d in instances])
+        h = C.c_void_p()
+        st = C.c_void_p(int(stream)) if stream else None
+        _check(lib.lb_batch_create(scheme, storage, a, b, len(instances), arr, st, C.byref(h)))
+        self._h, self._lib, self.n = h, lib, len(instances)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init_drops(self, width: float = 2.0):
+        _check(self._lib.lb_batch_init_drops(self._h, width))
+
+    def init_fields(self, k: int, rho: np.ndarray, u: np.ndarray | None = None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        _check(self._lib.lb_batch_init_fields(self._h, k, _dptr(rho), _dptr(uu)))
+
+    def step(self, n: int = 1):
+        _check(self._lib.lb_batch_step(self._h, int(n)))
+
+    def autotune(self, steps: int = 10):
+        tx, ty = C.c_int(), C.c_int()
+        _check(self._lib.lb_batch_autotune(self._h, steps, C.byref(tx), C.byref(ty)))
+        return tx.value, ty.value
+
+    def run_to_steady(self, tol: float = 1e-10, every: int = 100, min_steps: int = 0, max_steps: int = 200000):
+        steps = (C.c_longlong * self.n)()
+        status = (C.c_int * self.n)()
+        total = C.c_longlong()
+        _check(self._lib.lb_batch_run_to_steady(self._h, tol, every, min_steps, max_steps, steps, status,
+                                                C.byref(total)))
+        return list(steps), list(status), total.value
+
+    def fields(self, k: int):
+        d = self.instances[k]
+        rho = np.empty((d["ny"], d["nx"]), dtype=np.float64)
+        u = np.empty((2, d["ny"], d["nx"]), dtype=np.float64)
+        _check(self._lib.lb_batch_fields(self._h, k, _dptr(rho), _dptr(u)))
+        return rho, u
+
+    def populations(self, k: int):
+        d = self.instances[k]
+        f = np.empty((9, 1, d["ny"], d["nx"]), dtype=np.float64)
+        _check(self._lib.lb_batch_populations(self._h, k, _dptr(f)))
+        return f
+
+    def info(self):
+        tx, ty, sites, steps = C.c_int(), C.c_int(), C.c_longlong(), C.c_longlong()
+        _check(self._lib.lb_batch_info(self._h, C.byref(tx), C.byref(ty), C.byref(sites), C.byref(steps)))
+        return {"tile": (tx.value, ty.value), "sites": sites.value, "steps": steps.value}

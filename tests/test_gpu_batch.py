@@ -1,0 +1,100 @@
+"""Batched D2Q9 sweeps (lb_batch_*) through the C ABI.
+
+An instance of a batch runs the same per-tile arithmetic as a single-lattice
+context, so float64 results agree bit for bit whatever tile the autotuner
+picks; one instance is also checked against the oracle.  Retirement by the
+convergence check is compared with the same check done by hand.
+"""
+import numpy as np
+import pytest
+
+from oracle import lb_oracle as O
+from tests.helpers import A_VDW, B_VDW, library, make_ctx, oracle_model, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+INST = [dict(nx=40, ny=33, T=0.55, kappa=0.01, tau=0.8, radius=9.0),
+        dict(nx=64, ny=64, T=0.53, kappa=0.012, tau=1.2, radius=15.0),
+        dict(nx=19, ny=45, T=0.56, kappa=0.006, tau=0.65, radius=5.0)]
+
+
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_batch_instances_match_single_contexts_bitwise(scheme):
+    lb = library()
+    sch = 0 if scheme == "equilibrium" else 1
+    with lb.Batch(INST, A_VDW, B_VDW, scheme=sch, storage=lb.F64) as bt:
+        bt.init_drops(2.0)
+        f_init = [bt.populations(k) for k in range(len(INST))]
+        bt.autotune(3)
+        for k in range(len(INST)):
+            assert np.array_equal(bt.populations(k), f_init[k])      # autotune restored the state
+        bt.step(37)
+        got = [bt.populations(k) for k in range(len(INST))]
+    for k, d in enumerate(INST):
+        with make_ctx(lb, "D2Q9", scheme, (d["nx"], d["ny"]), T=d["T"], kappa=d["kappa"], tau=d["tau"]) as ctx:
+            ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
+            assert np.array_equal(ctx.get_populations(), f_init[k])
+            ctx.step(37)
+            assert np.array_equal(ctx.get_populations(), got[k])
+    # oracle check on a parameter set where rounding perturbations do not grow
+    # (at T = 0.52, kappa = 0.02, tau = 1.2 a 1e-16 perturbation reaches 1e-10
+    # within 37 steps in the oracle itself: an unstable mode)
+    d = INST[1]
+    m = oracle_model("D2Q9", scheme, T=d["T"], kappa=d["kappa"], tau=d["tau"])
+    want = O.run(f_init[1], m, 37)
+    assert rel_inf(got[1], want) < 1e-12
+
+
+def test_run_to_steady_retires_at_the_hand_check():
+    """Retirement step = first multiple of `every` with max|u(t) - u(t-every)| < tol."""
+    lb = library()
+    inst = [dict(nx=32, ny=32, T=0.55, kappa=0.01, tau=1.0, radius=8.0),
+            dict(nx=24, ny=40, T=0.54, kappa=0.015, tau=0.9, radius=6.0)]
+    tol, every = 1e-7, 50
+    with lb.Batch(inst, A_VDW, B_VDW, scheme=1, storage=lb.F64) as bt:
+        bt.init_drops(2.0)
+        steps, status, total = bt.run_to_steady(tol=tol, every=every, max_steps=20000)
+    assert status == [0, 0]
+    for k, d in enumerate(inst):
+        with make_ctx(lb, "D2Q9", "forcing", (d["nx"], d["ny"]), T=d["T"], kappa=d["kappa"], tau=d["tau"]) as ctx:
+            ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
+            uprev = np.zeros((2, d["ny"], d["nx"]))
+            t = 0
+            while True:
+                ctx.step(every)
+                t += every
+                _, u, _ = ctx.fields(want_v=False)
+                du = np.sqrt(((u - uprev) ** 2).sum(axis=0)).max()
+                uprev = u
+                if du < tol:
+                    break
+            assert steps[k] == t
+
+
+def test_unstable_instance_is_retired_alone():
+    """A NaN density in one instance marks it LB_EUNSTABLE; the others converge."""
+    lb = library()
+    inst = [dict(nx=24, ny=24, T=0.55, kappa=0.01, tau=1.0, radius=6.0),
+            dict(nx=24, ny=24, T=0.55, kappa=0.01, tau=1.0, radius=6.0)]
+    with lb.Batch(inst, A_VDW, B_VDW, scheme=0, storage=lb.F64) as bt:
+        bt.init_drops(2.0)
+        rho, _ = bt.fields(1)
+        rho[3, 3] = np.nan
+        bt.init_fields(1, rho)
+        steps, status, total = bt.run_to_steady(tol=1e-6, every=20, max_steps=4000)
+    assert status[0] == 0 and status[1] == 4
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_reduced_storage_batch_matches_single_context(storage):
+    lb = library()
+    with lb.Batch(INST, A_VDW, B_VDW, scheme=1, storage=storage) as bt:
+        bt.init_drops(2.0)
+        bt.step(20)
+        got = bt.populations(0)
+    d = INST[0]
+    with make_ctx(lb, "D2Q9", "forcing", (d["nx"], d["ny"]), storage=storage, T=d["T"], kappa=d["kappa"],
+                  tau=d["tau"]) as ctx:
+        ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
+        ctx.step(20)
+        assert np.array_equal(ctx.get_populations(), got)
