@@ -197,6 +197,47 @@ lb_status lb_batch_populations(lb_batch* batch, int k, double* f);
 lb_status lb_batch_info(const lb_batch* batch, int* tile_x, int* tile_y, long long* sites, long long* steps);
 
 /* ------------------------------------------------------------------------
+ * Learned warm start (a build addition; the paper has no learned component).
+ * A 4-layer fully convolutional network (periodic 3x3 convolutions, 5 -> 32
+ * -> 32 -> 32 -> 3 channels, tanh between layers, fp16 weights with float32
+ * accumulation) maps the planes (tanh-start density, T, kappa, tau, 10/R) of
+ * a D2Q9 drop to its steady (density correction, 1000 u_x, 1000 u_y), so a
+ * run can start from lb_init_fields(predicted rho, u) instead of the tanh
+ * profile.  Training (forward, backward, MSE, Adam) runs in the library's
+ * kernels.  Image arrays are float32, layout [sample][channel][y][x].
+ * Parameters are packed as W_1 (32x5x3x3), b_1, W_2, b_2, W_3, b_3, W_4 (3x32x3x3), b_4.
+ */
+#define LB_WS_IN 5
+#define LB_WS_HIDDEN 32
+#define LB_WS_OUT 3
+typedef struct lb_ws lb_ws;
+lb_status lb_ws_create(int seed, void* cuda_stream, lb_ws** out);
+lb_status lb_ws_destroy(lb_ws* ws);   /* NULL-safe */
+lb_status lb_ws_num_params(const lb_ws* ws, long long* n);
+lb_status lb_ws_set_params(lb_ws* ws, const float* params, size_t count);   /* resets the Adam state */
+lb_status lb_ws_get_params(lb_ws* ws, float* params, size_t count);
+/* y (n x 3 x H x W) = network(x (n x 5 x H x W)). */
+lb_status lb_ws_forward(lb_ws* ws, const float* x, int n, int H, int W, float* y);
+/* Prediction for one drop (x: 5 x H x W) averaged over the symmetries of the periodic lattice
+ * that fix the domain centre (reflections about W/2 and H/2, and the transpose when H == W), with
+ * the velocity channels transformed as a vector: the result has the symmetry of the input. */
+lb_status lb_ws_predict_sym(lb_ws* ws, const float* x, int H, int W, float* y);
+/* Mean squared error of network(x) against t and its parameter gradients (packed; may be NULL). */
+lb_status lb_ws_loss_grad(lb_ws* ws, const float* x, const float* t, int n, int H, int W, double* loss,
+                          float* grads);
+/* Adam (beta 0.9, 0.999) on minibatches of `batch` samples, reshuffled every epoch;
+ * loss_history[e] = mean minibatch loss of epoch e (may be NULL). */
+lb_status lb_ws_train(lb_ws* ws, const float* x, const float* t, int n, int H, int W, int epochs, int batch,
+                      float lr, int seed, double* loss_history);
+/* Input planes of one drop, and the decoding of a prediction into rho (N) and u (2N); decoding
+ * keeps the mass of the tanh start (the mass residual of the predicted density correction is
+ * removed with weight 1 - 4c^2, c the normalised tanh density, i.e. inside the interface). */
+lb_status lb_ws_features(int nx, int ny, const double* rho_tanh, double rho_l, double rho_g, double T, double kappa,
+                         double tau, double R, float* x);
+lb_status lb_ws_decode(int nx, int ny, const double* rho_tanh, double rho_l, double rho_g, const float* y,
+                       double* rho, double* u);
+
+/* ------------------------------------------------------------------------
  * Allocation-free reductions.  The paper has no counterpart: this is a
  * library service for callers that cannot allocate device memory when they
  * need the numbers, e.g. an application whose allocator has already reserved
