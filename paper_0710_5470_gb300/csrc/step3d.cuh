@@ -32,9 +32,10 @@ struct Layout3D {
     static constexpr int NT = TX * TY;
     static constexpr int NA = (RN + NT - 1) / NT;
     static constexpr int NB = FORCING ? (SN + NT - 1) / NT : 1;
+    static constexpr int LAG_C = FORCING ? 2 : 1;   // stage C trails stage A by LAG_C planes
+    // rho and stash slots: planes p .. p - LAG_C are live; a barrier closes each plane
     static constexpr int NRHO = 3;
     static constexpr int NSTASH = FORCING ? 3 : 2;
-    static constexpr int LAG_C = FORCING ? 2 : 1;
     static constexpr int OFF_RHO = 0;
     static constexpr int OFF_STASH = OFF_RHO + NRHO * RN;
     static constexpr int OFF_MP = OFF_STASH + NSTASH * Q * NT;
@@ -80,7 +81,7 @@ __device__ __forceinline__ void assemble(const PlaneParts<real>& lo, const Plane
 }
 
 template <bool FORCING, class S, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, sizeof(typename S::real) == 4 ? 2 : 1) step_kernel3d(const StepArgs args) {
+__global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX * TY <= 256) ? 2 : 1) step_kernel3d(const StepArgs args) {
     using L = D3Q19;
     using real = typename S::real;
     using Lay = Layout3D<FORCING, TX, TY, real>;
@@ -141,15 +142,25 @@ __global__ void __launch_bounds__(TX* TY, sizeof(typename S::real) == 4 ? 2 : 1)
 
     const int pstart = z0 - Lay::LAG_C;
     const int pend = z1 + Lay::LAG_C;
+    const int vol = nz * plane;
+    // plane offsets wrapped once here and advanced by one plane per use
+    // (v + plane wraps to 0 at vol): the plane loaded next, and planes s-1,
+    // s, s+1 of the next stage C
+    int ld_off = wrapi(pstart, nz) * plane;
+    int zr[3] = {wrapi(z0 - 1, nz) * plane, wrapi(z0, nz) * plane, wrapi(z0 + 1, nz) * plane};
+    auto advance = [&](int& v) {
+        v += plane;
+        if (v == vol) v = 0;
+    };
 
     typename S::raw0 r0[Lay::NA];
     typename S::rawi ri[Lay::NA][Q - 1];
-    auto issue = [&](int p) {
-        const int poff = wrapi(p, nz) * plane;
+    // load plane ld_off of the halo region into r0/ri, then advance ld_off
+    auto issue = [&]() {
 #pragma unroll
         for (int m = 0; m < Lay::NA; ++m) {
             if (a_in[m] >= 0) {
-                const size_t q = size_t(poff + a_in[m]);
+                const size_t q = size_t(ld_off + a_in[m]);
                 r0[m] = S::ld0(args.src[0], q);
                 static_for<1, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
@@ -157,9 +168,10 @@ __global__ void __launch_bounds__(TX* TY, sizeof(typename S::real) == 4 ? 2 : 1)
                 });
             }
         }
+        advance(ld_off);
     };
     constexpr bool PREFETCH = sizeof(real) == 4;
-    if (PREFETCH) issue(pstart);
+    if (PREFETCH) issue();
 
     // carried stencil parts of the stage-B items: planes p-2 (lo) and p-1 (mid)
     PlaneParts<real> pl_lo[Lay::NB], pl_mid[Lay::NB];
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(TX* TY, sizeof(typename S::real) == 4 ? 2 : 1)
         const int it = p - pstart;
         // ---------------- stage A: density of plane p on the halo region
         {
-            if (!PREFETCH) issue(p);
+            if (!PREFETCH) issue();
             real* rho_w = rho_s + (it % Lay::NRHO) * RN;
             real* st_w = stash + (it % Lay::NSTASH) * Q * NT;
             const bool keep = p >= z0 && p < z1;
@@ -197,7 +209,7 @@ __global__ void __launch_bounds__(TX* TY, sizeof(typename S::real) == 4 ? 2 : 1)
                     }
                 }
             }
-            if (PREFETCH && p + 1 < pend) issue(p + 1);
+            if (PREFETCH && p + 1 < pend) issue();
         }
         __syncthreads();
 
@@ -325,13 +337,17 @@ __global__ void __launch_bounds__(TX* TY, sizeof(typename S::real) == 4 ? 2 : 1)
             if (!(rho > real(0)) || !(rho < real(1e30))) atomicOr(args.status, 1u);
             real out[Q];
             collide<L, FORCING, real>(f, rho, G, lap, gf, pa, pb, pT, pk, om, nu, pref, rsum, out);
-            const int zr[3] = {wrapi(s - 1, nz) * plane, wrapi(s, nz) * plane, wrapi(s + 1, nz) * plane};
             static_for<0, Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 const int idx = zr[1 + L::ez(i)] + yr[1 + L::ey(i)] + xw[1 + L::ex(i)];
                 if constexpr (i == 0) S::st0(args.dst[0], size_t(idx), out[0]);
                 else S::sti(args.dst[i], size_t(idx), out[i]);
             });
+        }
+        if (s >= z0) {
+            advance(zr[0]);
+            advance(zr[1]);
+            advance(zr[2]);
         }
         __syncthreads();
     }
