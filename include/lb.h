@@ -191,6 +191,22 @@ lb_status lb_batch_autotune(lb_batch* batch, int steps, int* tile_x, int* tile_y
  * LB_EUNSTABLE (non-finite density).  every must be even; no instance retires before min_steps. */
 lb_status lb_batch_run_to_steady(lb_batch* batch, double tol, int every, long long min_steps, long long max_steps,
                                  long long* steps_out, int* status_out, long long* total_steps);
+/* Steady-state test against a reference, for storage whose rounding keeps max|u(t) - u(t - every)|
+ * above any useful tol: instance k with umax_ref > 0 is converged once, for `hold` consecutive checks,
+ * max|u| is within band * umax_ref of umax_ref and, if rho_max_ref > 0, the largest and smallest
+ * densities are within tol_rho of rho_max_ref and rho_min_ref (bulk liquid and gas; these do not
+ * change when rounding noise translates the drop, which the periodic lattice allows).  umax_ref = 0
+ * restores the max|du| < tol test for k.  The paper defines no steady-state test (Sec. IV runs to a
+ * fixed time); the reference is typically the float64 steady state, so runs in other storage formats
+ * stop at equal accuracy.  LB_EINVAL for k out of range, umax_ref < 0 or a non-finite value.  Applies
+ * to later lb_batch_run_to_steady calls. */
+lb_status lb_batch_set_reference(lb_batch* batch, int k, double umax_ref, double rho_max_ref, double rho_min_ref);
+/* Parameters of the reference test (defaults band 0.05, tol_rho 1e-3, hold 10); LB_EINVAL for a
+ * negative band or tol_rho or hold < 1. */
+lb_status lb_batch_set_band(lb_batch* batch, double band, double tol_rho, int hold);
+/* max|u(t) - u(t - every)|, max|u|, max rho and min rho of each instance at its last check (0 before
+ * the first check; frozen at retirement).  Any output may be NULL.  Synchronises. */
+lb_status lb_batch_last_check(lb_batch* batch, double* du, double* umax, double* rho_max, double* rho_min);
 /* Host copies of rho (N) and u (2N) of instance k, and of its populations (9N, layout as lb_get_populations). */
 lb_status lb_batch_fields(lb_batch* batch, int k, double* rho, double* u);
 lb_status lb_batch_populations(lb_batch* batch, int k, double* f);

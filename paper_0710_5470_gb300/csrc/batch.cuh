@@ -3,9 +3,9 @@
 // of work items (instance, tile) drives the launches, so one launch advances
 // every active instance by one time step with the same per-tile code as the
 // single-lattice kernel (step2d_tile).  Every `every` steps a check kernel
-// computes max |u(t) - u(t - every)| per instance (float64), a finalize
-// kernel retires converged or unstable instances and rebuilds the work list
-// on the device.  No kernel waits on another CTA.
+// computes max |u(t) - u(t - every)| and max |u| per instance (float64), a
+// finalize kernel retires converged or unstable instances and rebuilds the
+// work list on the device.  No kernel waits on another CTA.
 #pragma once
 #include "aux_kernels.cuh"
 
@@ -27,6 +27,13 @@ struct BatchState {
     int* active;                 // per instance: 1 while stepping
     unsigned int* status;        // per instance: bit 0 = non-finite density seen
     unsigned long long* maxdu;   // per instance: max |du| of the current check (double bits)
+    unsigned long long* maxu;    // per instance: max |u| of the current check (double bits)
+    unsigned long long* maxrho;  // per instance: max rho of the current check (double bits)
+    unsigned long long* minrho;  // per instance: min rho of the current check (double bits)
+    double* last;                // per instance: max |du|, max |u|, max rho, min rho of its last check
+    const double* ref;           // per instance: reference max |u|, max rho, min rho (max |u| <= 0: tol test;
+                                 // max rho <= 0: no density condition)
+    int* inband;                 // per instance: consecutive checks inside the band
     long long* steps_done;       // per instance: steps when retired (-1 while active)
     long long* gstep;            // steps taken by the batch (device copy)
     double* uprev;               // u at the previous check, 2 per site
@@ -51,13 +58,13 @@ __global__ void __launch_bounds__(TX* TY) batch_step_kernel(BatchState bs, char*
 template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) batch_check_kernel(BatchState bs, const char* buf, int parity) {
     if (blockIdx.x >= *bs.count) return;
-    __shared__ double red[TX * TY];
+    __shared__ double red[TX * TY], redu[TX * TY], rmax[TX * TY], rmin[TX * TY];
     const int it = bs.items[blockIdx.x];
     const int k = it >> 20, t = it & 0xFFFFF;
     const BatchInst& I = bs.inst[k];
     const int x = (t % I.tiles_x) * TX + int(threadIdx.x) % TX;
     const int y = (t / I.tiles_x) * TY + int(threadIdx.x) / TX;
-    double du = 0.0;
+    double du = 0.0, um = 0.0, rhi = 0.0, rlo = 1e300;
     if (x < I.nx && y < I.ny) {
         const size_t q = size_t(y) * I.nx + x;
         const char* src = buf + I.off[parity];
@@ -77,22 +84,44 @@ __global__ void __launch_bounds__(TX* TY) batch_check_kernel(BatchState bs, cons
         const double dx = ux - up[0], dy = uy - up[1];
         du = sqrt(dx * dx + dy * dy);
         if (!(du <= 1e300)) du = 1e300;   // non-finite -> huge
+        um = sqrt(ux * ux + uy * uy);
+        if (!(um <= 1e300)) um = 1e300;
+        rhi = rho > 0.0 && rho <= 1e300 ? rho : 1e300;   // non-finite or non-positive -> out of any band
+        rlo = rho > 0.0 && rho <= 1e300 ? rho : 0.0;
         up[0] = ux;
         up[1] = uy;
     }
     red[threadIdx.x] = du;
+    redu[threadIdx.x] = um;
+    rmax[threadIdx.x] = rhi;
+    rmin[threadIdx.x] = rlo;
     __syncthreads();
     for (int s = TX * TY / 2; s > 0; s >>= 1) {
-        if (int(threadIdx.x) < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        if (int(threadIdx.x) < s) {
+            red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+            redu[threadIdx.x] = fmax(redu[threadIdx.x], redu[threadIdx.x + s]);
+            rmax[threadIdx.x] = fmax(rmax[threadIdx.x], rmax[threadIdx.x + s]);
+            rmin[threadIdx.x] = fmin(rmin[threadIdx.x], rmin[threadIdx.x + s]);
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicMax(bs.maxdu + k, (unsigned long long)__double_as_longlong(red[0]));
+    // non-negative doubles order like their bit patterns
+    if (threadIdx.x == 0) {
+        atomicMax(bs.maxdu + k, (unsigned long long)__double_as_longlong(red[0]));
+        atomicMax(bs.maxu + k, (unsigned long long)__double_as_longlong(redu[0]));
+        atomicMax(bs.maxrho + k, (unsigned long long)__double_as_longlong(rmax[0]));
+        atomicMin(bs.minrho + k, (unsigned long long)__double_as_longlong(rmin[0]));
+    }
 }
 
-// Retire converged (max |du| < tol) and unstable instances, advance the step
-// counter by `every`, and rebuild the work list of the remaining instances.
+// Retire unstable and converged instances, advance the step counter by
+// `every`, and rebuild the work list of the remaining instances.  Converged:
+// max |du| < tol, or, for an instance with a reference, max |u| within
+// band * (its reference) of the reference and (with reference densities) max
+// rho and min rho within tol_rho of theirs, for `hold` consecutive checks.
 // One block; instances are visited in order, so the list is deterministic.
-__global__ void batch_finalize_kernel(BatchState bs, double tol, int every, long long min_steps) {
+__global__ void batch_finalize_kernel(BatchState bs, double tol, int every, long long min_steps, double band,
+                                      double tol_rho, int hold) {
     __shared__ int offs[1025];
     __shared__ long long g;
     if (threadIdx.x == 0) {
@@ -103,15 +132,33 @@ __global__ void batch_finalize_kernel(BatchState bs, double tol, int every, long
     for (int k = threadIdx.x; k < bs.n; k += blockDim.x) {
         if (bs.active[k]) {
             const double du = __longlong_as_double((long long)bs.maxdu[k]);
-            if (bs.status[k]) {
-                bs.active[k] = 0;
-                bs.steps_done[k] = g;
-            } else if (du < tol && g >= min_steps) {
+            const double um = __longlong_as_double((long long)bs.maxu[k]);
+            const double hi = __longlong_as_double((long long)bs.maxrho[k]);
+            const double lo = __longlong_as_double((long long)bs.minrho[k]);
+            bs.last[4 * k] = du;
+            bs.last[4 * k + 1] = um;
+            bs.last[4 * k + 2] = hi;
+            bs.last[4 * k + 3] = lo;
+            bool done = false;
+            const double* r = bs.ref + 3 * k;
+            if (r[0] > 0.0) {
+                const bool in = fabs(um - r[0]) <= band * r[0] &&
+                                (!(r[1] > 0.0) || (fabs(hi - r[1]) <= tol_rho && fabs(lo - r[2]) <= tol_rho));
+                const int c = in ? bs.inband[k] + 1 : 0;
+                bs.inband[k] = c;
+                done = c >= hold;
+            } else {
+                done = du < tol;
+            }
+            if (bs.status[k] || (done && g >= min_steps)) {
                 bs.active[k] = 0;
                 bs.steps_done[k] = g;
             }
         }
         bs.maxdu[k] = 0ull;
+        bs.maxu[k] = 0ull;
+        bs.maxrho[k] = 0ull;
+        bs.minrho[k] = (unsigned long long)__double_as_longlong(1e300);
     }
     __syncthreads();
     // work list: prefix sum of active tile counts, in chunks of blockDim instances

@@ -121,6 +121,14 @@ struct lb_batch {
     int* d_active = nullptr;
     unsigned* d_status = nullptr;
     unsigned long long* d_maxdu = nullptr;
+    unsigned long long* d_maxu = nullptr;
+    unsigned long long* d_maxrho = nullptr;
+    unsigned long long* d_minrho = nullptr;
+    double* d_last = nullptr;
+    double* d_ref = nullptr;          // per instance: reference max |u|, max rho, min rho
+    int* d_inband = nullptr;
+    double band = 0.05, tol_rho = 1e-3;
+    int hold = 10;
     long long* d_steps = nullptr;
     long long* d_gstep = nullptr;
     double* d_uprev = nullptr;
@@ -132,13 +140,16 @@ struct lb_batch {
     double graph_tol = 0;
     long long graph_min = 0;
     int graph_tile = -1;
+    double graph_band = -1, graph_tol_rho = -1;
+    int graph_hold = -1;
 };
 
 namespace {
 
 BatchState state_of(lb_batch* B) {
-    return BatchState{B->d_inst, B->d_items, B->d_count, B->d_active, B->d_status, B->d_maxdu,
-                      B->d_steps,  B->d_gstep, B->d_uprev, B->n};
+    return BatchState{B->d_inst,   B->d_items,  B->d_count,  B->d_active, B->d_status, B->d_maxdu,
+                      B->d_maxu,   B->d_maxrho, B->d_minrho, B->d_last,   B->d_ref,    B->d_inband,
+                      B->d_steps,  B->d_gstep,  B->d_uprev,  B->n};
 }
 
 PopPtrs pops_of(lb_batch* B, int k, int parity) {
@@ -193,6 +204,14 @@ lb_status reset_run_state(lb_batch* B) {
     cudaError_t e = cudaMemcpyAsync(B->d_active, ones.data(), B->n * sizeof(int), cudaMemcpyHostToDevice, B->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_status, 0, B->n * sizeof(unsigned), B->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_maxdu, 0, B->n * sizeof(unsigned long long), B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_maxu, 0, B->n * sizeof(unsigned long long), B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_maxrho, 0, B->n * sizeof(unsigned long long), B->stream);
+    const double big = 1e300;
+    std::vector<double> bigs(B->n, big);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_minrho, bigs.data(), B->n * sizeof(double), cudaMemcpyHostToDevice, B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_last, 0, B->n * 4 * sizeof(double), B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_inband, 0, B->n * sizeof(int), B->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_steps, minus.data(), B->n * sizeof(long long), cudaMemcpyHostToDevice, B->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_gstep, 0, sizeof(long long), B->stream);
@@ -286,6 +305,12 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
         (e = cudaMalloc(&B->d_active, n * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_status, n * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_maxdu, n * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_maxu, n * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_maxrho, n * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_minrho, n * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_last, n * 4 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_ref, n * 3 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_inband, n * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_steps, n * sizeof(long long))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_gstep, sizeof(long long))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_uprev, size_t(B->sites) * 2 * sizeof(double))) != cudaSuccess ||
@@ -294,6 +319,10 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
         (e = cudaMalloc(&B->w_io, size_t(B->max_sites) * 9 * sizeof(double))) != cudaSuccess) {
         lb_batch_destroy(B);
         return fail(LB_ENOMEM, std::string("batch buffers: ") + cudaGetErrorString(e));
+    }
+    if ((e = cudaMemsetAsync(B->d_ref, 0, n * 3 * sizeof(double), B->stream)) != cudaSuccess) {
+        lb_batch_destroy(B);
+        return cuda_err(e, "batch targets");
     }
     lb_status s = reset_run_state(B);
     if (s != LB_OK) { lb_batch_destroy(B); return s; }
@@ -312,6 +341,12 @@ lb_status lb_batch_destroy(lb_batch* B) {
     cudaFree(B->d_active);
     cudaFree(B->d_status);
     cudaFree(B->d_maxdu);
+    cudaFree(B->d_maxu);
+    cudaFree(B->d_maxrho);
+    cudaFree(B->d_minrho);
+    cudaFree(B->d_last);
+    cudaFree(B->d_ref);
+    cudaFree(B->d_inband);
     cudaFree(B->d_steps);
     cudaFree(B->d_gstep);
     cudaFree(B->d_uprev);
@@ -419,7 +454,8 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
     }
     // one graph: `every` steps, the convergence check, retirement and work-list rebuild
     if (!B->graph || B->graph_every != every || B->graph_tol != tol || B->graph_min != min_steps ||
-        B->graph_tile != B->tile) {
+        B->graph_tile != B->tile || B->graph_band != B->band || B->graph_hold != B->hold ||
+        B->graph_tol_rho != B->tol_rho) {
         if (B->graph) cudaGraphExecDestroy(B->graph);
         B->graph = nullptr;
         cudaGraph_t g;
@@ -428,7 +464,7 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
         const BatchState bs = state_of(B);
         for (int s = 0; s < every; ++s) B->k.step(bs, B->buf, s & 1, B->max_items, B->stream);
         B->k.check(bs, B->buf, 0, B->max_items, B->stream);
-        batch_finalize_kernel<<<1, 1024, 0, B->stream>>>(bs, tol, every, min_steps);
+        batch_finalize_kernel<<<1, 1024, 0, B->stream>>>(bs, tol, every, min_steps, B->band, B->tol_rho, B->hold);
         e = cudaStreamEndCapture(B->stream, &g);
         if (e != cudaSuccess) return cuda_err(e, "end capture");
         e = cudaGraphInstantiate(&B->graph, g, 0);
@@ -438,6 +474,9 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
         B->graph_tol = tol;
         B->graph_min = min_steps;
         B->graph_tile = B->tile;
+        B->graph_band = B->band;
+        B->graph_tol_rho = B->tol_rho;
+        B->graph_hold = B->hold;
     }
     // the device step counter continues from the host one
     cudaError_t e = cudaMemcpyAsync(B->d_gstep, &B->gstep, sizeof(long long), cudaMemcpyHostToDevice, B->stream);
@@ -462,6 +501,43 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
         if (status_out) status_out[k] = stat[k] ? LB_EUNSTABLE : (st[k] < 0 ? LB_ETIMEOUT : LB_OK);
     }
     if (total_steps) *total_steps = done;
+    return LB_OK;
+}
+
+lb_status lb_batch_set_reference(lb_batch* B, int k, double umax_ref, double rho_max_ref, double rho_min_ref) {
+    if (!B || k < 0 || k >= B->n) return fail(LB_EINVAL, "bad arguments");
+    if (!(umax_ref >= 0.0) || !std::isfinite(umax_ref) || !std::isfinite(rho_max_ref) || !std::isfinite(rho_min_ref))
+        return fail(LB_EINVAL, "references must be finite, umax_ref >= 0");
+    const double r[3] = {umax_ref, rho_max_ref, rho_min_ref};
+    cudaError_t e = cudaMemcpyAsync(B->d_ref + 3 * k, r, sizeof(r), cudaMemcpyHostToDevice, B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_inband + k, 0, sizeof(int), B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return cuda_err(e, "batch reference");
+    return LB_OK;
+}
+
+lb_status lb_batch_set_band(lb_batch* B, double band, double tol_rho, int hold) {
+    if (!B || !(band >= 0.0) || !(tol_rho >= 0.0) || hold < 1)
+        return fail(LB_EINVAL, "need band >= 0, tol_rho >= 0 and hold >= 1");
+    B->band = band;
+    B->tol_rho = tol_rho;
+    B->hold = hold;
+    return LB_OK;
+}
+
+lb_status lb_batch_last_check(lb_batch* B, double* du, double* umax, double* rho_max, double* rho_min) {
+    if (!B) return fail(LB_EINVAL, "null batch");
+    std::vector<double> last(size_t(B->n) * 4);
+    cudaError_t e = cudaMemcpyAsync(last.data(), B->d_last, last.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                    B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return cuda_err(e, "batch last check");
+    for (int k = 0; k < B->n; ++k) {
+        if (du) du[k] = last[4 * k];
+        if (umax) umax[k] = last[4 * k + 1];
+        if (rho_max) rho_max[k] = last[4 * k + 2];
+        if (rho_min) rho_min[k] = last[4 * k + 3];
+    }
     return LB_OK;
 }
 

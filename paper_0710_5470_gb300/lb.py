@@ -74,6 +74,9 @@ _SIGNATURES = {
     "lb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lb_batch_run_to_steady": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_longlong, C.c_longlong,
                                          C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "lb_batch_set_reference": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double]),
+    "lb_batch_set_band": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int]),
+    "lb_batch_last_check": (C.c_int, [C.c_void_p, _DPTR, _DPTR, _DPTR, _DPTR]),
     "lb_batch_fields": (C.c_int, [C.c_void_p, C.c_int, _DPTR, _DPTR]),
     "lb_batch_populations": (C.c_int, [C.c_void_p, C.c_int, _DPTR]),
     "lb_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong),
@@ -293,6 +296,20 @@ class Batch:
         _check(self._lib.lb_batch_run_to_steady(self._h, tol, every, min_steps, max_steps, steps, status,
                                                 C.byref(total)))
         return list(steps), list(status), total.value
+
+    def set_reference(self, k: int, umax_ref: float, rho_max_ref: float = 0.0, rho_min_ref: float = 0.0):
+        """Reference steady state of instance k for the reference test
+        (lb_batch_set_reference); umax_ref = 0 clears it."""
+        _check(self._lib.lb_batch_set_reference(self._h, k, float(umax_ref), float(rho_max_ref), float(rho_min_ref)))
+
+    def set_band(self, band: float = 0.05, tol_rho: float = 1e-3, hold: int = 10):
+        _check(self._lib.lb_batch_set_band(self._h, band, tol_rho, hold))
+
+    def last_check(self):
+        """(max|du|, max|u|, max rho, min rho) per instance at its last check."""
+        out = [np.empty(self.n, dtype=np.float64) for _ in range(4)]
+        _check(self._lib.lb_batch_last_check(self._h, *(_dptr(a) for a in out)))
+        return tuple(out)
 
     def fields(self, k: int):
         d = self.instances[k]

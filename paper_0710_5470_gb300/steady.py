@@ -1,0 +1,219 @@
+"""Time to steady state of a sweep of D2Q9 drop runs, driven through the C ABI.
+
+Two ways to bring every instance of a sweep to its steady state:
+
+* ``plain``: the float64 solver one instance at a time (a batch of one per
+  run), tanh start;
+* ``fast``: every instance in one batch (one launch per step for the whole
+  sweep, CUDA-graph replay of ``every`` steps plus the check, autotuned tile),
+  a reduced storage format, and optionally the learned warm start
+  (lb_ws_* prediction of the steady density from the tanh start).
+
+Steady-state tests (the paper defines none; Sec. IV runs to a fixed time):
+``tol``: max|u(t) - u(t - every)| < tol, the float64 test; rounding of
+reduced storage keeps this quantity above any useful tol, so the
+equal-accuracy comparison uses the reference test of lb_batch_set_reference:
+for ``hold`` (10) consecutive checks, max|u| within ``band`` (5%) of the
+float64 steady max|u| and the bulk densities (max rho, min rho) within
+``tol_rho`` of the float64 steady ones, applied to both ways alike.  The
+test is blind to a translation of the drop: rounding noise of reduced
+storage moves drops slowly on the periodic lattice (a neutral mode), which
+changes no steady-state observable.
+
+Both are timed on the wall clock from the creation of the solver state to
+the last instance retired (set-up, inference and autotuning included).
+``compare`` measures how close the fast steady states are to the float64
+ones.  All arithmetic runs in the library; this module moves arrays between
+the calls and reads the clock.
+
+  python -m paper_0710_5470_gb300.steady [--count 16] [--warm]   (one JSON line)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import lb
+from . import warmstart as W
+
+
+def _set_refs(bt, refs, band, tol_rho, hold):
+    bt.set_band(band, tol_rho, hold)
+    for k, (umax, rho_max, rho_min) in enumerate(refs):
+        bt.set_reference(k, umax, rho_max, rho_min)
+
+
+def plain(instances, tol=1e-10, every=100, max_steps=200000, scheme=lb.FORCING, refs=None, band=0.05,
+          tol_rho=1e-3, hold=10, stream=None):
+    """float64, one instance per batch, tanh start; the reference test with
+    refs[k] = (umax, rho_max, rho_min) when refs is given, else the tol test.
+    Returns wall time (s, total and per instance), per-instance steps,
+    status, last-check max|u|, max rho, min rho and final (rho, u)."""
+    steps, status, final, secs, umax, rmax, rmin = [], [], [], [], [], [], []
+    t0 = time.perf_counter()
+    for k, d in enumerate(instances):
+        t1 = time.perf_counter()
+        with lb.Batch([d], W.A_VDW, W.B_VDW, scheme=scheme, storage=lb.F64, stream=stream) as bt:
+            if refs is not None:
+                _set_refs(bt, [refs[k]], band, tol_rho, hold)
+            bt.init_drops(2.0)
+            s, st, _ = bt.run_to_steady(tol=tol, every=every, max_steps=max_steps)
+            steps.append(s[0])
+            status.append(st[0])
+            _, um, hi, lo = bt.last_check()
+            umax.append(float(um[0]))
+            rmax.append(float(hi[0]))
+            rmin.append(float(lo[0]))
+            final.append(bt.fields(0))
+        secs.append(time.perf_counter() - t1)
+    return {"seconds": time.perf_counter() - t0, "instance_seconds": secs, "steps": steps, "status": status,
+            "umax": umax, "rho_max": rmax, "rho_min": rmin, "final": final}
+
+
+def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, scheme=lb.FORCING, ws=None,
+         refs=None, band=0.05, tol_rho=1e-3, hold=10, autotune_steps=5, stream=None):
+    """All instances in one batch with the given storage, tanh start or the
+    network's prediction (ws); reference test when refs is given.  Same
+    return layout as ``plain`` plus the time of the warm-start prediction."""
+    t0 = time.perf_counter()
+    with lb.Batch(instances, W.A_VDW, W.B_VDW, scheme=scheme, storage=storage, stream=stream) as bt:
+        if refs is not None:
+            _set_refs(bt, refs, band, tol_rho, hold)
+        bt.init_drops(2.0)
+        t_pred = 0.0
+        if ws is not None:
+            tp = time.perf_counter()
+            for k, d in enumerate(instances):
+                rho, u = W.predict_start(ws, bt.fields(k)[0], d, use_u=False, interface_only=True)
+                bt.init_fields(k, rho, u)
+            t_pred = time.perf_counter() - tp
+        if autotune_steps > 0:
+            bt.autotune(autotune_steps)
+        s, st, total = bt.run_to_steady(tol=tol, every=every, max_steps=max_steps)
+        seconds = time.perf_counter() - t0
+        _, um, hi, lo = bt.last_check()
+        final = [bt.fields(k) for k in range(len(instances))]
+    return {"seconds": seconds, "steps": list(s), "status": list(st), "umax": [float(v) for v in um],
+            "rho_max": [float(v) for v in hi], "rho_min": [float(v) for v in lo], "final": final,
+            "predict_seconds": t_pred, "batch_steps": total}
+
+
+def _centre(rho):
+    """Centre of the drop on the periodic lattice: argument of the first
+    Fourier mode of rho - mean(rho) along each axis (x, y)."""
+    c = []
+    for ax, n in ((1, rho.shape[1]), (0, rho.shape[0])):
+        prof = (rho - rho.mean()).sum(axis=1 - ax)
+        ph = np.angle(np.sum(prof * np.exp(2j * np.pi * np.arange(n) / n)))
+        c.append((ph % (2 * np.pi)) * n / (2 * np.pi))
+    return np.array(c)
+
+
+def compare(ref, run):
+    """Per-instance accuracy of ``run`` against ``ref`` (results of plain or
+    fast on the same instances), for the instances that converged in both
+    (None otherwise): relative error of max|u|, errors of the bulk densities
+    (max rho, min rho), the displacement of the drop centre (periodic
+    distance, sites) and the largest pointwise density difference."""
+    out = []
+    for k, ((r0, u0), (r1, u1)) in enumerate(zip(ref["final"], run["final"])):
+        if ref["status"][k] != 0 or run["status"][k] != 0:
+            out.append(None)
+            continue
+        m0 = float(np.sqrt((u0 ** 2).sum(axis=0)).max())
+        m1 = float(np.sqrt((u1 ** 2).sum(axis=0)).max())
+        d = _centre(r1) - _centre(r0)
+        n = np.array([r0.shape[1], r0.shape[0]])
+        d = (d + n / 2) % n - n / 2
+        out.append({"max_u_ref": m0, "max_u": m1, "max_u_rel_err": abs(m1 - m0) / m0,
+                    "rho_max_err": abs(float(r1.max() - r0.max())), "rho_min_err": abs(float(r1.min() - r0.min())),
+                    "shift": float(np.hypot(*d)), "rho_pointwise_err": float(np.abs(r1 - r0).max())})
+    return out
+
+
+def train_network(seeds=(1, 2, 3, 4), count=64, side=64, epochs=200, tol=1e-8, every=50, max_steps=40000):
+    """A warm-start network trained on steady states of sweeps with the given
+    seeds (sweep parameter ranges, lattices resized to side^2).  Returns the
+    network, the training time (s) and the number of training samples."""
+    from . import inputs
+    t0 = time.perf_counter()
+    inst = []
+    for s in seeds:
+        inst += W.instances_from_sweep(inputs.sweep_instances(seed=s, count=count), side=side)
+    x, t, keep, _ = W.steady_dataset(inst, tol=tol, every=every, max_steps=max_steps)
+    ws, _ = W.train(x, t, epochs=epochs, batch=16, lr=1e-3)
+    return ws, time.perf_counter() - t0, len(keep)
+
+
+def _summary(name, res, ref=None):
+    ok = [k for k, s in enumerate(res["status"]) if s == 0]
+    out = {"seconds": res["seconds"], "converged": len(ok), "instances": len(res["status"]),
+           "mean_steps": float(np.mean([res["steps"][k] for k in ok])) if ok else None}
+    if "predict_seconds" in res:
+        out["predict_seconds"] = res["predict_seconds"]
+    if ref is not None:
+        c = [x for x in compare(ref, res) if x]
+        if c:
+            for key in ("max_u_rel_err", "rho_max_err", "rho_min_err", "shift", "rho_pointwise_err"):
+                out[key + "_max"] = max(x[key] for x in c)
+    return out
+
+
+def experiment(count=16, seed=0, every=100, max_steps=200000, band=0.05, tol_rho=1e-3, hold=10, warm=False):
+    """The time-to-steady comparison on the first ``count`` instances of a
+    parameter sweep (inputs.sweep_instances(seed)): float64 runs to the tol
+    test give the reference steady states; every way is then timed with the
+    reference test on the instances whose float64 run converged."""
+    from . import inputs
+    inst_all = W.instances_from_sweep(inputs.sweep_instances(seed=seed, count=count))
+    ref_all = plain(inst_all, tol=1e-10, every=every, max_steps=max_steps)
+    ok = [k for k, s in enumerate(ref_all["status"]) if s == 0]
+    inst = [inst_all[k] for k in ok]
+    refs = [(ref_all["umax"][k], ref_all["rho_max"][k], ref_all["rho_min"][k]) for k in ok]
+    ref = {key: [ref_all[key][k] for k in ok]
+           for key in ("steps", "status", "umax", "rho_max", "rho_min", "final", "instance_seconds")}
+    ref["seconds"] = float(sum(ref["instance_seconds"]))
+    out = {"sweep": {"seed": seed, "count": count, "sites": int(sum(d["nx"] * d["ny"] for d in inst)),
+                     "converged_f64": len(ok),
+                     "unstable_f64": sum(s == 4 for s in ref_all["status"]),
+                     "not_converged_f64": sum(s == 5 for s in ref_all["status"])},
+           "test": {"tol_f64": 1e-10, "every": every, "band": band, "tol_rho": tol_rho, "hold": hold},
+           "plain_f64_tol": _summary("plain_f64_tol", ref)}
+    kw = dict(every=every, max_steps=max_steps, refs=refs, band=band, tol_rho=tol_rho, hold=hold)
+    runs = {"plain_f64_ref": plain(inst, **kw)}
+    for name, st in (("batch_f64", lb.F64), ("batch_f32", lb.F32), ("batch_f16dev", lb.F16DEV),
+                     ("batch_bf16dev", lb.BF16DEV)):
+        runs[name] = fast(inst, storage=st, **kw)
+    if warm:
+        ws, t_train, n_train = train_network()
+        runs["batch_f16dev_warm"] = fast(inst, storage=lb.F16DEV, ws=ws, **kw)
+        out["training"] = {"seconds": t_train, "samples": n_train}
+        ws.close()
+    base = runs["plain_f64_ref"]["seconds"]
+    for name, r in runs.items():
+        out[name] = _summary(name, r, ref)
+        out[name]["speedup_vs_plain_f64_ref"] = base / r["seconds"]
+        out[name]["speedup_vs_plain_f64_tol"] = ref["seconds"] / r["seconds"]
+    return out
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--count", type=int, default=16)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--every", type=int, default=100)
+    p.add_argument("--max-steps", type=int, default=200000)
+    p.add_argument("--tol-rho", type=float, default=1e-3)
+    p.add_argument("--warm", action="store_true")
+    a = p.parse_args()
+    from . import build
+    build.build()
+    lb.load_library()
+    print(json.dumps(experiment(a.count, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho, warm=a.warm)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

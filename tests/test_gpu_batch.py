@@ -98,3 +98,41 @@ def test_reduced_storage_batch_matches_single_context(storage):
         ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
         ctx.step(20)
         assert np.array_equal(ctx.get_populations(), got)
+
+
+def test_reference_test_stops_reduced_storage_at_float64_accuracy():
+    """lb_batch_set_reference: float32 instances retire once, for 10 checks,
+    max|u| is within 5% of the float64 steady max|u| and the bulk densities
+    within 1e-3 of the float64 steady ones; the last-check values agree with
+    the retired state's fields."""
+    lb = library()
+    inst = [dict(nx=32, ny=32, T=0.55, kappa=0.01, tau=1.0, radius=8.0),
+            dict(nx=24, ny=40, T=0.54, kappa=0.015, tau=0.9, radius=6.0)]
+    with lb.Batch(inst, A_VDW, B_VDW, scheme=1, storage=lb.F64) as bt:
+        bt.init_drops(2.0)
+        steps64, status64, _ = bt.run_to_steady(tol=1e-10, every=100, max_steps=100000)
+        du, umax, hi, lo = bt.last_check()
+        ref = [bt.fields(k) for k in range(len(inst))]
+    assert status64 == [0, 0] and (du < 1e-10).all()
+    for k in range(len(inst)):
+        m = np.sqrt((ref[k][1] ** 2).sum(axis=0)).max()
+        assert abs(umax[k] - m) <= 1e-12 * m
+        assert hi[k] == ref[k][0].max() and lo[k] == ref[k][0].min()
+    with lb.Batch(inst, A_VDW, B_VDW, scheme=1, storage=lb.F32) as bt:
+        with pytest.raises(lb.LBError):
+            bt.set_band(band=-1.0)
+        with pytest.raises(lb.LBError):
+            bt.set_reference(2, 1e-6)
+        bt.set_band(band=0.05, tol_rho=1e-3, hold=10)
+        for k in range(len(inst)):
+            bt.set_reference(k, umax[k], hi[k], lo[k])
+        bt.init_drops(2.0)
+        steps32, status32, _ = bt.run_to_steady(tol=1e-10, every=100, max_steps=100000)
+        _, um32, hi32, lo32 = bt.last_check()
+        got = [bt.fields(k) for k in range(len(inst))]
+    assert status32 == [0, 0]
+    for k in range(len(inst)):
+        assert abs(um32[k] - umax[k]) <= 0.05 * umax[k]
+        assert abs(hi32[k] - hi[k]) <= 1e-3 and abs(lo32[k] - lo[k]) <= 1e-3
+        assert 1000 <= steps32[k] <= 2 * steps64[k] + 1000
+        assert abs(got[k][0].max() - hi32[k]) <= 1e-12 and abs(got[k][0].min() - lo32[k]) <= 1e-12
