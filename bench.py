@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-steady", action="store_true")
     return p.parse_args()
 
 
@@ -312,6 +313,30 @@ def run_native(args):
                                             "traffic": NCU_TRAFFIC.get((fp, sname, n))},
                                "max_v": vst["max_v"]}
 
+    # time to steady state (second half of the metric): plain float64, one
+    # instance per launch, against one batch in fp16-deviation storage, both
+    # stopped by the same reference test (float64 steady max|u| within 5%,
+    # bulk densities within 1e-3, 10 consecutive checks)
+    tts = None
+    if rank == 0 and world == 1 and not args.no_steady:
+        from paper_0710_5470_gb300 import steady
+        ex = steady.experiment(count=16, seed=0, arms=("f16dev",))
+        fast_s = ex["batch_f16dev"]["seconds"]
+        tts = {"workload": "first 16 instances of the D2Q9 drop sweep seed 0 (side 64-384, T 0.50-0.56, "
+                           "kappa 0.002-0.03, tau 0.6-1.5, one centred drop, forcing scheme); the "
+                           f"{ex['sweep']['converged_f64']} whose float64 run converges "
+                           f"({ex['sweep']['unstable_f64']} unstable, {ex['sweep']['not_converged_f64']} not "
+                           "converged in 2e5 steps)",
+               "test": "max|u| within 5% and max/min rho within 1e-3 of the float64 steady values for 10 "
+                       "consecutive checks, every 100 steps",
+               "plain_f64_s": ex["plain_f64_ref"]["seconds"], "fast_s": fast_s,
+               "speedup": ex["plain_f64_ref"]["seconds"] / fast_s,
+               "fast": "one batch, fp16-deviation storage, CUDA-graph replay, autotuned tile",
+               "plain_f64_to_du_1e-10_s": ex["plain_f64_tol"]["seconds"],
+               "converged": {"plain": ex["plain_f64_ref"]["converged"], "fast": ex["batch_f16dev"]["converged"]},
+               "accuracy_fast": {k: ex["batch_f16dev"].get(k) for k in ("max_u_rel_err_max", "rho_max_err_max",
+                                                                        "rho_min_err_max")}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         edge = n
@@ -338,6 +363,7 @@ def run_native(args):
             "gpu_launches": args.steps,
             "clocks": clk,
             "variants": variants,
+            "time_to_steady": tts,
             "check": {"max_v": st["max_v"], "mass": st["mass"], "status": st["status"]},
         }
         print(json.dumps(line), flush=True)

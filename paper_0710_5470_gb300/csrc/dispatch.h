@@ -10,6 +10,11 @@ struct LbKernelSet {
     size_t smem = 0;              // dynamic shared memory of the fused step
     const void* step_fn = nullptr;
     cudaError_t (*step)(const lbk::StepArgs&, dim3 grid, cudaStream_t) = nullptr;
+    // the same step with one site per load (any nx); `step` moves two sites
+    // per load in its halo stage and needs an even nx when this flag is set
+    const void* step1_fn = nullptr;
+    cudaError_t (*step1)(const lbk::StepArgs&, dim3 grid, cudaStream_t) = nullptr;
+    bool step_pair_needs_even_nx = false;
     cudaError_t (*init_feq)(const double* rho, const double* u, const lbk::PopPtrs&, lbk::Grid3, lbk::Phys,
                             cudaStream_t) = nullptr;
     cudaError_t (*moments)(const lbk::PopPtrs&, lbk::Grid3, double* rho, double* u, cudaStream_t) = nullptr;

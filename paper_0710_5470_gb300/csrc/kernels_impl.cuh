@@ -6,9 +6,10 @@
 
 namespace lbk {
 
-// Fused step kernel of a lattice: the z-split kernel for D3Q19, the generic
-// single-plane kernel for D2Q9.
-template <class L, bool FORCING, class S, int TX, int TY>
+// Fused step kernel of a lattice: the z-split kernel for D3Q19 (PAIR: two
+// sites per stage-A load, even nx only), the generic single-plane kernel for
+// D2Q9 (PAIR ignored).
+template <class L, bool FORCING, class S, int TX, int TY, bool PAIR = false>
 struct StepKernelOf {
     using real = typename S::real;
     static constexpr bool D3 = L::D == 3;
@@ -17,12 +18,12 @@ struct StepKernelOf {
         else return StepLayout<L, FORCING, TX, TY, real>::BYTES;
     }
     static const void* fn() {
-        if constexpr (D3) return reinterpret_cast<const void*>(step_kernel3d<FORCING, S, TX, TY>);
+        if constexpr (D3) return reinterpret_cast<const void*>(step_kernel3d<FORCING, S, TX, TY, PAIR>);
         else return reinterpret_cast<const void*>(step_kernel<L, FORCING, S, TX, TY>);
     }
     static void launch(dim3 grid, cudaStream_t st, const StepArgs& a) {
         if constexpr (D3) {
-            step_kernel3d<FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(a);
+            step_kernel3d<FORCING, S, TX, TY, PAIR><<<grid, TX * TY, bytes(), st>>>(a);
         } else {
             Tile2DArgs t{a.src_base, a.dst_base, a.pitch, a.nx, a.ny, a.a, a.b, a.T, a.kappa, a.omega, a.nu,
                          a.pref, a.rsum, a.status};
@@ -34,18 +35,25 @@ struct StepKernelOf {
 template <class L, bool FORCING, class S, int TX, int TY>
 struct Launchers {
     using real = typename S::real;
-    using K = StepKernelOf<L, FORCING, S, TX, TY>;
+    // paired stage A for D3Q19 with 32-bit arithmetic (float64 is bound by its
+    // arithmetic and would spill with twice the halo registers)
+    static constexpr bool PAIRED = L::D == 3 && sizeof(real) == 4;
+    using K = StepKernelOf<L, FORCING, S, TX, TY, PAIRED>;
+    using K1 = StepKernelOf<L, FORCING, S, TX, TY, false>;       // one site per stage-A item
 
-    static cudaError_t step(const StepArgs& a, dim3 grid, cudaStream_t st) {
+    template <class KK>
+    static cudaError_t launch_step(const StepArgs& a, dim3 grid, cudaStream_t st) {
         static int attr_done = 0;
         if (!attr_done) {
-            cudaError_t e = cudaFuncSetAttribute(K::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::bytes()));
+            cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(KK::bytes()));
             if (e != cudaSuccess) return e;
             attr_done = 1;
         }
-        K::launch(grid, st, a);
+        KK::launch(grid, st, a);
         return cudaGetLastError();
     }
+    static cudaError_t step(const StepArgs& a, dim3 grid, cudaStream_t st) { return launch_step<K>(a, grid, st); }
+    static cudaError_t step1(const StepArgs& a, dim3 grid, cudaStream_t st) { return launch_step<K1>(a, grid, st); }
     static cudaError_t init_feq(const double* rho, const double* u, const PopPtrs& p, Grid3 g, Phys ph,
                                 cudaStream_t st) {
         const size_t n = size_t(g.nx) * g.ny * g.nz;
@@ -83,6 +91,9 @@ struct Launchers {
         k.smem = K::bytes();
         k.step_fn = K::fn();
         k.step = &step;
+        k.step1_fn = K1::fn();
+        k.step1 = &step1;
+        k.step_pair_needs_even_nx = PAIRED;
         k.init_feq = &init_feq;
         k.moments = &moments;
         k.mprime = &mprime;

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/lb.h: parameter validation,
 // the Maxwell construction, device buffers, and kernel launches.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -281,6 +282,12 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     c->buf_bytes = c->pitch * (elem0 + size_t(c->Q - 1) * elemi);
     c->ks = c->D == 2 ? lbk_kernels_d2q9(p->scheme, p->storage) : lbk_kernels_d3q19(p->scheme, p->storage);
     if (!c->ks.step) { delete c; return fail(LB_EINVAL, "no kernel for this combination"); }
+    // two sites per halo load need an even nx; LB_NO_PAIR selects the
+    // one-site form (same arithmetic) everywhere, for comparison
+    if (c->ks.step_pair_needs_even_nx && (p->nx % 2 != 0 || std::getenv("LB_NO_PAIR"))) {
+        c->ks.step = c->ks.step1;
+        c->ks.step_fn = c->ks.step1_fn;
+    }
 
     cudaError_t e = cudaMalloc(&c->fbuf, 2 * c->buf_bytes);
     if (e != cudaSuccess) { delete c; return fail(LB_ENOMEM, std::string("population buffers: ") + cudaGetErrorString(e)); }

@@ -19,6 +19,8 @@
 //     = -(U+(q+1) + U0(q) + U-(q-1)), U+/0/- the contributions of one plane's
 //     M' e_i to the plane above / itself / below (43 values per site).
 #pragma once
+#include <type_traits>
+
 #include "step_kernel.cuh"
 
 namespace lbk {
@@ -26,11 +28,14 @@ namespace lbk {
 template <bool FORCING, int TX, int TY, class real>
 struct Layout3D {
     static constexpr int Q = 19;
+    // density halo: 2 sites in x for both schemes (pairs of sites start on an
+    // even x), H in y (2 forcing: the divergence of M' on the tile needs the
+    // gradient on ring 1; 1 equilibrium)
     static constexpr int H = FORCING ? 2 : 1;
-    static constexpr int RX = TX + 2 * H, RY = TY + 2 * H, RN = RX * RY;
+    static constexpr int HX = 2, HY = H;
+    static constexpr int RX = TX + 2 * HX, RY = TY + 2 * HY, RN = RX * RY;
     static constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY;
     static constexpr int NT = TX * TY;
-    static constexpr int NA = (RN + NT - 1) / NT;
     static constexpr int NB = FORCING ? (SN + NT - 1) / NT : 1;
     static constexpr int LAG_C = FORCING ? 2 : 1;   // stage C trails stage A by LAG_C planes
     // rho and stash slots: planes p .. p - LAG_C are live; a barrier closes each plane
@@ -80,13 +85,41 @@ __device__ __forceinline__ void assemble(const PlaneParts<real>& lo, const Plane
     lap = real(2) * (mid.lin + hi.s + lo.s) - real(4) * mid.c;
 }
 
-template <bool FORCING, class S, int TX, int TY>
+// Sum of a[B], ..., a[E-1] as a balanced tree (short dependency chains).
+template <int B, int E, class real>
+__device__ __forceinline__ real tree_sum(const real* a) {
+    if constexpr (E - B == 1) return a[B];
+    else {
+        constexpr int M = B + (E - B) / 2;
+        return tree_sum<B, M>(a) + tree_sum<M, E>(a);
+    }
+}
+
+// Density of one site from f_0 and the deviations d_1..d_18 (Eq. 3):
+// rho = (rsum + f_0) + sum_i d_i.
+template <int Q, class real>
+__device__ __forceinline__ real site_rho(const real (&f)[Q], real rsum) {
+    return (rsum + f[0]) + tree_sum<1, Q>(f);
+}
+
+template <class real>
+__device__ __forceinline__ void st_pair(real* p, real a, real b) {
+    if constexpr (sizeof(real) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// PAIR: stage A moves two adjacent x sites per thread with 2-vector loads
+// (requires an even nx); otherwise one site per thread.
+template <bool FORCING, class S, int TX, int TY, bool PAIR>
 __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX * TY <= 256) ? 2 : 1) step_kernel3d(const StepArgs args) {
     using L = D3Q19;
     using real = typename S::real;
     using Lay = Layout3D<FORCING, TX, TY, real>;
-    constexpr int Q = 19, H = Lay::H, NT = Lay::NT;
+    constexpr int Q = 19, HX = Lay::HX, HY = Lay::HY, NT = Lay::NT;
     constexpr int RX = Lay::RX, RN = Lay::RN, SX = Lay::SX, SN = Lay::SN;
+    constexpr int W = PAIR ? 2 : 1;                 // sites per stage-A item
+    constexpr int RXW = RX / W, NIT = RN / W;       // items per region row, per region
+    constexpr int NA = (NIT + NT - 1) / NT;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* sm = reinterpret_cast<real*>(smem_raw);
@@ -107,16 +140,20 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
     const real om = real(args.omega), nu = real(args.nu);
     const real pref = real(args.pref), rsum = real(args.rsum);
 
-    int a_in[Lay::NA], a_st[Lay::NA];
+    // stage-A items: W adjacent region sites each; a_in = in-plane element
+    // index of the first (even when PAIR: x0 - HX is even and nx is even),
+    // a_st = its stash index if the item lies in the tile (items never
+    // straddle the tile edge since HX is even); rho slot index = k * W
+    int a_in[NA], a_st[NA];
 #pragma unroll
-    for (int m = 0; m < Lay::NA; ++m) {
+    for (int m = 0; m < NA; ++m) {
         const int k = tid + m * NT;
         a_in[m] = -1;
         a_st[m] = -1;
-        if (k < RN) {
-            const int rx = k % RX, ry = k / RX;
-            a_in[m] = wrapi(y0 - H + ry, ny) * nx + wrapi(x0 - H + rx, nx);
-            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY) a_st[m] = (ry - H) * TX + (rx - H);
+        if (k < NIT) {
+            const int rx = (k % RXW) * W, ry = k / RXW;
+            a_in[m] = wrapi(y0 - HY + ry, ny) * nx + wrapi(x0 - HX + rx, nx);
+            if (rx >= HX && rx < HX + TX && ry >= HY && ry < HY + TY) a_st[m] = (ry - HY) * TX + (rx - HX);
         }
     }
     // stage-B items: the tile + 1 ring (forcing) or the thread's own site
@@ -127,11 +164,11 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
             const int k = tid + m * NT;
             const int sx = k % SX, sy = k / SX;
             b_k[m] = k < SN ? k : -1;
-            b_rc[m] = (sy + H - 1) * RX + (sx + H - 1);
+            b_rc[m] = (sy + HY - 1) * RX + (sx + HX - 1);
             b_r0[m] = (k < SN && sx >= 1 && sx <= TX && sy >= 1 && sy <= TY) ? (sy - 1) * TX + (sx - 1) : -1;
         } else {
             b_k[m] = tid;
-            b_rc[m] = (ty + H) * RX + (tx + H);
+            b_rc[m] = (ty + HY) * RX + (tx + HX);
             b_r0[m] = tid;
         }
     }
@@ -153,18 +190,22 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
         if (v == vol) v = 0;
     };
 
-    typename S::raw0 r0[Lay::NA];
-    typename S::rawi ri[Lay::NA][Q - 1];
+    using R0 = std::conditional_t<PAIR, typename S::raw0x2, typename S::raw0>;
+    using RI = std::conditional_t<PAIR, typename S::rawix2, typename S::rawi>;
+    R0 r0[NA];
+    RI ri[NA][Q - 1];
     // load plane ld_off of the halo region into r0/ri, then advance ld_off
     auto issue = [&]() {
 #pragma unroll
-        for (int m = 0; m < Lay::NA; ++m) {
+        for (int m = 0; m < NA; ++m) {
             if (a_in[m] >= 0) {
                 const size_t q = size_t(ld_off + a_in[m]);
-                r0[m] = S::ld0(args.src[0], q);
+                if constexpr (PAIR) r0[m] = S::ld0x2(args.src[0], q);
+                else r0[m] = S::ld0(args.src[0], q);
                 static_for<1, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    ri[m][i - 1] = S::ldi(args.src[i], q);
+                    if constexpr (PAIR) ri[m][i - 1] = S::ldix2(args.src[i], q);
+                    else ri[m][i - 1] = S::ldi(args.src[i], q);
                 });
             }
         }
@@ -189,23 +230,36 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
             real* st_w = stash + (it % Lay::NSTASH) * Q * NT;
             const bool keep = p >= z0 && p < z1;
 #pragma unroll
-            for (int m = 0; m < Lay::NA; ++m) {
+            for (int m = 0; m < NA; ++m) {
                 if (a_in[m] >= 0) {
-                    real f[Q];               // f_0 and the deviations d_i
-                    f[0] = S::dec0(r0[m]);
-                    static_for<1, Q>([&](auto I) {
-                        constexpr int i = decltype(I)::value;
-                        f[i] = S::devi(ri[m][i - 1]);
-                    });
-                    real r = rsum;
-                    static_for<1, Q>([&](auto I) { r += f[decltype(I)::value]; });
-                    r += f[0];
-                    rho_w[tid + m * NT] = r;
-                    if (keep && a_st[m] >= 0) {
-                        static_for<0, Q>([&](auto I) {
+                    if constexpr (PAIR) {
+                        real fa[Q], fb[Q];   // f_0 and the deviations d_i of the two sites
+                        S::dec0x2(r0[m], fa[0], fb[0]);
+                        static_for<1, Q>([&](auto I) {
                             constexpr int i = decltype(I)::value;
-                            st_w[i * NT + a_st[m]] = f[i];
+                            S::devix2(ri[m][i - 1], fa[i], fb[i]);
                         });
+                        st_pair(rho_w + 2 * (tid + m * NT), site_rho(fa, rsum), site_rho(fb, rsum));
+                        if (keep && a_st[m] >= 0) {
+                            static_for<0, Q>([&](auto I) {
+                                constexpr int i = decltype(I)::value;
+                                st_pair(st_w + i * NT + a_st[m], fa[i], fb[i]);
+                            });
+                        }
+                    } else {
+                        real f[Q];           // f_0 and the deviations d_i
+                        f[0] = S::dec0(r0[m]);
+                        static_for<1, Q>([&](auto I) {
+                            constexpr int i = decltype(I)::value;
+                            f[i] = S::devi(ri[m][i - 1]);
+                        });
+                        rho_w[tid + m * NT] = site_rho(f, rsum);
+                        if (keep && a_st[m] >= 0) {
+                            static_for<0, Q>([&](auto I) {
+                                constexpr int i = decltype(I)::value;
+                                st_w[i * NT + a_st[m]] = f[i];
+                            });
+                        }
                     }
                 }
             }
@@ -320,7 +374,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                 constexpr int i = decltype(I)::value;
                 f[i] = st_r[i * NT + tid];
             });
-            const real rho = rho_s[(is % Lay::NRHO) * RN + (ty + H) * RX + (tx + H)];
+            const real rho = rho_s[(is % Lay::NRHO) * RN + (ty + HY) * RX + (tx + HX)];
             real G[3], lap;
             if constexpr (FORCING) {
                 const real* gl = gl_s + ((s - pstart) & 1) * 4 * NT;

@@ -10,6 +10,8 @@
 // contrast between the phases and stays float32.
 //
 // Populations are separate arrays (structure of arrays), one pointer each.
+// The x2 forms move two adjacent sites (even element index q, arrays
+// 256-byte aligned) with one 2-vector access.
 // The step kernels work on deviations d_i = f_i - fref_i (i >= 1; fref = 0
 // for StF64 / StF32): devi / sti read and write the stored deviation, f_0 is
 // stored as is.
@@ -23,7 +25,13 @@ struct StF64 {
     using real = double;
     using raw0 = double;   // stored type of f_0
     using rawi = double;   // stored type of f_i, i >= 1
+    using raw0x2 = double2;   // two adjacent sites (element index even)
+    using rawix2 = double2;
     static constexpr int id = 0;
+    __device__ __forceinline__ static raw0x2 ld0x2(const char* p, size_t q) { return reinterpret_cast<const double2*>(p)[q >> 1]; }
+    __device__ __forceinline__ static rawix2 ldix2(const char* p, size_t q) { return reinterpret_cast<const double2*>(p)[q >> 1]; }
+    __device__ __forceinline__ static void dec0x2(raw0x2 v, real& a, real& b) { a = v.x; b = v.y; }
+    __device__ __forceinline__ static void devix2(rawix2 v, real& a, real& b) { a = v.x; b = v.y; }
     __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const double*>(p)[idx]; }
     __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) { return reinterpret_cast<const double*>(p)[idx]; }
     __device__ __forceinline__ static real dec0(raw0 v) { return v; }
@@ -45,7 +53,13 @@ struct StF32 {
     using real = float;
     using raw0 = float;
     using rawi = float;
+    using raw0x2 = float2;
+    using rawix2 = float2;
     static constexpr int id = 1;
+    __device__ __forceinline__ static raw0x2 ld0x2(const char* p, size_t q) { return reinterpret_cast<const float2*>(p)[q >> 1]; }
+    __device__ __forceinline__ static rawix2 ldix2(const char* p, size_t q) { return reinterpret_cast<const float2*>(p)[q >> 1]; }
+    __device__ __forceinline__ static void dec0x2(raw0x2 v, real& a, real& b) { a = v.x; b = v.y; }
+    __device__ __forceinline__ static void devix2(rawix2 v, real& a, real& b) { a = v.x; b = v.y; }
     __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
     __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
     __device__ __forceinline__ static real dec0(raw0 v) { return v; }
@@ -67,7 +81,16 @@ struct StF16 {
     using real = float;
     using raw0 = float;
     using rawi = __half;
+    using raw0x2 = float2;
+    using rawix2 = __half2;
     static constexpr int id = 2;
+    __device__ __forceinline__ static raw0x2 ld0x2(const char* p, size_t q) { return reinterpret_cast<const float2*>(p)[q >> 1]; }
+    __device__ __forceinline__ static rawix2 ldix2(const char* p, size_t q) { return reinterpret_cast<const __half2*>(p)[q >> 1]; }
+    __device__ __forceinline__ static void dec0x2(raw0x2 v, real& a, real& b) { a = v.x; b = v.y; }
+    __device__ __forceinline__ static void devix2(rawix2 v, real& a, real& b) {
+        a = __low2float(v);
+        b = __high2float(v);
+    }
     __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
     __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) { return reinterpret_cast<const __half*>(p)[idx]; }
     __device__ __forceinline__ static real dec0(raw0 v) { return v; }
@@ -98,7 +121,18 @@ struct StBF16 {
     using real = float;
     using raw0 = float;
     using rawi = __nv_bfloat16;
+    using raw0x2 = float2;
+    using rawix2 = __nv_bfloat162;
     static constexpr int id = 3;
+    __device__ __forceinline__ static raw0x2 ld0x2(const char* p, size_t q) { return reinterpret_cast<const float2*>(p)[q >> 1]; }
+    __device__ __forceinline__ static rawix2 ldix2(const char* p, size_t q) {
+        return reinterpret_cast<const __nv_bfloat162*>(p)[q >> 1];
+    }
+    __device__ __forceinline__ static void dec0x2(raw0x2 v, real& a, real& b) { a = v.x; b = v.y; }
+    __device__ __forceinline__ static void devix2(rawix2 v, real& a, real& b) {
+        a = __low2float(v);
+        b = __high2float(v);
+    }
     __device__ __forceinline__ static raw0 ld0(const char* p, size_t idx) { return reinterpret_cast<const float*>(p)[idx]; }
     __device__ __forceinline__ static rawi ldi(const char* p, size_t idx) {
         return reinterpret_cast<const __nv_bfloat16*>(p)[idx];

@@ -162,7 +162,11 @@ def _summary(name, res, ref=None):
     return out
 
 
-def experiment(count=16, seed=0, every=100, max_steps=200000, band=0.05, tol_rho=1e-3, hold=10, warm=False):
+ARMS = {"f64": lb.F64, "f32": lb.F32, "f16dev": lb.F16DEV, "bf16dev": lb.BF16DEV}
+
+
+def experiment(count=16, seed=0, every=100, max_steps=200000, band=0.05, tol_rho=1e-3, hold=10, warm=False,
+               arms=("f64", "f32", "f16dev", "bf16dev")):
     """The time-to-steady comparison on the first ``count`` instances of a
     parameter sweep (inputs.sweep_instances(seed)): float64 runs to the tol
     test give the reference steady states; every way is then timed with the
@@ -184,9 +188,8 @@ def experiment(count=16, seed=0, every=100, max_steps=200000, band=0.05, tol_rho
            "plain_f64_tol": _summary("plain_f64_tol", ref)}
     kw = dict(every=every, max_steps=max_steps, refs=refs, band=band, tol_rho=tol_rho, hold=hold)
     runs = {"plain_f64_ref": plain(inst, **kw)}
-    for name, st in (("batch_f64", lb.F64), ("batch_f32", lb.F32), ("batch_f16dev", lb.F16DEV),
-                     ("batch_bf16dev", lb.BF16DEV)):
-        runs[name] = fast(inst, storage=st, **kw)
+    for a in arms:
+        runs["batch_" + a] = fast(inst, storage=ARMS[a], **kw)
     if warm:
         ws, t_train, n_train = train_network()
         runs["batch_f16dev_warm"] = fast(inst, storage=lb.F16DEV, ws=ws, **kw)
