@@ -66,7 +66,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=50)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--storage", default="f16dev", choices=list(BYTES_POP))
-    p.add_argument("--n", type=int, default=WORKLOAD["n"])
+    p.add_argument("--edge", type=int, default=WORKLOAD["n"], help="lattice edge (default 128)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
@@ -155,6 +155,13 @@ def barrier(dist):
         dist.barrier()
 
 
+def whole_job(dist, world: int, sites_per_rank: int, steps: int, ms_local: float):
+    """Slowest rank's time (ms) and the whole-job MLUPS: every rank advances
+    its own replica of sites_per_rank sites by `steps` steps."""
+    ms = reduce_max(dist, ms_local)
+    return ms, sites_per_rank * steps * world / (ms / 1e3) / 1e6
+
+
 def oracle_sample(n_edge: int, steps: int):
     """FP64 oracle on an n_edge^3 periodic box holding the same drop scaled to
     the box (R = 30/128 of the edge): returns (MLUPS, seconds, sites*steps)."""
@@ -181,7 +188,7 @@ def run_reference(args):
     # stays within about two minutes of host time
     budget = 120.0 / max(1, args.steps + args.warmup)
     rate = 0.25e6                                     # oracle LU/s, measured order of magnitude
-    edge = int(max(8, min(args.n, round((budget * rate) ** (1 / 3)))))
+    edge = int(max(8, min(args.edge, round((budget * rate) ** (1 / 3)))))
     from oracle import lb_oracle as O
     m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme="forcing")
     rl, rg = O.coexistence(A_VDW, B_VDW, WORKLOAD["T"])
@@ -242,7 +249,7 @@ def run_native(args):
     if rank != 0:
         build.build()
     lb.load_library()
-    n = args.n
+    n = args.edge
     sites = n ** 3
     stream = torch.cuda.current_stream()
     peaks = measured_peaks()
@@ -259,8 +266,7 @@ def run_native(args):
     clk = clocks.stop()
     ctx.synchronize()
     st = ctx.stats()
-    ms = reduce_max(dist, ms_local)
-    mlups = sites * args.steps * world / (ms / 1e3) / 1e6
+    ms, mlups = whole_job(dist, world, sites, args.steps, ms_local)
 
     # roofline of the fused step kernel (the only kernel in the timed region):
     # algorithmic bytes per launch / average launch duration
