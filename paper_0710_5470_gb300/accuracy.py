@@ -1,0 +1,68 @@
+"""Accuracy of the reduced storage formats on the D3Q19 drop, driven through the C ABI.
+
+Runs the same drop (tanh start, forcing scheme) for the same number of
+steps in float64 and in each reduced format, and compares the spurious
+velocity max|v| (v = u + g/(2 rho), Eq. 40), the velocity field and the
+density field with the float64 run.  The float64 path is the one checked
+against the oracle to 1e-12 per step on small lattices; at 128^3 it stands
+in for the oracle, which would need hours per 1000 steps.
+
+  python -m paper_0710_5470_gb300.accuracy [--edge 128] [--steps 10000]   (one JSON line)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import lb
+
+A_VDW, B_VDW = 9.0 / 49.0, 2.0 / 21.0
+
+
+def run(storage, edge=128, steps=10000, T=0.55, kappa=0.01, tau=1.0, radius=None, width=2.0):
+    """(rho, v, seconds) after `steps` steps of the centred drop in the given storage."""
+    R = 30.0 * edge / 128 if radius is None else radius
+    with lb.Context(lb.D3Q19, (edge,) * 3, A_VDW, B_VDW, T, kappa, tau, scheme=lb.FORCING,
+                    storage=lb.STORAGE_NAMES[storage]) as ctx:
+        ctx.init_drops([(edge / 2,) * 3], [R], width)
+        t0 = time.perf_counter()
+        ctx.step(steps)
+        ctx.synchronize()
+        dt = time.perf_counter() - t0
+        rho, _, v = ctx.fields()
+    return rho, v, dt
+
+
+def storage_accuracy(edge=128, steps=10000, storages=("f32", "f16dev", "bf16dev")):
+    rho0, v0, dt0 = run("f64", edge, steps)
+    vmag0 = np.sqrt((v0 ** 2).sum(axis=0))
+    out = {"workload": f"D3Q19 {edge}^3, one centred drop R={30.0 * edge / 128:g}, forcing, T=0.55, kappa=0.01, "
+                       f"tau=1.0, {steps} steps from the tanh start",
+           "f64": {"max_v": float(vmag0.max()), "seconds": dt0}}
+    for s in storages:
+        rho, v, dt = run(s, edge, steps)
+        vmag = np.sqrt((v ** 2).sum(axis=0))
+        out[s] = {"max_v": float(vmag.max()), "seconds": dt,
+                  "max_v_rel_err": float(abs(vmag.max() - vmag0.max()) / vmag0.max()),
+                  "v_field_err_rel": float(np.abs(v - v0).max() / vmag0.max()),
+                  "rho_max_err": float(np.abs(rho - rho0).max()),
+                  "rho_bulk_err": max(abs(float(rho.max() - rho0.max())), abs(float(rho.min() - rho0.min())))}
+    return out
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--edge", type=int, default=128)
+    p.add_argument("--steps", type=int, default=10000)
+    a = p.parse_args()
+    from . import build
+    build.build()
+    lb.load_library()
+    print(json.dumps(storage_accuracy(a.edge, a.steps)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
