@@ -41,14 +41,50 @@ struct Layout3D {
     // rho and stash slots: planes p .. p - LAG_C are live; a barrier closes each plane
     static constexpr int NRHO = 3;
     static constexpr int NSTASH = FORCING ? 3 : 2;
+    static constexpr int al4(int x) { return (x + 3) / 4 * 4; }
     static constexpr int OFF_RHO = 0;
-    static constexpr int OFF_STASH = OFF_RHO + NRHO * RN;
-    static constexpr int OFF_MP = OFF_STASH + NSTASH * Q * NT;
-    static constexpr int OFF_G = OFF_MP + (FORCING ? 6 * SN : 0);
+    // stash: the tile's populations, [slot][population][site] (a site-major
+    // layout would let stage C read a site with 128-bit loads, but the paired
+    // stage-A writes then conflict on banks: measured slower)
+    static constexpr int OFF_STASH = al4(OFF_RHO + NRHO * RN);
+    // M' of one plane on the tile + 1 ring: (Mxx, Mxy, Mxz, Myy) per site, then (Myz, Mzz) per site
+    static constexpr int OFF_MP = al4(OFF_STASH + NSTASH * Q * NT);
+    // G and the Laplacian of the tile for two planes: (G_x, G_y, G_z, lap) per site
+    static constexpr int OFF_G = al4(OFF_MP + (FORCING ? 6 * SN : 0));
     static constexpr int TOTAL = OFF_G + (FORCING ? 2 * 4 * NT : 0);
     static constexpr size_t BYTES = size_t(TOTAL) * sizeof(real);
 };
 
+// 4- and 2-vectors of reals in shared memory (16-byte / 8- or 16-byte aligned).
+template <class real>
+__device__ __forceinline__ void st4(real* p, real a, real b, real c, real d) {
+    if constexpr (sizeof(real) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+        reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+    }
+}
+template <class real>
+__device__ __forceinline__ void ld4(const real* p, real& a, real& b, real& c, real& d) {
+    if constexpr (sizeof(real) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        a = v.x; b = v.y; c = v.z; d = v.w;
+    } else {
+        const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+        a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+    }
+}
+template <class real>
+__device__ __forceinline__ void ld2(const real* p, real& a, real& b) {
+    if constexpr (sizeof(real) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x; b = v.y;
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x; b = v.y;
+    }
+}
 // Per-plane parts of the gradient / Laplacian stencil at one site.
 template <class real>
 struct PlaneParts {
@@ -125,8 +161,9 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
     real* sm = reinterpret_cast<real*>(smem_raw);
     real* rho_s = sm + Lay::OFF_RHO;
     real* stash = sm + Lay::OFF_STASH;
-    real* mp_s = sm + Lay::OFF_MP;     // M' of one plane on the tile + 1 ring: [comp][SN]
-    real* gl_s = sm + Lay::OFF_G;      // G, lap of the tile for two planes: [slot][4][NT]
+    real* mpA = sm + Lay::OFF_MP;              // (Mxx, Mxy, Mxz, Myy) per ring-1 site
+    real* mpB = sm + Lay::OFF_MP + 4 * SN;     // (Myz, Mzz) per ring-1 site
+    real* gl_s = sm + Lay::OFF_G;              // [slot][site](G_x, G_y, G_z, lap)
 
     const int nx = args.nx, ny = args.ny, nz = args.nz;
     const int tid = threadIdx.x;
@@ -283,18 +320,12 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                         const real g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
                         const real hk = real(0.5) * pk * g2;
                         const int k = b_k[m];
-                        mp_s[0 * SN + k] = pk * G[0] * G[0] - hk;
-                        mp_s[1 * SN + k] = pk * G[1] * G[1] - hk;
-                        mp_s[2 * SN + k] = pk * G[2] * G[2] - hk;
-                        mp_s[3 * SN + k] = pk * G[0] * G[1];
-                        mp_s[4 * SN + k] = pk * G[1] * G[2];
-                        mp_s[5 * SN + k] = pk * G[0] * G[2];
+                        st4(mpA + 4 * k, pk * G[0] * G[0] - hk, pk * G[0] * G[1], pk * G[0] * G[2],
+                            pk * G[1] * G[1] - hk);
+                        st_pair(mpB + 2 * k, pk * G[1] * G[2], pk * G[2] * G[2] - hk);
                         if (b_r0[m] >= 0) {
                             real* gl = gl_s + ((q - pstart) & 1) * 4 * NT;
-                            gl[0 * NT + b_r0[m]] = G[0];
-                            gl[1 * NT + b_r0[m]] = G[1];
-                            gl[2 * NT + b_r0[m]] = G[2];
-                            gl[3 * NT + b_r0[m]] = lap;
+                            st4(gl + 4 * b_r0[m], G[0], G[1], G[2], lap);
                         }
                     } else {
                         Geq[0] = G[0];
@@ -314,37 +345,37 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
         if constexpr (FORCING) {
             if (assemble_q) {
                 const int kc = (ty + 1) * SX + (tx + 1);
-                const real* Mxx = mp_s;
-                const real* Myy = mp_s + SN;
-                const real* Mzz = mp_s + 2 * SN;
-                const real* Mxy = mp_s + 3 * SN;
-                const real* Myz = mp_s + 4 * SN;
-                const real* Mxz = mp_s + 5 * SN;
                 real sp[3] = {0, 0, 0}, sz[3] = {0, 0, 0}, se[3] = {0, 0, 0};
+                real xx, xy, xz, yy, yz, zz;
 #pragma unroll
                 for (int sgn = -1; sgn <= 1; sgn += 2) {
                     const int kx = kc + sgn, ky = kc + sgn * SX;
                     const real s = real(sgn);
                     // x faces: s (Mxx, Mxy, Mxz); z parts (Mxz, Myz, Mzz)
-                    const real axx = Mxx[kx], axy = Mxy[kx], axz = Mxz[kx], ayz = Myz[kx], azz = Mzz[kx];
-                    sp[0] += s * axx; sp[1] += s * axy; sp[2] += s * axz;
-                    sz[0] += axz; sz[1] += ayz; sz[2] += azz;
+                    ld4(mpA + 4 * kx, xx, xy, xz, yy);
+                    ld2(mpB + 2 * kx, yz, zz);
+                    sp[0] += s * xx; sp[1] += s * xy; sp[2] += s * xz;
+                    sz[0] += xz; sz[1] += yz; sz[2] += zz;
                     // y faces: s (Mxy, Myy, Myz)
-                    const real bxy = Mxy[ky], byy = Myy[ky], byz = Myz[ky], bxz = Mxz[ky], bzz = Mzz[ky];
-                    sp[0] += s * bxy; sp[1] += s * byy; sp[2] += s * byz;
-                    sz[0] += bxz; sz[1] += byz; sz[2] += bzz;
+                    ld4(mpA + 4 * ky, xx, xy, xz, yy);
+                    ld2(mpB + 2 * ky, yz, zz);
+                    sp[0] += s * xy; sp[1] += s * yy; sp[2] += s * yz;
+                    sz[0] += xz; sz[1] += yz; sz[2] += zz;
                     // xy diagonals (sx = sgn, sy = +-1)
 #pragma unroll
                     for (int sgy = -1; sgy <= 1; sgy += 2) {
                         const int ke = kc + sgn + sgy * SX;
                         const real ty_ = real(sgy);
-                        const real exx = Mxx[ke], exy = Mxy[ke], eyy = Myy[ke], exz = Mxz[ke], eyz = Myz[ke];
-                        se[0] += s * exx + ty_ * exy;
-                        se[1] += s * exy + ty_ * eyy;
-                        se[2] += s * exz + ty_ * eyz;
+                        ld4(mpA + 4 * ke, xx, xy, xz, yy);
+                        ld2(mpB + 2 * ke, yz, zz);
+                        se[0] += s * xx + ty_ * xy;
+                        se[1] += s * xy + ty_ * yy;
+                        se[2] += s * xz + ty_ * yz;
                     }
                 }
-                const real zc[3] = {Mxz[kc], Myz[kc], Mzz[kc]};
+                ld4(mpA + 4 * kc, xx, xy, xz, yy);
+                ld2(mpB + 2 * kc, yz, zz);
+                const real zc[3] = {xz, yz, zz};
                 const real sixth = real(1) / real(6), twelfth = real(1) / real(12);
                 real up[3], u0[3], um[3];
 #pragma unroll
@@ -378,10 +409,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
             real G[3], lap;
             if constexpr (FORCING) {
                 const real* gl = gl_s + ((s - pstart) & 1) * 4 * NT;
-                G[0] = gl[tid];
-                G[1] = gl[NT + tid];
-                G[2] = gl[2 * NT + tid];
-                lap = gl[3 * NT + tid];
+                ld4(gl + 4 * tid, G[0], G[1], G[2], lap);
             } else {
                 G[0] = Geq[0];
                 G[1] = Geq[1];
