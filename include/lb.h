@@ -149,6 +149,24 @@ lb_status lb_fields(lb_ctx* ctx, double* rho, double* u, double* v);
 /* float64 reductions of the current state (see lb_stats).  Synchronises. */
 lb_status lb_stats_get(lb_ctx* ctx, lb_stats* out);
 
+/* Free parameters of the D2Q9 model (Sec. III, Eq. 16): the diagonal weights w^p_{5-8} (pressure),
+ * w^t_{5-8} (interface term) and w^xx_{5-8} (M term) of the equilibrium, and the diagonal
+ * coefficients B of the gradient stencil (Eq. 10), D of the Laplacian (Eq. 11) and F of the force
+ * stencil (Eq. 28).  The other weights follow from the constraints after Eqs. 14-15 and from
+ * 2A + 4B = 1, C + 2D = 1, 2E + 4F = 1.  The optimum of Sec. III is 1/12, 1/12, -1/24, 1/12, 1/6,
+ * 1/12 (what the fused kernels hard-wire); other values give the scans of Fig. 2 and the prior-art
+ * choices of Sec. III. */
+typedef struct {
+    double wp58, wt58, wxx58, B, D, F;
+} lb_free_params;
+
+/* Run a D2Q9 float64 context with these free parameters: later lb_init_drops / lb_init_fields,
+ * lb_step and the v of lb_fields / lb_stats_get use them, through plain float64 kernels (three
+ * launches per step; for parameter studies, not for throughput).  NULL returns the context to
+ * the fused kernels.  LB_EINVAL for another lattice or storage or a non-finite value; the first
+ * call allocates 6 float64 per site of work arrays. */
+lb_status lb_set_free_params(lb_ctx* ctx, const lb_free_params* params);
+
 /* Number of sites N and populations Q of the context. */
 lb_status lb_shape(const lb_ctx* ctx, long long* n_sites, int* q);
 

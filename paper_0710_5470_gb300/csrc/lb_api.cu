@@ -9,6 +9,7 @@
 
 #include "../../include/lb.h"
 #include "dispatch.h"
+#include "param2d.h"
 
 namespace {
 
@@ -124,6 +125,12 @@ struct lb_ctx {
     double* w_part = nullptr;
     int stat_blocks = 0;
     double* w_io = nullptr;   // Q*N staging for population import/export
+    // run-time free parameters (lb_set_free_params): D2Q9 float64 only
+    bool free_params = false;
+    lbk::Free2D fw{};
+    double* p2_rho = nullptr;   // N
+    double* p2_gl = nullptr;    // 3N: d_x rho, d_y rho, lap rho
+    double* p2_mp = nullptr;    // 2N: M'_xx, M'_xy
 };
 
 namespace {
@@ -151,6 +158,12 @@ lbk::Grid3 grid3(const lb_ctx* c) { return lbk::Grid3{c->p.nx, c->p.ny, c->p.nz}
 lbk::Phys phys(const lb_ctx* c) {
     return lbk::Phys{c->p.a, c->p.b, c->p.T, c->p.kappa, (c->p.tau - 0.5) / 3.0};
 }
+
+lbk::Phys2 phys2(const lb_ctx* c) {
+    return lbk::Phys2{c->p.a, c->p.b, c->p.T, c->p.kappa, 1.0 / c->p.tau, (c->p.tau - 0.5) / 3.0};
+}
+
+double* pop_base(lb_ctx* c, int buf) { return reinterpret_cast<double*>(c->fbuf + size_t(buf) * c->buf_bytes); }
 
 lb_status check_ctx(lb_ctx* c) {
     if (!c) return fail(LB_EINVAL, "null context");
@@ -207,7 +220,11 @@ lb_status compute_fields(lb_ctx* c, bool need_v) {
     const lbk::PopPtrs src = pop_ptrs(c, c->cur);
     cudaError_t e = c->ks.moments(src, grid3(c), c->w_rho, c->w_u, c->stream);
     if (e != cudaSuccess) return record(c, e, "moments");
-    if (need_v && c->p.scheme == LB_SCHEME_FORCING) {
+    if (need_v && c->p.scheme == LB_SCHEME_FORCING && c->free_params) {
+        e = lbk::free2d_velocity_v(c->fw, c->p.kappa, c->w_rho, c->w_u, c->p.nx, c->p.ny, c->p2_gl, c->p2_mp,
+                                   c->w_v, c->stream);
+        if (e != cudaSuccess) return record(c, e, "body force");
+    } else if (need_v && c->p.scheme == LB_SCHEME_FORCING) {
         e = c->ks.mprime(c->w_rho, grid3(c), c->p.kappa, c->w_mp, c->stream);
         if (e == cudaSuccess) e = c->ks.velocity_v(c->w_rho, c->w_u, c->w_mp, grid3(c), c->w_v, c->stream);
         if (e != cudaSuccess) return record(c, e, "body force");
@@ -334,7 +351,34 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->w_mp);
     cudaFree(c->w_part);
     cudaFree(c->w_io);
+    cudaFree(c->p2_rho);
+    cudaFree(c->p2_gl);
+    cudaFree(c->p2_mp);
     delete c;
+    return LB_OK;
+}
+
+lb_status lb_set_free_params(lb_ctx* c, const lb_free_params* fp) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!fp) {
+        c->free_params = false;
+        return LB_OK;
+    }
+    if (c->p.lattice != LB_D2Q9 || c->p.storage != LB_F64)
+        return fail(LB_EINVAL, "free parameters need a D2Q9 context with float64 storage");
+    const double v[6] = {fp->wp58, fp->wt58, fp->wxx58, fp->B, fp->D, fp->F};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(LB_EINVAL, "free parameters must be finite");
+    if (!c->p2_rho) {
+        cudaError_t e;
+        if ((e = cudaMalloc(&c->p2_rho, c->N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&c->p2_gl, 3 * c->N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&c->p2_mp, 2 * c->N * sizeof(double))) != cudaSuccess)
+            return fail(LB_ENOMEM, std::string("free-parameter work arrays: ") + cudaGetErrorString(e));
+    }
+    c->fw = lbk::free2d_weights(fp->wp58, fp->wt58, fp->wxx58, fp->B, fp->D, fp->F);
+    c->free_params = true;
     return LB_OK;
 }
 
@@ -362,7 +406,11 @@ lb_status lb_device_state(lb_ctx* c, void** dptr, size_t* bytes) {
 
 static lb_status init_from_device_rho(lb_ctx* c, const double* d_rho, const double* d_u) {
     const lbk::PopPtrs dst = pop_ptrs(c, c->cur);
-    cudaError_t e = c->ks.init_feq(d_rho, d_u, dst, grid3(c), phys(c), c->stream);
+    cudaError_t e = c->free_params
+                        ? lbk::free2d_init(c->fw, phys2(c), c->p.scheme == LB_SCHEME_FORCING, pop_base(c, c->cur),
+                                           (long long)c->pitch, c->p.nx, c->p.ny, d_rho, d_u, c->p2_gl, c->p2_mp,
+                                           c->stream)
+                        : c->ks.init_feq(d_rho, d_u, dst, grid3(c), phys(c), c->stream);
     if (e != cudaSuccess) return record(c, e, "init_feq");
     e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return record(c, e, "status reset");
@@ -471,7 +519,11 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
         a.src_base = a.src[0];
         a.dst_base = a.dst[0];
         a.pitch = (long long)c->pitch;
-        cudaError_t e = c->ks.step(a, c->grid, c->stream);
+        cudaError_t e = c->free_params
+                            ? lbk::free2d_step(c->fw, phys2(c), c->p.scheme == LB_SCHEME_FORCING, pop_base(c, c->cur),
+                                               pop_base(c, 1 - c->cur), (long long)c->pitch, c->p.nx, c->p.ny,
+                                               c->p2_rho, c->p2_gl, c->p2_mp, c->d_status, c->stream)
+                            : c->ks.step(a, c->grid, c->stream);
         if (e != cudaSuccess) return record(c, e, "step kernel");
         c->cur = 1 - c->cur;
         ++c->step;

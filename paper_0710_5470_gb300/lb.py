@@ -28,6 +28,14 @@ class LBError(RuntimeError):
         self.status = status
 
 
+class lb_free_params(C.Structure):
+    _fields_ = [("wp58", C.c_double), ("wt58", C.c_double), ("wxx58", C.c_double), ("B", C.c_double),
+                ("D", C.c_double), ("F", C.c_double)]
+
+
+OPTIMUM_FREE = dict(wp58=1 / 12, wt58=1 / 12, wxx58=-1 / 24, B=1 / 12, D=1 / 6, F=1 / 12)
+
+
 class lb_params(C.Structure):
     _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("a", C.c_double), ("b", C.c_double), ("T", C.c_double), ("kappa", C.c_double),
@@ -64,6 +72,7 @@ _SIGNATURES = {
     "lb_fields": (C.c_int, [C.c_void_p, _DPTR, _DPTR, _DPTR]),
     "lb_stats_get": (C.c_int, [C.c_void_p, C.POINTER(lb_stats)]),
     "lb_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+    "lb_set_free_params": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lb_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
     "lb_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(lb_instance),
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -230,6 +239,19 @@ class Context:
         for a, k in ((rho, 1), (u, self.dim), (v, self.dim)):
             assert a is None or (a.dtype == np.float64 and a.size == k * self.n and a.flags["C_CONTIGUOUS"])
         _check(self._lib.lb_fields(self._h, _dptr(rho), _dptr(u), _dptr(v)))
+
+    def set_free_params(self, **kw):
+        """lb_set_free_params with the given values (others at the optimum)."""
+        vals = dict(OPTIMUM_FREE)
+        unknown = set(kw) - set(vals)
+        if unknown:
+            raise TypeError(f"unknown free parameters {sorted(unknown)}")
+        vals.update(kw)
+        fp = lb_free_params(**vals)
+        _check(self._lib.lb_set_free_params(self._h, C.byref(fp)))
+
+    def clear_free_params(self):
+        _check(self._lib.lb_set_free_params(self._h, None))
 
     def stats(self) -> dict:
         s = lb_stats()

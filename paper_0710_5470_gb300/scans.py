@@ -1,0 +1,113 @@
+"""Spurious velocity scans of Secs. IV-V (Figs. 2 and 3), driven through the C ABI.
+
+Fig. 2: each free parameter of the D2Q9 model (w^p_{5-8}, w^t_{5-8},
+w^xx_{5-8}, B, D; lb_set_free_params) is varied alone, the others at the
+optimum of Sec. III, and the spurious velocity max|u| of the equilibrium
+scheme is recorded.  The paper scans quasi-statically; here each value is
+a run of its own from the tanh start (same 10^4 steps).
+
+The paper's drop (D2Q9 100^2, R = 25 at the centre, T = 0.56, kappa = 0.025,
+tanh start of width 2) is run for 10^4 steps at each relaxation time, in
+float64, with the equilibrium scheme (Sec. II-IV, spurious velocity max|u|)
+and with the forcing scheme (Sec. VI, max|v|, v = u + g/(2 rho), Eq. 40).
+Beside each point: the factor S(tau) = tau - 6 tau^2 + 6 tau^3 (Eq. 26) that
+multiplies the O(d^3) stencil errors, zero at tau = 1/2 + 1/(2 sqrt 3).
+
+  python -m paper_0710_5470_gb300.scans tau|fig2 [--steps 10000]   (one JSON line)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+from . import lb
+
+A_VDW, B_VDW = 9.0 / 49.0, 2.0 / 21.0
+PAPER_DROP = dict(n=100, R=25.0, T=0.56, kappa=0.025, width=2.0)
+TAUS = (0.55, 0.6, 0.65, 0.7, 0.75, 0.789, 0.85, 0.9, 1.0, 1.1, 1.25, 1.5, 1.75, 2.0)
+
+
+def S(tau: float) -> float:
+    """Eq. 26: (1/tau) sum_i i^3 z^(i-1), z = 1 - 1/tau."""
+    return tau - 6 * tau ** 2 + 6 * tau ** 3
+
+
+def spurious_velocity(scheme: int, tau: float, steps: int = 10000, drop=PAPER_DROP, storage=lb.F64) -> dict:
+    """max|u| and max|v| of the drop after `steps` steps; spurious = None
+    when the run went unstable (LB_EUNSTABLE)."""
+    n = drop["n"]
+    with lb.Context(lb.D2Q9, (n, n), A_VDW, B_VDW, drop["T"], drop["kappa"], tau, scheme=scheme,
+                    storage=storage) as ctx:
+        ctx.init_drops([(n / 2, n / 2)], [drop["R"]], drop["width"])
+        ctx.step(steps)
+        try:
+            st = ctx.stats()
+        except lb.LBError as e:
+            return {"tau": tau, "max_u": None, "max_v": None, "status": e.status, "spurious": None}
+    return {"tau": tau, "max_u": st["max_u"], "max_v": st["max_v"], "status": st["status"],
+            "spurious": st["max_u"] if scheme == lb.EQUILIBRIUM else st["max_v"]}
+
+
+OPTIMUM = dict(lb.OPTIMUM_FREE)
+FIG2 = {
+    "wp58": [0.0, 1 / 48, 1 / 24, 1 / 16, 1 / 12, 5 / 48, 1 / 8, 7 / 48, 1 / 6],
+    "wt58": [0.0, 1 / 48, 1 / 24, 1 / 16, 1 / 12, 5 / 48, 1 / 8, 7 / 48, 1 / 6],
+    "wxx58": [-1 / 12, -5 / 72, -1 / 18, -1 / 24, -1 / 36, -1 / 72, 0.0],
+    "B": [0.0, 1 / 48, 1 / 24, 1 / 16, 1 / 12, 5 / 48, 1 / 8, 7 / 48],
+    "D": [1 / 12, 1 / 8, 1 / 6, 5 / 24, 1 / 4],
+}
+
+
+def free_param_point(param: str, value: float, scheme: int = lb.EQUILIBRIUM, steps: int = 10000, tau: float = 1.0,
+                     drop=PAPER_DROP) -> dict:
+    """Spurious velocity with one free parameter changed from the optimum."""
+    n = drop["n"]
+    with lb.Context(lb.D2Q9, (n, n), A_VDW, B_VDW, drop["T"], drop["kappa"], tau, scheme=scheme,
+                    storage=lb.F64) as ctx:
+        ctx.set_free_params(**{param: value})
+        ctx.init_drops([(n / 2, n / 2)], [drop["R"]], drop["width"])
+        ctx.step(steps)
+        try:
+            st = ctx.stats()
+        except lb.LBError as e:
+            return {"value": value, "spurious": None, "status": e.status}
+    return {"value": value, "spurious": st["max_u"] if scheme == lb.EQUILIBRIUM else st["max_v"],
+            "status": st["status"]}
+
+
+def fig2_scans(scans=FIG2, steps: int = 10000) -> dict:
+    out = {"drop": dict(PAPER_DROP), "steps": steps, "optimum": OPTIMUM, "scans": {}}
+    for param, values in scans.items():
+        pts = [free_param_point(param, v, steps=steps) for v in values]
+        ok = [p for p in pts if p["spurious"] is not None]
+        best = min(ok, key=lambda p: p["spurious"])["value"] if ok else None
+        out["scans"][param] = {"points": pts, "argmin": best, "predicted": OPTIMUM[param]}
+    return out
+
+
+def tau_sweep(taus=TAUS, steps: int = 10000) -> dict:
+    out = {"drop": dict(PAPER_DROP), "steps": steps, "points": []}
+    for t in taus:
+        e = spurious_velocity(lb.EQUILIBRIUM, t, steps)
+        f = spurious_velocity(lb.FORCING, t, steps)
+        out["points"].append({"tau": t, "S": S(t), "equilibrium": e["spurious"], "forcing": f["spurious"],
+                              "status": [e["status"], f["status"]]})
+    out["S_zero"] = 0.5 + 0.5 / math.sqrt(3.0)
+    return out
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("what", choices=["tau", "fig2"])
+    p.add_argument("--steps", type=int, default=10000)
+    a = p.parse_args()
+    from . import build
+    build.build()
+    lb.load_library()
+    res = tau_sweep(steps=a.steps) if a.what == "tau" else fig2_scans(steps=a.steps)
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,48 @@
+"""The paper's parameter scans (Figs. 2 and 3) on the GPU, float64.
+
+Fig. 2 (Sec. IV): with the other parameters at the optimum of Sec. III, the
+spurious velocity of the equilibrium scheme is smallest at the predicted
+value of each free parameter (w^p_{5-8} = w^t_{5-8} = 1/12, w^xx_{5-8} =
+-1/24, B = 1/12, D = 1/6), and the simple gradient (B = 0) gives a spurious
+velocity ~10 times larger.  Fig. 3 (Sec. V, VI): for the equilibrium scheme
+the spurious velocity grows with tau beyond tau ~ 0.8 (the factor S of
+Eq. 26); the forcing scheme stays below it and grows more slowly.
+The paper's drop: 100^2, R = 25, T = 0.56, kappa = 0.025, 10^4 steps.
+"""
+import pytest
+
+from tests.helpers import library
+
+pytestmark = pytest.mark.gpu
+
+STEP = {"wp58": 1 / 48, "wt58": 1 / 48, "wxx58": 1 / 72, "B": 1 / 48, "D": 1 / 24}
+
+
+@pytest.mark.parametrize("param", list(STEP))
+def test_fig2_spurious_velocity_is_smallest_at_the_predicted_value(param):
+    library()
+    from paper_0710_5470_gb300 import scans
+    opt = scans.OPTIMUM[param]
+    u = [scans.free_param_point(param, opt + k * STEP[param])["spurious"] for k in (-1, 0, 1)]
+    assert None not in u
+    assert u[1] < u[0] and u[1] < u[2]
+
+
+def test_fig2_simple_gradient_is_about_ten_times_worse():
+    library()
+    from paper_0710_5470_gb300 import scans
+    u_opt = scans.free_param_point("B", 1 / 12)["spurious"]
+    u_b0 = scans.free_param_point("B", 0.0)["spurious"]
+    assert 5.0 < u_b0 / u_opt < 20.0
+
+
+def test_fig3_tau_dependence():
+    lb = library()
+    from paper_0710_5470_gb300 import scans
+    taus = (0.75, 1.0, 1.5, 2.0)
+    eq = [scans.spurious_velocity(lb.EQUILIBRIUM, t)["spurious"] for t in taus]
+    fo = [scans.spurious_velocity(lb.FORCING, t)["spurious"] for t in taus]
+    assert eq[0] < eq[1] < eq[2] < eq[3]                      # grows with S(tau) beyond ~0.8
+    assert all(f < e for f, e in zip(fo, eq))                 # forcing below the equilibrium scheme
+    assert fo[3] / fo[1] < eq[3] / eq[1]                      # and growing more slowly
+    assert 1e-6 < fo[1] < 5e-6                                # ~2e-6 c at tau = 1 (Sec. VI)
