@@ -96,6 +96,19 @@ __host__ __device__ constexpr double w_m(int i, int a, int b) {
     return ea != 0 ? -1.0 / 24.0 : 1.0 / 12.0;  // diagonal
 }
 
+// First and second nonzero component of e_i (-1 if none).
+template <class L>
+__host__ __device__ constexpr int first_axis(int i) {
+    return L::ex(i) != 0 ? 0 : (L::ey(i) != 0 ? 1 : (L::ez(i) != 0 ? 2 : -1));
+}
+template <class L>
+__host__ __device__ constexpr int second_axis(int i) {
+    const int a = first_axis<L>(i);
+    for (int c = a + 1; c < 3; ++c)
+        if (e_comp<L>(i, c) != 0) return c;
+    return -1;
+}
+
 // Index of the opposite velocity -e_i.
 template <class L>
 __host__ __device__ constexpr int opposite(int i) {

@@ -236,39 +236,67 @@ __device__ __forceinline__ void collide(const real (&f)[L::Q], real rho, const r
             for (int d = c; d < D; ++d) Mw[c][d] = ok * G[c] * G[d];
     }
     const real omw = real(1) - omega;
+    // Even part of pair (i, -i): Aw plus T_cc of every nonzero component c of
+    // e_i plus e_ic e_id T_cd.  Per axis E_c = Aw + T_cc; per plane of
+    // diagonals, weighted, WP_cd = w_diag (E_c + T_dd) and WT_cd = w_diag T_cd,
+    // so a diagonal pair's even part is WP_cd +- WT_cd.
+    constexpr real wax = real(L::D == 2 ? 1.0 / 3.0 : 1.0 / 6.0), wdg = real(1.0 / 12.0);
+    real E[3], WP[3][3], WT[3][3];
+#pragma unroll
+    for (int c = 0; c < D; ++c) E[c] = Aw + Tq[c][c];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int d = c + 1; d < D; ++d) {
+            WP[c][d] = wdg * (E[c] + Tq[d][d]);
+            WT[c][d] = wdg * Tq[c][d];
+        }
     real sum = real(0);
     static_for<1, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int o = opposite<L>(i);
         if constexpr (i < o) {
-            real even = Aw, odd = real(0);
+            constexpr int c = first_axis<L>(i), d = second_axis<L>(i);
+            real odd = real(0);
             static_for<0, D>([&](auto C) {
-                constexpr int c = decltype(C)::value;
-                constexpr int ec = e_comp<L>(i, c);
-                add_signed<ec>(odd, Jw[c]);
-                if constexpr (ec != 0) even += Tq[c][c];
-                static_for<c + 1, D>([&](auto Dd) {
-                    constexpr int d = decltype(Dd)::value;
-                    add_signed<ec * e_comp<L>(i, d)>(even, Tq[c][d]);
-                });
+                constexpr int cc = decltype(C)::value;
+                add_signed<e_comp<L>(i, cc)>(odd, Jw[cc]);
             });
             constexpr real wi = real(w_vel<L>(i));
-            real ev = wi * even;
+            real ev;
+            if constexpr (d < 0) {
+                ev = wax * E[c];
+            } else {
+                ev = WP[c][d];
+                add_signed<e_comp<L>(i, c) * e_comp<L>(i, d)>(ev, WT[c][d]);
+            }
             if constexpr (!FORCING) {
                 static_for<0, D>([&](auto C) {
-                    constexpr int c = decltype(C)::value;
-                    static_for<c, D>([&](auto Dd) {
-                        constexpr int d = decltype(Dd)::value;
-                        constexpr double wm = w_m<L>(i, c, d);
-                        if constexpr (wm != 0.0) ev += real(wm) * Mw[c][d];
+                    constexpr int c2 = decltype(C)::value;
+                    static_for<c2, D>([&](auto Dd) {
+                        constexpr int d2 = decltype(Dd)::value;
+                        constexpr double wm = w_m<L>(i, c2, d2);
+                        if constexpr (wm != 0.0) ev += real(wm) * Mw[c2][d2];
                     });
                 });
+                sum += ev;
             }
-            sum += ev;
             out[i] = omw * f[i] + (ev + wi * odd);
             out[o] = omw * f[o] + (ev - wi * odd);
         }
     });
+    if constexpr (FORCING) {
+        // sum over pairs of the even parts: the two diagonal pairs of a plane add to 2 WP_cd
+        real se = E[0];
+#pragma unroll
+        for (int c = 1; c < D; ++c) se += E[c];
+        real sp = real(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int d = c + 1; d < D; ++d) sp += WP[c][d];
+        sum = wax * se + real(2) * sp;
+    }
     out[0] = omw * f[0] + (omega * (rho - rsum) - real(2) * sum);  // Eq. 6 and sum_i F_i = 0
 }
 
