@@ -13,7 +13,10 @@ and with the forcing scheme (Sec. VI, max|v|, v = u + g/(2 rho), Eq. 40).
 Beside each point: the factor S(tau) = tau - 6 tau^2 + 6 tau^3 (Eq. 26) that
 multiplies the O(d^3) stencil errors, zero at tau = 1/2 + 1/(2 sqrt 3).
 
-  python -m paper_0710_5470_gb300.scans tau|fig2 [--steps 10000]   (one JSON line)
+Also the 512^2 multi-drop workload (1-8 drops, every (T, kappa) of the
+sweep grid, both schemes, float32 and float64): throughput and spurious velocity.
+
+  python -m paper_0710_5470_gb300.scans tau|fig2|multidrop [--steps N]   (one JSON line)
 """
 from __future__ import annotations
 
@@ -86,6 +89,40 @@ def fig2_scans(scans=FIG2, steps: int = 10000) -> dict:
     return out
 
 
+def multi_drop_sweep(seed: int = 0, storages=(lb.F32, lb.F64), steps: int = 20000, n: int = 512, tau: float = 0.8,
+                     Ts=(0.50, 0.53, 0.55), kappas=(0.004, 0.01, 0.02)) -> dict:
+    """D2Q9 n^2 with 1-8 non-overlapping drops R ~ U[20, 80] (inputs.random_drops(seed)), every
+    (T, kappa) pair, both schemes: throughput (wall clock around the steps, synchronised) and
+    the spurious velocity (max|u| equilibrium, max|v| forcing) after `steps` steps."""
+    import time
+    from . import inputs
+    centres, radii, _ = inputs.random_drops(seed, (n, n))
+    out = {"n": n, "steps": steps, "tau": tau, "drops": len(radii), "runs": []}
+    for storage in storages:
+        for scheme in (lb.EQUILIBRIUM, lb.FORCING):
+            for T in Ts:
+                for kappa in kappas:
+                    with lb.Context(lb.D2Q9, (n, n), A_VDW, B_VDW, T, kappa, tau, scheme=scheme,
+                                    storage=storage) as ctx:
+                        ctx.init_drops(centres, radii, 2.0)
+                        spur, t0, dt = None, None, None
+                        try:
+                            ctx.step(10)
+                            ctx.synchronize()
+                            t0 = time.perf_counter()
+                            ctx.step(steps)
+                            ctx.synchronize()
+                            dt = time.perf_counter() - t0
+                            st = ctx.stats()
+                            spur = st["max_u"] if scheme == lb.EQUILIBRIUM else st["max_v"]
+                        except lb.LBError:       # unstable (LB_EUNSTABLE): the failed sync still ends the steps
+                            if t0 is not None and dt is None:
+                                dt = time.perf_counter() - t0
+                    out["runs"].append({"storage": storage, "scheme": scheme, "T": T, "kappa": kappa,
+                                        "mlups": n * n * steps / dt / 1e6 if dt else None, "spurious": spur})
+    return out
+
+
 def tau_sweep(taus=TAUS, steps: int = 10000) -> dict:
     out = {"drop": dict(PAPER_DROP), "steps": steps, "points": []}
     for t in taus:
@@ -99,13 +136,18 @@ def tau_sweep(taus=TAUS, steps: int = 10000) -> dict:
 
 def main():
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    p.add_argument("what", choices=["tau", "fig2"])
+    p.add_argument("what", choices=["tau", "fig2", "multidrop"])
     p.add_argument("--steps", type=int, default=10000)
     a = p.parse_args()
     from . import build
     build.build()
     lb.load_library()
-    res = tau_sweep(steps=a.steps) if a.what == "tau" else fig2_scans(steps=a.steps)
+    if a.what == "tau":
+        res = tau_sweep(steps=a.steps)
+    elif a.what == "fig2":
+        res = fig2_scans(steps=a.steps)
+    else:
+        res = multi_drop_sweep(steps=a.steps)
     print(json.dumps(res), flush=True)
 
 
