@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the warm-start network (test infrastructure only).
+"""FP64 CPU oracle of the warm-start networks, 2D and 3D (test infrastructure only).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/ (never by the CUDA product
 path).  The warm start is a build addition, not part of the paper: a small
@@ -84,4 +84,73 @@ def init_params(channels, seed: int = 0):
     for cin, cout in zip(channels[:-1], channels[1:]):
         s = 1.0 / np.sqrt(9 * cin)
         params.append((rng.uniform(-s, s, (cout, cin, 3, 3)), np.zeros(cout)))
+    return params
+
+
+# --------------------------------------------------------------------------
+# 3D variant: periodic 3x3x3 convolutions over (z, y, x), same layer pattern.
+#   (W * h)[o, z, y, x] = sum_{c, dz, dy, dx} W[o, c, dz+1, dy+1, dx+1] h[c, z+dz, y+dy, x+dx]
+# --------------------------------------------------------------------------
+
+_TAPS3 = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+
+
+def conv3x3x3(h: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Periodic 3x3x3 convolution of h (N, C_in, D, H, W) -> (N, C_out, D, H, W)."""
+    N, C, D, H, Wd = h.shape
+    out = np.zeros((N, W.shape[0], D, H, Wd))
+    for dz, dy, dx in _TAPS3:
+        sh = np.roll(h, shift=(-dz, -dy, -dx), axis=(2, 3, 4))     # value at (z+dz, y+dy, x+dx)
+        out += np.einsum("oc,nczyx->nozyx", W[:, :, dz + 1, dy + 1, dx + 1], sh)
+    return out + b[None, :, None, None, None]
+
+
+def conv3x3x3_backward(h: np.ndarray, W: np.ndarray, dout: np.ndarray):
+    """Gradients of sum(dout * conv3x3x3(h, W, b)) w.r.t. h, W and b."""
+    dh = np.zeros_like(h)
+    dW = np.zeros_like(W)
+    for dz, dy, dx in _TAPS3:
+        sh = np.roll(h, shift=(-dz, -dy, -dx), axis=(2, 3, 4))
+        dW[:, :, dz + 1, dy + 1, dx + 1] = np.einsum("nozyx,nczyx->oc", dout, sh)
+        contrib = np.einsum("oc,nozyx->nczyx", W[:, :, dz + 1, dy + 1, dx + 1], dout)
+        dh += np.roll(contrib, shift=(dz, dy, dx), axis=(2, 3, 4))
+    db = dout.sum(axis=(0, 2, 3, 4))
+    return dh, dW, db
+
+
+def forward3(x: np.ndarray, params: list):
+    """3D network output and per-layer activations."""
+    acts = [x]
+    h = x
+    for li, (W, b) in enumerate(params):
+        z = conv3x3x3(h, W, b)
+        h = np.tanh(z) if li < len(params) - 1 else z
+        acts.append(h)
+    return h, acts
+
+
+def loss_and_grads3(x: np.ndarray, target: np.ndarray, params: list):
+    """MSE loss and its gradients for the 3D network (backpropagation)."""
+    y, acts = forward3(x, params)
+    n = y.size
+    loss = float(np.sum((y - target) ** 2) / n)
+    g = 2.0 * (y - target) / n
+    grads = [None] * len(params)
+    for li in range(len(params) - 1, -1, -1):
+        W, b = params[li]
+        if li < len(params) - 1:
+            g = g * (1.0 - acts[li + 1] ** 2)
+        dh, dW, db = conv3x3x3_backward(acts[li], W, g)
+        grads[li] = (dW, db)
+        g = dh
+    return loss, grads
+
+
+def init_params3(channels, seed: int = 0):
+    """3D layer parameters: W ~ U(-s, s), s = 1/sqrt(27 C_in), b = 0 (numpy PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    params = []
+    for cin, cout in zip(channels[:-1], channels[1:]):
+        s = 1.0 / np.sqrt(27 * cin)
+        params.append((rng.uniform(-s, s, (cout, cin, 3, 3, 3)), np.zeros(cout)))
     return params
