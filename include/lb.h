@@ -271,6 +271,30 @@ lb_status lb_ws_features(int nx, int ny, const double* rho_tanh, double rho_l, d
 lb_status lb_ws_decode(int nx, int ny, const double* rho_tanh, double rho_l, double rho_g, const float* y,
                        double* rho, double* u);
 
+/* 3D variant for D3Q19 drops: the same network with periodic 3x3x3 convolutions (5 -> 32 -> 32 ->
+ * 32 -> 4 channels); outputs (density correction, 1000 u_x, 1000 u_y, 1000 u_z).  Volumes are
+ * float32 [sample][channel][z][y][x]; W_l packed as [C_out][C_in][3][3][3].  The input features are
+ * those of lb_ws_features, which works site by site (call it with ny * nz as ny).  Same call
+ * conventions and errors as the 2D functions; lb_ws3_predict_sym averages over the eight axis
+ * reflections that fix the centre of the box (velocity components change sign accordingly). */
+#define LB_WS3_OUT 4
+typedef struct lb_ws3 lb_ws3;
+lb_status lb_ws3_create(int seed, void* cuda_stream, lb_ws3** out);
+lb_status lb_ws3_destroy(lb_ws3* ws);   /* NULL-safe */
+lb_status lb_ws3_num_params(const lb_ws3* ws, long long* n);
+lb_status lb_ws3_set_params(lb_ws3* ws, const float* params, size_t count);
+lb_status lb_ws3_get_params(lb_ws3* ws, float* params, size_t count);
+lb_status lb_ws3_forward(lb_ws3* ws, const float* x, int n, int D, int H, int W, float* y);
+lb_status lb_ws3_loss_grad(lb_ws3* ws, const float* x, const float* t, int n, int D, int H, int W, double* loss,
+                           float* grads);
+lb_status lb_ws3_train(lb_ws3* ws, const float* x, const float* t, int n, int D, int H, int W, int epochs, int batch,
+                       float lr, int seed, double* loss_history);
+lb_status lb_ws3_predict_sym(lb_ws3* ws, const float* x, int D, int H, int W, float* y);
+/* rho = rho_tanh + (rho_l - rho_g) * (y_0 minus its mass residual spread over the interface);
+ * u (3N, SoA) = 1e-3 y_{1..3}. */
+lb_status lb_ws3_decode(int nx, int ny, int nz, const double* rho_tanh, double rho_l, double rho_g, const float* y,
+                        double* rho, double* u);
+
 /* ------------------------------------------------------------------------
  * Allocation-free reductions.  The paper has no counterpart: this is a
  * library service for callers that cannot allocate device memory when they

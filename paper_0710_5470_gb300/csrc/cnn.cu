@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/lb.h"
+#include "cnn_common.cuh"
 
 void lb_internal_set_error(const char* msg);
 
@@ -28,11 +29,6 @@ constexpr int CH[NL + 1] = {LB_WS_IN, LB_WS_HIDDEN, LB_WS_HIDDEN, LB_WS_HIDDEN, 
 lb_status fail(lb_status s, const std::string& m) {
     lb_internal_set_error(m.c_str());
     return s;
-}
-
-__device__ __forceinline__ int wrap(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
 }
 
 // out[n,o,y,x] = act(b[o] + sum_{c,dy,dx} W[o,c,dy+1,dx+1] in[n,c,y+dy,x+dx]), periodic.
@@ -183,41 +179,6 @@ __global__ void __launch_bounds__(bwd_w_threads<CIN>()) conv_bwd_weight(const fl
     if (tid < COUT) atomicAdd(db + tid, bacc);
 }
 
-// dy = 2 (y - t) / count; loss += sum (y - t)^2 / count (float64 accumulation).
-__global__ void mse_grad(const float* y, const float* t, float* dy, size_t n, double* loss) {
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-        const float d = y[i] - t[i];
-        dy[i] = 2.f * d / float(n);
-        acc += double(d) * double(d);
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (int(threadIdx.x) < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicAdd(loss, red[0] / double(n));
-}
-
-__global__ void adam_update(float* w, __half* w16, const float* g, float* m, float* v, int n, float lr, float b1,
-                            float b2, float eps, float c1, float c2) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        w16[i] = __float2half_rn(w[i]);
-    }
-}
-
-__global__ void to_half(const float* w, __half* w16, int n) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w16[i] = __float2half_rn(w[i]);
-}
-
 size_t smem_fwd(int cin, int cout) { return size_t(cin * (TILE + 2) * (TILE + 2) + cin * 9 * cout) * 4; }
 size_t smem_bwd_w(int cin, int cout) { return size_t(cin * (TILE + 2) * (TILE + 2) + cout * TILE * TILE) * 4; }
 
@@ -337,22 +298,14 @@ lb_status lb_ws_create(int seed, void* cuda_stream, lb_ws** out) {
     unsigned long long st = (unsigned long long)seed;
     for (int l = 0; l < NL; ++l) {
         const double s = 1.0 / std::sqrt(9.0 * CH[l]);
-        for (int i = 0; i < CH[l + 1] * CH[l] * 9; ++i) {
-            st += 0x9E3779B97F4A7C15ull;
-            unsigned long long z = st;
-            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-            z ^= z >> 31;
-            const double u01 = double(z >> 11) * (1.0 / 9007199254740992.0);
-            h[w->woff[l] + i] = float((2.0 * u01 - 1.0) * s);
-        }
+        for (int i = 0; i < CH[l + 1] * CH[l] * 9; ++i) h[w->woff[l] + i] = float((2.0 * splitmix_u01(st) - 1.0) * s);
     }
     cudaError_t e;
     if ((e = cudaMalloc(&w->p, off * sizeof(float))) != cudaSuccess || (e = cudaMalloc(&w->p16, off * sizeof(__half))) != cudaSuccess ||
         (e = cudaMalloc(&w->g, off * sizeof(float))) != cudaSuccess || (e = cudaMalloc(&w->m, off * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&w->v, off * sizeof(float))) != cudaSuccess || (e = cudaMalloc(&w->loss, sizeof(double))) != cudaSuccess) {
         lb_ws_destroy(w);
-        return fail(LB_ENOMEM, "warm-start parameters");
+        return fail(LB_ENOMEM, std::string("warm-start parameters: ") + cudaGetErrorString(e));
     }
     lb_status s = lb_ws_set_params(w, h.data(), size_t(off));
     if (s != LB_OK) { lb_ws_destroy(w); return s; }

@@ -104,6 +104,19 @@ _SIGNATURES = {
     "lb_ws_features": (C.c_int, [C.c_int, C.c_int, _DPTR, C.c_double, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_double, C.c_void_p]),
     "lb_ws_decode": (C.c_int, [C.c_int, C.c_int, _DPTR, C.c_double, C.c_double, C.c_void_p, _DPTR, _DPTR]),
+    "lb_ws3_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lb_ws3_destroy": (C.c_int, [C.c_void_p]),
+    "lb_ws3_num_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
+    "lb_ws3_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lb_ws3_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lb_ws3_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "lb_ws3_predict_sym": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "lb_ws3_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.POINTER(C.c_double), C.c_void_p]),
+    "lb_ws3_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                               C.c_int, C.c_float, C.c_int, _DPTR]),
+    "lb_ws3_decode": (C.c_int, [C.c_int, C.c_int, C.c_int, _DPTR, C.c_double, C.c_double, C.c_void_p, _DPTR,
+                                _DPTR]),
     "lb_field_stats_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_longlong,
                                          C.c_void_p, C.c_void_p]),
 }
@@ -429,13 +442,86 @@ class WarmStart:
         return hist
 
 
+class WarmStart3(WarmStart):
+    """The 3D warm-start network (lb_ws3_*): 4 periodic 3x3x3 conv layers, 5 -> 32 -> 32 -> 32 -> 4."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        lib = load_library()
+        h = C.c_void_p()
+        st = C.c_void_p(int(stream)) if stream else None
+        _check(lib.lb_ws3_create(seed, st, C.byref(h)))
+        self._h, self._lib = h, lib
+        n = C.c_longlong()
+        _check(lib.lb_ws3_num_params(h, C.byref(n)))
+        self.num_params = n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lb_ws3_destroy(self._h)
+            self._h = None
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.num_params, dtype=np.float32)
+        _check(self._lib.lb_ws3_get_params(self._h, _fptr(p), p.size))
+        return p
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self._lib.lb_ws3_set_params(self._h, _fptr(p), p.size))
+
+    def forward(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n, c, D, H, W = x.shape
+        y = np.empty((n, 4, D, H, W), dtype=np.float32)
+        _check(self._lib.lb_ws3_forward(self._h, _fptr(x), n, D, H, W, _fptr(y)))
+        return y
+
+    def predict_sym(self, x: np.ndarray) -> np.ndarray:
+        """lb_ws3_predict_sym: reflection-averaged prediction for one drop (5 x D x H x W)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        c, D, H, W = x.shape
+        y = np.empty((4, D, H, W), dtype=np.float32)
+        _check(self._lib.lb_ws3_predict_sym(self._h, _fptr(x), D, H, W, _fptr(y)))
+        return y
+
+    def loss_grad(self, x: np.ndarray, t: np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        n, c, D, H, W = x.shape
+        loss = C.c_double()
+        g = np.empty(self.num_params, dtype=np.float32)
+        _check(self._lib.lb_ws3_loss_grad(self._h, _fptr(x), _fptr(t), n, D, H, W, C.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def train(self, x: np.ndarray, t: np.ndarray, epochs: int, batch: int, lr: float, seed: int = 0):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        n, c, D, H, W = x.shape
+        hist = np.zeros(epochs, dtype=np.float64)
+        _check(self._lib.lb_ws3_train(self._h, _fptr(x), _fptr(t), n, D, H, W, epochs, batch, lr, seed,
+                                      _dptr(hist)))
+        return hist
+
+
 def ws_features(rho_tanh: np.ndarray, rho_l: float, rho_g: float, T: float, kappa: float, tau: float, R: float):
-    """lb_ws_features: the 5 input planes (float32) of one D2Q9 drop."""
+    """lb_ws_features: the 5 input planes (float32) of one drop, 2D (ny, nx) or 3D (nz, ny, nx)."""
     r = np.ascontiguousarray(rho_tanh, dtype=np.float64)
-    ny, nx = r.shape[-2:]
-    x = np.empty((5, ny, nx), dtype=np.float32)
-    _check(load_library().lb_ws_features(nx, ny, _dptr(r), rho_l, rho_g, T, kappa, tau, R, _fptr(x)))
+    nx = r.shape[-1]
+    rows = r.size // nx
+    x = np.empty((5,) + r.shape, dtype=np.float32)
+    _check(load_library().lb_ws_features(nx, rows, _dptr(r), rho_l, rho_g, T, kappa, tau, R, _fptr(x)))
     return x
+
+
+def ws3_decode(rho_tanh: np.ndarray, rho_l: float, rho_g: float, y: np.ndarray):
+    """lb_ws3_decode: predicted volumes -> rho (nz, ny, nx), u (3, nz, ny, nx)."""
+    r = np.ascontiguousarray(rho_tanh, dtype=np.float64)
+    nz, ny, nx = r.shape
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    rho = np.empty((nz, ny, nx), dtype=np.float64)
+    u = np.empty((3, nz, ny, nx), dtype=np.float64)
+    _check(load_library().lb_ws3_decode(nx, ny, nz, _dptr(r), rho_l, rho_g, _fptr(y), _dptr(rho), _dptr(u)))
+    return rho, u
 
 
 def ws_decode(rho_tanh: np.ndarray, rho_l: float, rho_g: float, y: np.ndarray):
