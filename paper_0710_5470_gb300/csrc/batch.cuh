@@ -16,6 +16,7 @@ struct BatchInst {
     long long pitch;       // elements per population array
     long long site0;       // first site of the instance in the batch-wide site numbering
     int nx, ny, tiles_x, tiles_y;
+    int pair;              // two sites per halo load (nx even)
     double a, b, T, kappa, omega, nu;
     float pref, rsum;
 };
@@ -47,8 +48,8 @@ __global__ void __launch_bounds__(TX* TY) batch_step_kernel(BatchState bs, char*
     const int it = bs.items[blockIdx.x];
     const int k = it >> 20, t = it & 0xFFFFF;
     const BatchInst& I = bs.inst[k];
-    Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.a, I.b, I.T, I.kappa,
-                 I.omega, I.nu, I.pref, I.rsum, bs.status + k};
+    Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
+                 I.kappa, I.omega, I.nu, I.pref, I.rsum, bs.status + k};
     const int tx = I.tiles_x;
     step2d_tile<D2Q9, FORCING, S, TX, TY>(a, (t % tx) * TX, (t / tx) * TY,
                                           reinterpret_cast<typename S::real*>(smem_raw));

@@ -1,6 +1,7 @@
 // Batched D2Q9 sweeps: kernel instantiations and the lb_batch_* C ABI.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -275,6 +276,7 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
         B->max_sites = std::max(B->max_sites, N);
         I.nx = in.nx;
         I.ny = in.ny;
+        I.pair = (in.nx % 2 == 0 && !std::getenv("LB_NO_PAIR")) ? 1 : 0;
         I.a = a;
         I.b = b;
         I.T = in.T;

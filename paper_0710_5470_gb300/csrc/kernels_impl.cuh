@@ -25,8 +25,8 @@ struct StepKernelOf {
         if constexpr (D3) {
             step_kernel3d<FORCING, S, TX, TY, PAIR><<<grid, TX * TY, bytes(), st>>>(a);
         } else {
-            Tile2DArgs t{a.src_base, a.dst_base, a.pitch, a.nx, a.ny, a.a, a.b, a.T, a.kappa, a.omega, a.nu,
-                         a.pref, a.rsum, a.status};
+            Tile2DArgs t{a.src_base, a.dst_base, a.pitch, a.nx, a.ny, a.pair2d, a.a, a.b, a.T, a.kappa, a.omega,
+                         a.nu, a.pref, a.rsum, a.status};
             step_kernel<L, FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(t);
         }
     }

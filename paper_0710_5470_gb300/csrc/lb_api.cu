@@ -501,6 +501,7 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
     a.ny = c->p.ny;
     a.nz = c->p.nz;
     a.lz = c->lz;
+    a.pair2d = (c->D == 2 && c->p.nx % 2 == 0 && !std::getenv("LB_NO_PAIR")) ? 1 : 0;
     a.a = c->p.a;
     a.b = c->p.b;
     a.T = c->p.T;

@@ -121,29 +121,6 @@ __device__ __forceinline__ void assemble(const PlaneParts<real>& lo, const Plane
     lap = real(2) * (mid.lin + hi.s + lo.s) - real(4) * mid.c;
 }
 
-// Sum of a[B], ..., a[E-1] as a balanced tree (short dependency chains).
-template <int B, int E, class real>
-__device__ __forceinline__ real tree_sum(const real* a) {
-    if constexpr (E - B == 1) return a[B];
-    else {
-        constexpr int M = B + (E - B) / 2;
-        return tree_sum<B, M>(a) + tree_sum<M, E>(a);
-    }
-}
-
-// Density of one site from f_0 and the deviations d_1..d_18 (Eq. 3):
-// rho = (rsum + f_0) + sum_i d_i.
-template <int Q, class real>
-__device__ __forceinline__ real site_rho(const real (&f)[Q], real rsum) {
-    return (rsum + f[0]) + tree_sum<1, Q>(f);
-}
-
-template <class real>
-__device__ __forceinline__ void st_pair(real* p, real a, real b) {
-    if constexpr (sizeof(real) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
-    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
-}
-
 // PAIR: stage A moves two adjacent x sites per thread with 2-vector loads
 // (requires an even nx); otherwise one site per thread.
 template <bool FORCING, class S, int TX, int TY, bool PAIR>

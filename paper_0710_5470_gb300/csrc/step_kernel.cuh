@@ -5,10 +5,12 @@
 // and marches through a chunk of z planes (3D) keeping a short window of
 // planes in shared memory:
 //
-//   stage A  plane p:   read every f_i at the tile plus a density halo of H
-//                       sites (H = 1 equilibrium scheme, H = 2 forcing
-//                       scheme, Sec. VI), sum rho (Eq. 3); the populations of
-//                       the tile's own sites are kept in shared memory.
+//   stage A  plane p:   read every f_i at the tile plus a density halo (2
+//                       sites in x; in y 1 for the equilibrium scheme, 2 for
+//                       the forcing scheme, Sec. VI), sum rho (Eq. 3); the
+//                       populations of the tile's own sites are kept in
+//                       shared memory.  With an even nx a thread moves two
+//                       adjacent x sites per access.
 //   stage B  plane p-1: (forcing) gradient of rho on the tile plus one ring,
 //                       M'_ab = kappa (d_a rho d_b rho - delta_ab |d rho|^2/2),
 //                       gradient and Laplacian on the tile.
@@ -41,6 +43,7 @@ struct StepArgs {
     float pref, rsum;  // deviation storage: fref_i = w_i pref, rsum = pref sum_{i>=1} w_i
     int nx, ny, nz;
     int lz;  // z planes per CTA (3D)
+    int pair2d;  // 2D: two sites per halo load (nx even, 32-bit arithmetic)
     double a, b, T, kappa, omega, nu;
     unsigned int* status;
 };
@@ -50,12 +53,36 @@ __host__ __device__ __forceinline__ int wrapi(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
+// Sum of a[B], ..., a[E-1] as a balanced tree (short dependency chains).
+template <int B, int E, class real>
+__device__ __forceinline__ real tree_sum(const real* a) {
+    if constexpr (E - B == 1) return a[B];
+    else {
+        constexpr int M = B + (E - B) / 2;
+        return tree_sum<B, M>(a) + tree_sum<M, E>(a);
+    }
+}
+
+// Density of one site from f_0 and the deviations d_1..d_18 (Eq. 3):
+// rho = (rsum + f_0) + sum_i d_i.
+template <int Q, class real>
+__device__ __forceinline__ real site_rho(const real (&f)[Q], real rsum) {
+    return (rsum + f[0]) + tree_sum<1, Q>(f);
+}
+
+template <class real>
+__device__ __forceinline__ void st_pair(real* p, real a, real b) {
+    if constexpr (sizeof(real) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
 template <class L, bool FORCING, int TX, int TY, class real>
 struct StepLayout {
     static constexpr bool D3 = L::D == 3;
     static constexpr int Q = L::Q;
-    static constexpr int H = FORCING ? 2 : 1;                 // density halo
-    static constexpr int RX = TX + 2 * H, RY = TY + 2 * H, RN = RX * RY;
+    static constexpr int H = FORCING ? 2 : 1;                 // density halo in y
+    static constexpr int HX = 2, HY = H;                      // x halo even: pairs start on even x
+    static constexpr int RX = TX + 2 * HX, RY = TY + 2 * HY, RN = RX * RY;
     static constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY;  // tile + one ring
     static constexpr int NT = TX * TY;
     static constexpr int NA = (RN + NT - 1) / NT;
@@ -308,13 +335,14 @@ struct Tile2DArgs {
     char* dst;
     long long pitch;
     int nx, ny;
+    int pair;            // 1: two sites per halo load (nx even, 32-bit arithmetic)
     double a, b, T, kappa, omega, nu;
     float pref, rsum;
     unsigned int* status;
 };
 
 // One D2Q9 time step of the TX x TY tile at (x0, y0) (Eq. 4): stage A sums
-// rho on the tile plus a halo of H sites, stage B (forcing) computes the
+// rho on the tile plus its density halo, stage B (forcing) computes the
 // gradient and M' on the tile plus one ring, stage C collides and pushes the
 // tile's sites.  smem holds StepLayout<L, FORCING, TX, TY, real>::TOTAL reals.
 template <class L, bool FORCING, class S, int TX, int TY>
@@ -322,7 +350,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
     static_assert(L::D == 2, "2D tile step");
     using real = typename S::real;
     using Lay = StepLayout<L, FORCING, TX, TY, real>;
-    constexpr int Q = L::Q, D = 2, H = Lay::H, NT = Lay::NT;
+    constexpr int Q = L::Q, D = 2, HX = Lay::HX, HY = Lay::HY, NT = Lay::NT;
     constexpr int RX = Lay::RX, RN = Lay::RN, SX = Lay::SX, SN = Lay::SN;
     real* rho_s = sm + Lay::OFF_RHO;
     real* stash = sm + Lay::OFF_STASH;
@@ -338,29 +366,53 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
     const real pref = real(args.pref), rsum = real(args.rsum);
     const long long pitch = args.pitch;
 
-    // ---------------- stage A: density on the halo region
+    // ---------------- stage A: density on the halo region (2 columns in x, HY rows in y)
+    if (sizeof(real) == 4 && args.pair) {
+        // two adjacent sites per item, 2-vector loads (x0 - HX and nx even: aligned, never split by the wrap)
+        constexpr int NIT = RN / 2, NA2 = (NIT + NT - 1) / NT;
 #pragma unroll
-    for (int m = 0; m < Lay::NA; ++m) {
-        const int k = tid + m * NT;
-        if (k < RN) {
-            const int rx = k % RX, ry = k / RX;
-            const size_t q = size_t(wrapi(y0 - H + ry, ny)) * nx + wrapi(x0 - H + rx, nx);
-            real f[Q];
-            f[0] = S::dec0(S::ld0(args.src, q));
-            static_for<1, Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                f[i] = S::devi(S::ldi(args.src + S::pop_offset(i, pitch), q));
-            });
-            real r = rsum;
-            static_for<1, Q>([&](auto I) { r += f[decltype(I)::value]; });
-            r += f[0];
-            rho_s[k] = r;
-            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY) {
-                const int st = (ry - H) * TX + (rx - H);
-                static_for<0, Q>([&](auto I) {
+        for (int m = 0; m < NA2; ++m) {
+            const int k = tid + m * NT;
+            if (k < NIT) {
+                const int rx = (k % (RX / 2)) * 2, ry = k / (RX / 2);
+                const size_t q = size_t(wrapi(y0 - HY + ry, ny)) * nx + wrapi(x0 - HX + rx, nx);
+                real fa[Q], fb[Q];
+                S::dec0x2(S::ld0x2(args.src, q), fa[0], fb[0]);
+                static_for<1, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    stash[i * NT + st] = f[i];
+                    S::devix2(S::ldix2(args.src + S::pop_offset(i, pitch), q), fa[i], fb[i]);
                 });
+                st_pair(rho_s + 2 * k, site_rho(fa, rsum), site_rho(fb, rsum));
+                if (rx >= HX && rx < HX + TX && ry >= HY && ry < HY + TY) {
+                    const int st = (ry - HY) * TX + (rx - HX);
+                    static_for<0, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        st_pair(stash + i * NT + st, fa[i], fb[i]);
+                    });
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < Lay::NA; ++m) {
+            const int k = tid + m * NT;
+            if (k < RN) {
+                const int rx = k % RX, ry = k / RX;
+                const size_t q = size_t(wrapi(y0 - HY + ry, ny)) * nx + wrapi(x0 - HX + rx, nx);
+                real f[Q];
+                f[0] = S::dec0(S::ld0(args.src, q));
+                static_for<1, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    f[i] = S::devi(S::ldi(args.src + S::pop_offset(i, pitch), q));
+                });
+                rho_s[k] = site_rho(f, rsum);
+                if (rx >= HX && rx < HX + TX && ry >= HY && ry < HY + TY) {
+                    const int st = (ry - HY) * TX + (rx - HX);
+                    static_for<0, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        stash[i * NT + st] = f[i];
+                    });
+                }
             }
         }
     }
@@ -373,7 +425,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
             const int k = tid + m * NT;
             if (k < SN) {
                 const int sx = k % SX, sy = k / SX;
-                const int rc = (sy + H - 1) * RX + (sx + H - 1);
+                const int rc = (sy + HY - 1) * RX + (sx + HX - 1);
                 const real r0 = rho_s[rc];
                 real G[2] = {real(0), real(0)};
                 real lap = real(0);
@@ -408,7 +460,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
             constexpr int i = decltype(I)::value;
             f[i] = stash[i * NT + tid];
         });
-        const int rc = (ty + H) * RX + (tx + H);
+        const int rc = (ty + HY) * RX + (tx + HX);
         const real rho = rho_s[rc];
         real G[3] = {real(0), real(0), real(0)};
         real g[3] = {real(0), real(0), real(0)};
