@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/lb.h: parameter validation,
 // the Maxwell construction, device buffers, and kernel launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -114,6 +115,7 @@ struct lb_ctx {
     LbKernelSet ks;
     int lz = 1;
     dim3 grid;
+    int4* d_work = nullptr;   // 3D: per-CTA (x0, y0, z0, z1)
     bool initialised = false;
     long long step = 0;
     lb_status sticky = LB_OK;
@@ -324,18 +326,34 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     cudaGetLastError();
     const int gx = (p->nx + c->ks.tx - 1) / c->ks.tx;
     const int gy = (p->ny + c->ks.ty - 1) / c->ks.ty;
-    int gz = 1;
     c->lz = 1;
+    c->grid = dim3(gx, gy, 1);
     if (c->D == 3) {
+        // Work list of (tile, z chunk): as many CTAs as are resident at once.  Each tile gets
+        // slots / tiles chunks, the remainder one more (no chunk under 4 planes); CTAs are
+        // listed longest chunk first so that the first wave puts one long CTA on every SM and
+        // the second wave pairs it with a short one.  All CTAs march at the same time, so the
+        // halo rows neighbouring tiles share are read close together (from L2).
         const long long slots = (long long)std::max(sms, 1) * occ;
-        long long chunks = slots / ((long long)gx * gy);
-        if (chunks < 1) chunks = 1;
-        int lz = int((p->nz + chunks - 1) / chunks);
-        if (lz < 4) lz = std::min(4, p->nz);
-        c->lz = lz;
-        gz = (p->nz + lz - 1) / lz;
+        const long long tiles = (long long)gx * gy;
+        const int maxc = std::max(1, p->nz / 4);
+        std::vector<int4> work;
+        for (long long t = 0; t < tiles; ++t) {
+            long long ct = tiles >= slots ? 1 : slots / tiles + (t < slots % tiles ? 1 : 0);
+            ct = std::min<long long>(ct, maxc);
+            const int x0 = int(t % gx) * c->ks.tx, y0 = int(t / gx) * c->ks.ty;
+            for (long long k = 0; k < ct; ++k)
+                work.push_back(make_int4(x0, y0, int(k * p->nz / ct), int((k + 1) * p->nz / ct)));
+        }
+        std::stable_sort(work.begin(), work.end(), [](const int4& u, const int4& v) { return u.w - u.z > v.w - v.z; });
+        c->lz = work.front().w - work.front().z;
+        if (cudaMalloc(&c->d_work, work.size() * sizeof(int4)) != cudaSuccess ||
+            cudaMemcpy(c->d_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) {
+            lb_destroy(c);
+            return fail(LB_ENOMEM, "work list");
+        }
+        c->grid = dim3(unsigned(work.size()), 1, 1);
     }
-    c->grid = dim3(gx, gy, gz);
     *out = c;
     return LB_OK;
 }
@@ -351,6 +369,7 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->w_mp);
     cudaFree(c->w_part);
     cudaFree(c->w_io);
+    cudaFree(c->d_work);
     cudaFree(c->p2_rho);
     cudaFree(c->p2_gl);
     cudaFree(c->p2_mp);
@@ -501,6 +520,7 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
     a.ny = c->p.ny;
     a.nz = c->p.nz;
     a.lz = c->lz;
+    a.work = c->d_work;
     a.pair2d = (c->D == 2 && c->p.nx % 2 == 0 && !std::getenv("LB_NO_PAIR")) ? 1 : 0;
     a.a = c->p.a;
     a.b = c->p.b;

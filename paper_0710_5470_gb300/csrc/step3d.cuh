@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
     const int nx = args.nx, ny = args.ny, nz = args.nz;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * args.lz;
-    const int z1 = min(z0 + args.lz, nz);
+    const int4 wk = args.work[blockIdx.x];    // this CTA's tile and z chunk
+    const int x0 = wk.x, y0 = wk.y;
+    const int z0 = wk.z, z1 = wk.w;
     const int plane = nx * ny;
 
     const real pa = real(args.a), pb = real(args.b), pT = real(args.T), pk = real(args.kappa);

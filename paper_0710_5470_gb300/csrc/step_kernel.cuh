@@ -42,7 +42,8 @@ struct StepArgs {
     float fref[MAXQ];
     float pref, rsum;  // deviation storage: fref_i = w_i pref, rsum = pref sum_{i>=1} w_i
     int nx, ny, nz;
-    int lz;  // z planes per CTA (3D)
+    int lz;  // longest z chunk of a CTA (3D)
+    const int4* work;  // 3D: per CTA (x0, y0, z0, z1) of its column tile and z chunk
     int pair2d;  // 2D: two sites per halo load (nx even, 32-bit arithmetic)
     double a, b, T, kappa, omega, nu;
     unsigned int* status;
