@@ -38,8 +38,8 @@ KERNEL_SOURCES = ["step3d.cuh", "step_kernel.cuh", "storage.cuh", "lattice.cuh"]
 # fingerprint of the kernel sources they were measured on and the storage.
 # A changed kernel has a new fingerprint and reports traffic = null.
 NCU_TRAFFIC = {
-    ("5ab7b7658ba2", "f16dev", 128): 132.68e6,   # 93.88 MB read + 38.80 MB written
-    ("5ab7b7658ba2", "f32", 128): 291.28e6,      # 179.64 MB read + 111.64 MB written
+    ("f36d13fade8b", "f16dev", 128): 136.68e6,   # 97.18 MB read + 39.50 MB written
+    ("f36d13fade8b", "f32", 128): 301.65e6,      # 188.66 MB read + 113.00 MB written
 }
 
 
