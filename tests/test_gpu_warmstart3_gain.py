@@ -3,7 +3,7 @@
 The 3x3x3 network is trained on the GPU on solver-made steady states of 32^3
 drops and applied to held-out 32^3 drops: its start is closer (rms) to the
 solver's steady density than the tanh profile, and at least half of the runs
-end in the tanh start's steady state (the solver stays the judge).  Steps to
+end in the tanh start's steady state (the solver has the last word).  Steps to
 the steady-state check are printed, not asserted: measured, the network's
 start takes more steps than the tanh start (its density is not in
 mechanical balance), so the learned start is not a speed-up in 3D.

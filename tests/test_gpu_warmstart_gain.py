@@ -3,7 +3,7 @@
 The network (trained on the GPU by the library's kernels on solver-made
 steady states) starts a run closer to the solver's steady density than the
 tanh profile does, and at least 80% of the held-out runs end in the tanh
-start's steady state (the solver stays the judge; a heuristic start can send
+start's steady state (the solver has the last word; a heuristic start can send
 a drop elsewhere, which is counted and printed).  Steps to the steady-state
 check are measured and printed: they are about the same from either start,
 so no speed-up is asserted.
