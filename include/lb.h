@@ -104,7 +104,9 @@ lb_status lb_coexistence(double a, double b, double T, double* rho_l, double* rh
 /* Create a context: validates *p, solves the coexistence densities and
  * allocates the two population buffers on the current CUDA device.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream); it must
- * outlive the context.  *out receives the context, or NULL on error. */
+ * outlive the context.  *out receives the context, or NULL on error.
+ * LB_EINVAL also for more than 2^31 - 1 sites (the kernels index sites with
+ * 32-bit integers). */
 lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out);
 
 /* Release every device allocation of the context.  NULL-safe. */
@@ -192,7 +194,8 @@ typedef struct {
     double radius;         /* radius of its centred drop (lb_batch_init_drops); <= 0: no drop */
 } lb_instance;
 
-/* n in 1..4096 instances; cuda_stream NULL => the batch creates its own stream. */
+/* n in 1..4096 instances, each with at most 2^20 tiles of 32 x 8 sites (LB_EINVAL otherwise);
+ * cuda_stream NULL => the batch creates its own stream. */
 lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, const lb_instance* inst,
                           void* cuda_stream, lb_batch** out);
 lb_status lb_batch_destroy(lb_batch* batch);   /* NULL-safe */

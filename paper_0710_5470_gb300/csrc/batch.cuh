@@ -23,7 +23,7 @@ struct BatchInst {
 
 struct BatchState {
     const BatchInst* inst;
-    int* items;                  // (instance << 20) | tile, active instances only
+    unsigned* items;             // (instance << 20) | tile (12 + 20 bits), active instances only
     int* count;                  // number of valid items
     int* active;                 // per instance: 1 while stepping
     unsigned int* status;        // per instance: bit 0 = non-finite density seen
@@ -45,8 +45,8 @@ template <bool FORCING, class S, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) batch_step_kernel(BatchState bs, char* buf, int parity) {
     if (blockIdx.x >= *bs.count) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int it = bs.items[blockIdx.x];
-    const int k = it >> 20, t = it & 0xFFFFF;
+    const unsigned it = bs.items[blockIdx.x];
+    const int k = int(it >> 20), t = int(it & 0xFFFFFu);
     const BatchInst& I = bs.inst[k];
     Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
                  I.kappa, I.omega, I.nu, I.pref, I.rsum, bs.status + k};
@@ -60,8 +60,8 @@ template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) batch_check_kernel(BatchState bs, const char* buf, int parity) {
     if (blockIdx.x >= *bs.count) return;
     __shared__ double red[TX * TY], redu[TX * TY], rmax[TX * TY], rmin[TX * TY];
-    const int it = bs.items[blockIdx.x];
-    const int k = it >> 20, t = it & 0xFFFFF;
+    const unsigned it = bs.items[blockIdx.x];
+    const int k = int(it >> 20), t = int(it & 0xFFFFFu);
     const BatchInst& I = bs.inst[k];
     const int x = (t % I.tiles_x) * TX + int(threadIdx.x) % TX;
     const int y = (t / I.tiles_x) * TY + int(threadIdx.x) / TX;
@@ -179,7 +179,7 @@ __global__ void batch_finalize_kernel(BatchState bs, double tol, int every, long
         }
         __syncthreads();
         if (k < bs.n)
-            for (int tt = 0; tt < ntile; ++tt) bs.items[base + offs[threadIdx.x] + tt] = (k << 20) | tt;
+            for (int tt = 0; tt < ntile; ++tt) bs.items[base + offs[threadIdx.x] + tt] = (unsigned(k) << 20) | unsigned(tt);
         __syncthreads();
         const int chunk = offs[min(int(blockDim.x), bs.n - k0)];
         base += chunk;

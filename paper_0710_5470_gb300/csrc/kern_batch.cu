@@ -117,7 +117,7 @@ struct lb_batch {
     // device
     char* buf = nullptr;              // states: [instance][buffer][populations]
     BatchInst* d_inst = nullptr;
-    int* d_items = nullptr;
+    unsigned* d_items = nullptr;
     int* d_count = nullptr;
     int* d_active = nullptr;
     unsigned* d_status = nullptr;
@@ -175,18 +175,18 @@ lb_status set_tile(lb_batch* B, int tile) {
     B->tile = tile;
     B->k = batch_kernels(B->scheme, B->storage, tile);
     cudaFuncSetAttribute(B->k.step_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B->k.smem));
-    std::vector<int> items;
+    std::vector<unsigned> items;
     for (int k = 0; k < B->n; ++k) {
         BatchInst& I = B->di[k];
         I.tiles_x = (I.nx + B->k.tx - 1) / B->k.tx;
         I.tiles_y = (I.ny + B->k.ty - 1) / B->k.ty;
-        for (int t = 0; t < I.tiles_x * I.tiles_y; ++t) items.push_back((k << 20) | t);
+        for (int t = 0; t < I.tiles_x * I.tiles_y; ++t) items.push_back((unsigned(k) << 20) | unsigned(t));
     }
     if (int(items.size()) > B->max_items) return fail(LB_EINVAL, "work list larger than allocated");
     cudaError_t e = cudaMemcpyAsync(B->d_inst, B->di.data(), B->di.size() * sizeof(BatchInst),
                                     cudaMemcpyHostToDevice, B->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(B->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(B->d_items, items.data(), items.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
                             B->stream);
     int cnt = int(items.size());
     if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_count, &cnt, sizeof(int), cudaMemcpyHostToDevice, B->stream);
@@ -257,10 +257,14 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
     B->rho_l.resize(n);
     B->rho_g.resize(n);
     long long off = 0;
-    int max_items = 0;
+    long long max_items = 0;
     for (int k = 0; k < n; ++k) {
         const lb_instance& in = inst[k];
-        if (in.nx < 1 || in.ny < 1 || double(in.nx) * in.ny > 1e9) { delete B; return fail(LB_EINVAL, "bad instance size"); }
+        // a work item holds the tile index in 20 bits: at most 2^20 tiles of the smallest variant (32 x 8)
+        if (in.nx < 1 || in.ny < 1 || double((in.nx + 31) / 32) * ((in.ny + 7) / 8) > double(1 << 20)) {
+            delete B;
+            return fail(LB_EINVAL, "bad instance size (1 <= nx, ny; at most 2^20 tiles of 32 x 8)");
+        }
         if (!(in.tau > 0.5) || !(in.kappa > 0)) { delete B; return fail(LB_EINVAL, "bad instance tau/kappa"); }
         lb_status s = lb_coexistence(a, b, in.T, &B->rho_l[k], &B->rho_g[k]);
         if (s != LB_OK) { delete B; return s; }
@@ -291,7 +295,8 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
         most = int(((in.nx + 31) / 32) * ((in.ny + 7) / 8));
         max_items += most;
     }
-    B->max_items = max_items;
+    if (max_items > 0x7fffffffLL) { delete B; return fail(LB_EINVAL, "batch too large"); }
+    B->max_items = int(max_items);
     B->state_bytes = size_t(off);
     if (cuda_stream) {
         B->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -302,7 +307,7 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
     cudaError_t e;
     if ((e = cudaMalloc(&B->buf, B->state_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&B->d_inst, n * sizeof(BatchInst))) != cudaSuccess ||
-        (e = cudaMalloc(&B->d_items, size_t(max_items) * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_items, size_t(max_items) * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_count, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_active, n * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_status, n * sizeof(unsigned))) != cudaSuccess ||

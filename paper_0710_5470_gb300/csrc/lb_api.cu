@@ -243,7 +243,8 @@ lb_status validate(const lb_params* p) {
     if (p->lattice != LB_D2Q9 && p->lattice != LB_D3Q19) return fail(LB_EINVAL, "unknown lattice");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LB_EINVAL, "grid sizes must be >= 1");
     if (p->lattice == LB_D2Q9 && p->nz != 1) return fail(LB_EINVAL, "D2Q9 needs nz = 1");
-    if (double(p->nx) * p->ny > 2.0e9) return fail(LB_EINVAL, "nx*ny too large");
+    if (double(p->nx) * p->ny * p->nz > 2147483647.0)
+        return fail(LB_EINVAL, "lattice too large: the kernels index sites with 32-bit integers (at most 2^31 - 1 sites)");
     if (!(p->tau > 0.5)) return fail(LB_EINVAL, "tau must exceed 1/2");
     if (!(p->kappa > 0)) return fail(LB_EINVAL, "kappa must be positive");
     if (!(p->a > 0 && p->b > 0)) return fail(LB_EINVAL, "a and b must be positive");

@@ -48,6 +48,23 @@ def test_invalid_parameters_rejected_before_device_work():
         lb.Context(0, (8, 8, 2), A_VDW, B_VDW, 0.55, 0.01, 0.8)   # D2Q9 needs nz = 1
     with pytest.raises(lb.LBError):
         lb.coexistence(A_VDW, B_VDW, 8 * A_VDW / (27 * B_VDW))
+    # site indices are 32-bit in the kernels: more than 2^31 - 1 sites is refused
+    with pytest.raises(lb.LBError) as e:
+        lb.Context(1, (1300, 1300, 1300), A_VDW, B_VDW, 0.55, 0.01, 0.8)
+    assert e.value.status == 1 and "32-bit" in str(e.value)
+
+
+def test_batch_limits_rejected_before_device_work():
+    """A batch work item holds 12 bits of instance and 20 bits of tile: more than
+    4096 instances or 2^20 tiles of 32 x 8 in one instance is refused."""
+    lb = library()
+    ok = dict(nx=32, ny=32, T=0.55, kappa=0.01, tau=1.0, radius=8.0)
+    with pytest.raises(lb.LBError) as e:
+        lb.Batch([dict(ok, nx=32768, ny=8200)], A_VDW, B_VDW)
+    assert e.value.status == 1
+    with pytest.raises(lb.LBError) as e:
+        lb.Batch([ok] * 4097, A_VDW, B_VDW)
+    assert e.value.status == 1
 
 
 def test_missing_library_fails_loudly(tmp_path):
