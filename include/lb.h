@@ -253,7 +253,8 @@ lb_status lb_ws_destroy(lb_ws* ws);   /* NULL-safe */
 lb_status lb_ws_num_params(const lb_ws* ws, long long* n);
 lb_status lb_ws_set_params(lb_ws* ws, const float* params, size_t count);   /* resets the Adam state */
 lb_status lb_ws_get_params(lb_ws* ws, float* params, size_t count);
-/* y (n x 3 x H x W) = network(x (n x 5 x H x W)). */
+/* y (n x 3 x H x W) = network(x (n x 5 x H x W)).  At most 65535 samples per call (and per
+ * training minibatch); more is LB_EINVAL. */
 lb_status lb_ws_forward(lb_ws* ws, const float* x, int n, int H, int W, float* y);
 /* Prediction for one drop (x: 5 x H x W) averaged over the symmetries of the periodic lattice
  * that fix the domain centre (reflections about W/2 and H/2, and the transpose when H == W), with
@@ -278,7 +279,8 @@ lb_status lb_ws_decode(int nx, int ny, const double* rho_tanh, double rho_l, dou
  * 32 -> 4 channels); outputs (density correction, 1000 u_x, 1000 u_y, 1000 u_z).  Volumes are
  * float32 [sample][channel][z][y][x]; W_l packed as [C_out][C_in][3][3][3].  The input features are
  * those of lb_ws_features, which works site by site (call it with ny * nz as ny).  Same call
- * conventions and errors as the 2D functions; lb_ws3_predict_sym averages over the eight axis
+ * conventions and errors as the 2D functions (with samples x depth at most 65535 per call and per
+ * minibatch); lb_ws3_predict_sym averages over the eight axis
  * reflections that fix the centre of the box (velocity components change sign accordingly). */
 #define LB_WS3_OUT 4
 typedef struct lb_ws3 lb_ws3;

@@ -248,11 +248,15 @@ void launch_bwd(lb_ws* w, int l, int n, int H, int Wd) {
     }
 }
 
-void forward(lb_ws* w, int n, int H, int Wd) {
+// The sample index is the grid's z dimension: at most 65535 samples per launch.
+constexpr int MAX_SAMPLES = 65535;
+
+cudaError_t forward(lb_ws* w, int n, int H, int Wd) {
     launch_fwd<LB_WS_IN, LB_WS_HIDDEN, true>(w->act[0], w->p16 + w->woff[0], w->p + w->boff[0], w->act[1], n, H, Wd, w->st);
     launch_fwd<LB_WS_HIDDEN, LB_WS_HIDDEN, true>(w->act[1], w->p16 + w->woff[1], w->p + w->boff[1], w->act[2], n, H, Wd, w->st);
     launch_fwd<LB_WS_HIDDEN, LB_WS_HIDDEN, true>(w->act[2], w->p16 + w->woff[2], w->p + w->boff[2], w->act[3], n, H, Wd, w->st);
     launch_fwd<LB_WS_HIDDEN, LB_WS_OUT, false>(w->act[3], w->p16 + w->woff[3], w->p + w->boff[3], w->act[4], n, H, Wd, w->st);
+    return cudaGetLastError();
 }
 
 // loss and gradients of the batch whose inputs sit in act[0] and targets in dact[4]'s place (t)
@@ -357,13 +361,14 @@ lb_status lb_ws_get_params(lb_ws* w, float* params, size_t count) {
 }
 
 lb_status lb_ws_forward(lb_ws* w, const float* x, int n, int H, int Wd, float* y) {
-    if (!w || !x || !y || n < 1 || H < 1 || Wd < 1) return fail(LB_EINVAL, "bad arguments");
+    if (!w || !x || !y || n < 1 || n > MAX_SAMPLES || H < 1 || Wd < 1) return fail(LB_EINVAL, "bad arguments");
     const size_t pix = size_t(n) * H * Wd;
     lb_status s = ensure_acts(w, pix);
     if (s != LB_OK) return s;
     cudaError_t e = cudaMemcpyAsync(w->act[0], x, pix * LB_WS_IN * sizeof(float), cudaMemcpyHostToDevice, w->st);
     if (e != cudaSuccess) return fail(LB_ECUDA, "upload");
-    forward(w, n, H, Wd);
+    if ((e = forward(w, n, H, Wd)) != cudaSuccess)
+        return fail(LB_ECUDA, std::string("warm-start forward launch: ") + cudaGetErrorString(e));
     e = cudaMemcpyAsync(y, w->act[4], pix * LB_WS_OUT * sizeof(float), cudaMemcpyDeviceToHost, w->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(w->st);
     return e == cudaSuccess ? LB_OK : fail(LB_ECUDA, std::string("warm-start forward: ") + cudaGetErrorString(e));
@@ -371,7 +376,7 @@ lb_status lb_ws_forward(lb_ws* w, const float* x, int n, int H, int Wd, float* y
 
 lb_status lb_ws_loss_grad(lb_ws* w, const float* x, const float* t, int n, int H, int Wd, double* loss,
                           float* grads) {
-    if (!w || !x || !t || n < 1 || H < 1 || Wd < 1) return fail(LB_EINVAL, "bad arguments");
+    if (!w || !x || !t || n < 1 || n > MAX_SAMPLES || H < 1 || Wd < 1) return fail(LB_EINVAL, "bad arguments");
     const size_t pix = size_t(n) * H * Wd;
     lb_status s = ensure_acts(w, pix);
     if (s != LB_OK) return s;
@@ -393,6 +398,7 @@ lb_status lb_ws_train(lb_ws* w, const float* x, const float* t, int n, int H, in
                       float lr, int seed, double* loss_history) {
     if (!w || !x || !t || n < 1 || H < 1 || Wd < 1 || epochs < 1 || batch < 1) return fail(LB_EINVAL, "bad arguments");
     batch = batch < n ? batch : n;
+    if (batch > MAX_SAMPLES) return fail(LB_EINVAL, "batch larger than 65535 samples");
     const size_t img = size_t(H) * Wd;
     lb_status s = ensure_acts(w, size_t(batch) * img);
     if (s != LB_OK) return s;

@@ -258,11 +258,12 @@ void launch_bwd3(lb_ws3* w, int l, int n, int D, int H, int Wd) {
     }
 }
 
-void forward3(lb_ws3* w, int n, int D, int H, int Wd) {
+cudaError_t forward3(lb_ws3* w, int n, int D, int H, int Wd) {
     launch_fwd3<LB_WS_IN, LB_WS_HIDDEN, true>(w->act[0], w->p16 + w->woff[0], w->p + w->boff[0], w->act[1], n, D, H, Wd, w->st);
     launch_fwd3<LB_WS_HIDDEN, LB_WS_HIDDEN, true>(w->act[1], w->p16 + w->woff[1], w->p + w->boff[1], w->act[2], n, D, H, Wd, w->st);
     launch_fwd3<LB_WS_HIDDEN, LB_WS_HIDDEN, true>(w->act[2], w->p16 + w->woff[2], w->p + w->boff[2], w->act[3], n, D, H, Wd, w->st);
     launch_fwd3<LB_WS_HIDDEN, LB_WS3_OUT, false>(w->act[3], w->p16 + w->woff[3], w->p + w->boff[3], w->act[4], n, D, H, Wd, w->st);
+    return cudaGetLastError();
 }
 
 lb_status loss_grad3(lb_ws3* w, const float* t, int n, int D, int H, int Wd, double* loss_out) {
@@ -285,7 +286,10 @@ lb_status loss_grad3(lb_ws3* w, const float* t, int n, int D, int H, int Wd, dou
     return LB_OK;
 }
 
-bool dims_ok(int n, int D, int H, int Wd) { return n >= 1 && D >= 1 && H >= 1 && Wd >= 1; }
+// (sample, z plane) is the grid's z dimension: at most 65535 per launch.
+bool dims_ok(int n, int D, int H, int Wd) {
+    return n >= 1 && D >= 1 && H >= 1 && Wd >= 1 && (long long)n * D <= 65535;
+}
 
 }  // namespace
 
@@ -380,7 +384,8 @@ lb_status lb_ws3_forward(lb_ws3* w, const float* x, int n, int D, int H, int Wd,
     if (s != LB_OK) return s;
     cudaError_t e = cudaMemcpyAsync(w->act[0], x, vox * LB_WS_IN * sizeof(float), cudaMemcpyHostToDevice, w->st);
     if (e != cudaSuccess) return fail(LB_ECUDA, "upload");
-    forward3(w, n, D, H, Wd);
+    if ((e = forward3(w, n, D, H, Wd)) != cudaSuccess)
+        return fail(LB_ECUDA, std::string("3D warm-start forward launch: ") + cudaGetErrorString(e));
     e = cudaMemcpyAsync(y, w->act[4], vox * LB_WS3_OUT * sizeof(float), cudaMemcpyDeviceToHost, w->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(w->st);
     return e == cudaSuccess ? LB_OK : fail(LB_ECUDA, std::string("3D warm-start forward: ") + cudaGetErrorString(e));
@@ -408,8 +413,10 @@ lb_status lb_ws3_loss_grad(lb_ws3* w, const float* x, const float* t, int n, int
 
 lb_status lb_ws3_train(lb_ws3* w, const float* x, const float* t, int n, int D, int H, int Wd, int epochs, int batch,
                        float lr, int seed, double* loss_history) {
-    if (!w || !x || !t || !dims_ok(n, D, H, Wd) || epochs < 1 || batch < 1) return fail(LB_EINVAL, "bad arguments");
+    if (!w || !x || !t || n < 1 || !dims_ok(1, D, H, Wd) || epochs < 1 || batch < 1)
+        return fail(LB_EINVAL, "bad arguments");
     batch = batch < n ? batch : n;
+    if (!dims_ok(batch, D, H, Wd)) return fail(LB_EINVAL, "batch * depth larger than 65535");
     const size_t vol = size_t(D) * H * Wd;
     lb_status s = ensure_acts3(w, size_t(batch) * vol);
     if (s != LB_OK) return s;
