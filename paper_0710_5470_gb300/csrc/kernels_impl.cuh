@@ -14,7 +14,7 @@ struct StepKernelOf {
     using real = typename S::real;
     static constexpr bool D3 = L::D == 3;
     static constexpr size_t bytes() {
-        if constexpr (D3) return Layout3D<FORCING, TX, TY, real>::BYTES;
+        if constexpr (D3) return Layout3D<FORCING, TX, TY, real, sizeof(typename S::rawi) == 2>::BYTES;
         else return StepLayout<L, FORCING, TX, TY, real>::BYTES;
     }
     static const void* fn() {

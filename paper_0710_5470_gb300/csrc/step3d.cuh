@@ -25,7 +25,9 @@
 
 namespace lbk {
 
-template <bool FORCING, int TX, int TY, class real>
+// RAW: 16-bit deviation storage; the stash keeps f_0 (float) and the raw
+// 16-bit deviations as loaded, and stage C decodes them.
+template <bool FORCING, int TX, int TY, class real, bool RAW = false>
 struct Layout3D {
     static constexpr int Q = 19;
     // density halo: 2 sites in x for both schemes (pairs of sites start on an
@@ -47,8 +49,10 @@ struct Layout3D {
     // layout would let stage C read a site with 128-bit loads, but the paired
     // stage-A writes then conflict on banks: measured slower)
     static constexpr int OFF_STASH = al4(OFF_RHO + NRHO * RN);
+    // reals per stash slot: Q per site, or with RAW one f_0 and Q - 1 half-size deviations
+    static constexpr int SLOT = RAW ? NT + (Q - 1) * NT / 2 : Q * NT;
     // M' of one plane on the tile + 1 ring: (Mxx, Mxy, Mxz, Myy) per site, then (Myz, Mzz) per site
-    static constexpr int OFF_MP = al4(OFF_STASH + NSTASH * Q * NT);
+    static constexpr int OFF_MP = al4(OFF_STASH + NSTASH * SLOT);
     // G and the Laplacian of the tile for two planes: (G_x, G_y, G_z, lap) per site
     static constexpr int OFF_G = al4(OFF_MP + (FORCING ? 6 * SN : 0));
     static constexpr int TOTAL = OFF_G + (FORCING ? 2 * 4 * NT : 0);
@@ -127,7 +131,8 @@ template <bool FORCING, class S, int TX, int TY, bool PAIR>
 __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX * TY <= 256) ? 2 : 1) step_kernel3d(const StepArgs args) {
     using L = D3Q19;
     using real = typename S::real;
-    using Lay = Layout3D<FORCING, TX, TY, real>;
+    constexpr bool RAW = sizeof(typename S::rawi) == 2;
+    using Lay = Layout3D<FORCING, TX, TY, real, RAW>;
     constexpr int Q = 19, HX = Lay::HX, HY = Lay::HY, NT = Lay::NT;
     constexpr int RX = Lay::RX, RN = Lay::RN, SX = Lay::SX, SN = Lay::SN;
     constexpr int W = PAIR ? 2 : 1;                 // sites per stage-A item
@@ -241,7 +246,8 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
         {
             if (!PREFETCH) issue();
             real* rho_w = rho_s + (it % Lay::NRHO) * RN;
-            real* st_w = stash + (it % Lay::NSTASH) * Q * NT;
+            real* st_w = stash + (it % Lay::NSTASH) * Lay::SLOT;
+            typename S::rawi* sd_w = reinterpret_cast<typename S::rawi*>(st_w + NT);   // RAW deviations
             const bool keep = p >= z0 && p < z1;
 #pragma unroll
             for (int m = 0; m < NA; ++m) {
@@ -255,10 +261,18 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                         });
                         st_pair(rho_w + 2 * (tid + m * NT), site_rho(fa, rsum), site_rho(fb, rsum));
                         if (keep && a_st[m] >= 0) {
-                            static_for<0, Q>([&](auto I) {
-                                constexpr int i = decltype(I)::value;
-                                st_pair(st_w + i * NT + a_st[m], fa[i], fb[i]);
-                            });
+                            if constexpr (RAW) {
+                                st_pair(st_w + a_st[m], fa[0], fb[0]);
+                                static_for<1, Q>([&](auto I) {
+                                    constexpr int i = decltype(I)::value;
+                                    *reinterpret_cast<RI*>(sd_w + (i - 1) * NT + a_st[m]) = ri[m][i - 1];
+                                });
+                            } else {
+                                static_for<0, Q>([&](auto I) {
+                                    constexpr int i = decltype(I)::value;
+                                    st_pair(st_w + i * NT + a_st[m], fa[i], fb[i]);
+                                });
+                            }
                         }
                     } else {
                         real f[Q];           // f_0 and the deviations d_i
@@ -269,10 +283,18 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                         });
                         rho_w[tid + m * NT] = site_rho(f, rsum);
                         if (keep && a_st[m] >= 0) {
-                            static_for<0, Q>([&](auto I) {
-                                constexpr int i = decltype(I)::value;
-                                st_w[i * NT + a_st[m]] = f[i];
-                            });
+                            if constexpr (RAW) {
+                                st_w[a_st[m]] = f[0];
+                                static_for<1, Q>([&](auto I) {
+                                    constexpr int i = decltype(I)::value;
+                                    sd_w[(i - 1) * NT + a_st[m]] = ri[m][i - 1];
+                                });
+                            } else {
+                                static_for<0, Q>([&](auto I) {
+                                    constexpr int i = decltype(I)::value;
+                                    st_w[i * NT + a_st[m]] = f[i];
+                                });
+                            }
                         }
                     }
                 }
@@ -376,12 +398,21 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
         const int s = p - Lay::LAG_C;
         if (s >= z0 && own) {
             const int is = s - pstart;
-            const real* st_r = stash + (is % Lay::NSTASH) * Q * NT;
+            const real* st_r = stash + (is % Lay::NSTASH) * Lay::SLOT;
             real f[Q];
-            static_for<0, Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                f[i] = st_r[i * NT + tid];
-            });
+            if constexpr (RAW) {
+                const typename S::rawi* sd_r = reinterpret_cast<const typename S::rawi*>(st_r + NT);
+                f[0] = st_r[tid];
+                static_for<1, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    f[i] = S::devi(sd_r[(i - 1) * NT + tid]);
+                });
+            } else {
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    f[i] = st_r[i * NT + tid];
+                });
+            }
             const real rho = rho_s[(is % Lay::NRHO) * RN + (ty + HY) * RX + (tx + HX)];
             real G[3], lap;
             if constexpr (FORCING) {
