@@ -136,3 +136,21 @@ def test_reference_test_stops_reduced_storage_at_float64_accuracy():
         assert abs(hi32[k] - hi[k]) <= 1e-3 and abs(lo32[k] - lo[k]) <= 1e-3
         assert 1000 <= steps32[k] <= 2 * steps64[k] + 1000
         assert abs(got[k][0].max() - hi32[k]) <= 1e-12 and abs(got[k][0].min() - lo32[k]) <= 1e-12
+
+
+def test_maximum_instance_count_matches_single_contexts():
+    """4096 instances (the API's maximum; work items hold the instance in 12
+    bits): instances on both sides of 2048 step exactly like single contexts."""
+    lb = library()
+    base = dict(nx=16, ny=8, T=0.55, kappa=0.01, tau=1.0, radius=3.0)
+    inst = [dict(base, T=0.54 + 0.02 * (k % 7) / 7, tau=0.8 + 0.05 * (k % 5)) for k in range(4096)]
+    with lb.Batch(inst, A_VDW, B_VDW, scheme=1, storage=lb.F64) as bt:
+        bt.init_drops(2.0)
+        bt.step(12)
+        got = {k: bt.populations(k) for k in (0, 2047, 2048, 4095)}
+    for k, f in got.items():
+        d = inst[k]
+        with make_ctx(lb, "D2Q9", "forcing", (d["nx"], d["ny"]), T=d["T"], kappa=d["kappa"], tau=d["tau"]) as ctx:
+            ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
+            ctx.step(12)
+            assert np.array_equal(ctx.get_populations(), f), k
