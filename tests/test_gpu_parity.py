@@ -142,6 +142,26 @@ def test_degenerate_tiny_grids(lat, shape, scheme):
     assert rel_inf(got, want) < 1e-12
 
 
+@pytest.mark.parametrize("storage,tol", [(F32, 1e-5), (F16DEV, 5e-4), (BF16DEV, 5e-3)])
+@pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 7)), ("D2Q9", (2, 5)), ("D3Q19", (1, 1, 1)),
+                                       ("D3Q19", (2, 5, 1)), ("D3Q19", (2, 2, 3))])
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_degenerate_tiny_grids_reduced_storage(lat, shape, scheme, storage, tol):
+    """The same wrap-onto-itself grids in reduced storage (nx = 2 takes the
+    paired halo loads), from the rounded start, within the storage's bound."""
+    lb = library()
+    m = oracle_model(lat, scheme)
+    rng_f = drop_populations(m, shape, 1.0)
+    f0 = rng_f * (1.0 + 1e-2 * inputs.noise(12, rng_f.shape))
+    with make_ctx(lb, lat, scheme, shape, storage=storage) as ctx:
+        ctx.set_populations(f0)
+        start = ctx.get_populations()
+        ctx.step(7)
+        got = ctx.get_populations()
+    want = O.run(start, m, 7)
+    assert rel_inf(got, want) < tol
+
+
 def test_zero_steps_and_state_errors():
     lb = library()
     with make_ctx(lb, "D2Q9", "forcing", (16, 16)) as ctx:
