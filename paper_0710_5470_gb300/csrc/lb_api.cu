@@ -529,6 +529,12 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
     a.kappa = c->p.kappa;
     a.omega = 1.0 / c->p.tau;
     a.nu = (c->p.tau - 0.5) / 3.0;
+    a.fa = float(a.a);
+    a.fb = float(a.b);
+    a.fT = float(a.T);
+    a.fkappa = float(a.kappa);
+    a.fomega = float(a.omega);
+    a.fnu = float(a.nu);
     a.status = c->d_status;
     for (int i = 0; i < lbk::MAXQ; ++i) a.fref[i] = c->fref[i];
     a.pref = c->pref;

@@ -160,8 +160,9 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
     const int z0 = wk.z, z1 = wk.w;
     const int plane = nx * ny;
 
-    const real pa = real(args.a), pb = real(args.b), pT = real(args.T), pk = real(args.kappa);
-    const real om = real(args.omega), nu = real(args.nu);
+    const real pa = arg_param<real>(args.a, args.fa), pb = arg_param<real>(args.b, args.fb);
+    const real pT = arg_param<real>(args.T, args.fT), pk = arg_param<real>(args.kappa, args.fkappa);
+    const real om = arg_param<real>(args.omega, args.fomega), nu = arg_param<real>(args.nu, args.fnu);
     const real pref = real(args.pref), rsum = real(args.rsum);
 
     // stage-A items: W adjacent region sites each; a_in = in-plane element
@@ -258,16 +259,17 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
             for (int m = 0; m < NA; ++m) {
                 if (a_in[m] >= 0) {
                     if constexpr (PAIR) {
-                        real fa[Q], fb[Q];   // f_0 and the deviations d_i of the two sites
-                        S::dec0x2(r0[m], fa[0], fb[0]);
+                        pair_t<real> f2[Q];   // f_0 and the deviations d_i of the two sites
+                        S::dec0x2(r0[m], f2[0].x, f2[0].y);
                         static_for<1, Q>([&](auto I) {
                             constexpr int i = decltype(I)::value;
-                            S::devix2(ri[m][i - 1], fa[i], fb[i]);
+                            S::devix2(ri[m][i - 1], f2[i].x, f2[i].y);
                         });
-                        st_pair(rho_w + 2 * (tid + m * NT), site_rho(fa, rsum), site_rho(fb, rsum));
+                        const pair_t<real> r2 = site_rho_pair(f2, rsum);
+                        st_pair(rho_w + 2 * (tid + m * NT), r2.x, r2.y);
                         if (keep && a_st[m] >= 0) {
                             if constexpr (RAW) {
-                                st_pair(st_w + a_st[m], fa[0], fb[0]);
+                                st_pair(st_w + a_st[m], f2[0].x, f2[0].y);
                                 static_for<1, Q>([&](auto I) {
                                     constexpr int i = decltype(I)::value;
                                     *reinterpret_cast<RI*>(sd_w + (i - 1) * NT + a_st[m]) = ri[m][i - 1];
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                             } else {
                                 static_for<0, Q>([&](auto I) {
                                     constexpr int i = decltype(I)::value;
-                                    st_pair(st_w + i * NT + a_st[m], fa[i], fb[i]);
+                                    st_pair(st_w + i * NT + a_st[m], f2[i].x, f2[i].y);
                                 });
                             }
                         }

@@ -46,8 +46,19 @@ struct StepArgs {
     const int4* work;  // 3D: per CTA (x0, y0, z0, z1) of its column tile and z chunk
     int pair2d;  // 2D: two sites per halo load (nx even, 32-bit arithmetic)
     double a, b, T, kappa, omega, nu;
+    // the same parameters rounded to float32 (rounded on the host, so a
+    // 32-bit kernel reads them as constant operands instead of converting
+    // doubles inside its loops)
+    float fa, fb, fT, fkappa, fomega, fnu;
     unsigned int* status;
 };
+
+// A parameter in the arithmetic type: the double, or its float32 rounding.
+template <class real>
+__device__ __forceinline__ real arg_param(double d, float f) {
+    if constexpr (sizeof(real) == 4) return f;
+    else return d;
+}
 
 __host__ __device__ __forceinline__ int wrapi(int v, int n) {
     int r = v % n;
@@ -69,6 +80,29 @@ __device__ __forceinline__ real tree_sum(const real* a) {
 template <int Q, class real>
 __device__ __forceinline__ real site_rho(const real (&f)[Q], real rsum) {
     return (rsum + f[0]) + tree_sum<1, Q>(f);
+}
+
+// Two adjacent sites' values of one population: a packed pair, whose float32
+// adds run as one paired instruction.
+template <class real>
+using pair_t = std::conditional_t<sizeof(real) == 4, float2, double2>;
+
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 pair_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+template <int B, int E, class P>
+__device__ __forceinline__ P tree_sum_pair(const P* a) {
+    if constexpr (E - B == 1) return a[B];
+    else {
+        constexpr int M = B + (E - B) / 2;
+        return pair_add(tree_sum_pair<B, M>(a), tree_sum_pair<M, E>(a));
+    }
+}
+
+// site_rho of two sites at once, the same order of additions in each lane.
+template <int Q, class P, class real>
+__device__ __forceinline__ P site_rho_pair(const P (&f)[Q], real rsum) {
+    return pair_add(pair_add(P{rsum, rsum}, f[0]), tree_sum_pair<1, Q>(f));
 }
 
 template <class real>
@@ -377,18 +411,19 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
             if (k < NIT) {
                 const int rx = (k % (RX / 2)) * 2, ry = k / (RX / 2);
                 const size_t q = size_t(wrapi(y0 - HY + ry, ny)) * nx + wrapi(x0 - HX + rx, nx);
-                real fa[Q], fb[Q];
-                S::dec0x2(S::ld0x2(args.src, q), fa[0], fb[0]);
+                pair_t<real> f2[Q];
+                S::dec0x2(S::ld0x2(args.src, q), f2[0].x, f2[0].y);
                 static_for<1, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    S::devix2(S::ldix2(args.src + S::pop_offset(i, pitch), q), fa[i], fb[i]);
+                    S::devix2(S::ldix2(args.src + S::pop_offset(i, pitch), q), f2[i].x, f2[i].y);
                 });
-                st_pair(rho_s + 2 * k, site_rho(fa, rsum), site_rho(fb, rsum));
+                const pair_t<real> r2 = site_rho_pair(f2, rsum);
+                st_pair(rho_s + 2 * k, r2.x, r2.y);
                 if (rx >= HX && rx < HX + TX && ry >= HY && ry < HY + TY) {
                     const int st = (ry - HY) * TX + (rx - HX);
                     static_for<0, Q>([&](auto I) {
                         constexpr int i = decltype(I)::value;
-                        st_pair(stash + i * NT + st, fa[i], fb[i]);
+                        st_pair(stash + i * NT + st, f2[i].x, f2[i].y);
                     });
                 }
             }
