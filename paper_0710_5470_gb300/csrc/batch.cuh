@@ -18,6 +18,7 @@ struct BatchInst {
     int nx, ny, tiles_x, tiles_y;
     int pair;              // two sites per halo load (nx even)
     double a, b, T, kappa, omega, nu;
+    float fa, fb, fT, fkappa, fomega, fnu;   // their float32 roundings
     float pref, rsum;
 };
 
@@ -49,7 +50,8 @@ __global__ void __launch_bounds__(TX* TY) batch_step_kernel(BatchState bs, char*
     const int k = int(it >> 20), t = int(it & 0xFFFFFu);
     const BatchInst& I = bs.inst[k];
     Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
-                 I.kappa, I.omega, I.nu, I.pref, I.rsum, bs.status + k};
+                 I.kappa, I.omega, I.nu, I.fa, I.fb, I.fT, I.fkappa, I.fomega, I.fnu, I.pref, I.rsum,
+                 bs.status + k};
     const int tx = I.tiles_x;
     step2d_tile<D2Q9, FORCING, S, TX, TY>(a, (t % tx) * TX, (t / tx) * TY,
                                           reinterpret_cast<typename S::real*>(smem_raw));

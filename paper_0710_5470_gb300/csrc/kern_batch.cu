@@ -287,6 +287,12 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
         I.kappa = in.kappa;
         I.omega = 1.0 / in.tau;
         I.nu = (in.tau - 0.5) / 3.0;
+        I.fa = float(I.a);
+        I.fb = float(I.b);
+        I.fT = float(I.T);
+        I.fkappa = float(I.kappa);
+        I.fomega = float(I.omega);
+        I.fnu = float(I.nu);
         const double rl = B->rho_l[k];
         const double pref = (storage == LB_F16DEV || storage == LB_BF16DEV) ? rl * in.T / (1 - b * rl) - a * rl * rl : 0.0;
         I.pref = float(pref);

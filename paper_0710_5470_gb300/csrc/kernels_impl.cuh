@@ -26,7 +26,7 @@ struct StepKernelOf {
             step_kernel3d<FORCING, S, TX, TY, PAIR><<<grid, TX * TY, bytes(), st>>>(a);
         } else {
             Tile2DArgs t{a.src_base, a.dst_base, a.pitch, a.nx, a.ny, a.pair2d, a.a, a.b, a.T, a.kappa, a.omega,
-                         a.nu, a.pref, a.rsum, a.status};
+                         a.nu, a.fa, a.fb, a.fT, a.fkappa, a.fomega, a.fnu, a.pref, a.rsum, a.status};
             step_kernel<L, FORCING, S, TX, TY><<<grid, TX * TY, bytes(), st>>>(t);
         }
     }

@@ -119,15 +119,37 @@ __device__ __forceinline__ PlaneParts<real> plane_parts(const real* rho, int rc,
     return o;
 }
 
-// Gradient and Laplacian of plane q from the parts of planes q-1 (lo), q (mid), q+1 (hi).
+// Carried stencil state of one site along the march: the gradient and
+// Laplacian of plane q with the contributions of planes q-1 and q summed,
+// and Dx, Dy, S of plane q (for plane q+1).
 template <class real>
-__device__ __forceinline__ void assemble(const PlaneParts<real>& lo, const PlaneParts<real>& mid,
-                                         const PlaneParts<real>& hi, real (&G)[3], real& lap) {
+struct StencilAcc {
+    real gx, gy, gz, lap;
+    real dx, dy, s;
+};
+
+// Gradient and Laplacian of plane q: its accumulated parts plus plane q+1's (hi).
+template <class real>
+__device__ __forceinline__ void finish(const StencilAcc<real>& a, const PlaneParts<real>& hi, real (&G)[3],
+                                       real& lap) {
     const real twelfth = real(1) / real(12);
-    G[0] = mid.gx + twelfth * (hi.dx + lo.dx);
-    G[1] = mid.gy + twelfth * (hi.dy + lo.dy);
-    G[2] = hi.s - lo.s;
-    lap = real(2) * (mid.lin + hi.s + lo.s) - real(4) * mid.c;
+    G[0] = a.gx + twelfth * hi.dx;
+    G[1] = a.gy + twelfth * hi.dy;
+    G[2] = a.gz + hi.s;
+    lap = a.lap + real(2) * hi.s;
+}
+
+// Start plane q+1 (cur) from its in-plane parts and plane q's Dx, Dy, S.
+template <class real>
+__device__ __forceinline__ void start(StencilAcc<real>& a, const PlaneParts<real>& cur) {
+    const real twelfth = real(1) / real(12);
+    a.gx = cur.gx + twelfth * a.dx;
+    a.gy = cur.gy + twelfth * a.dy;
+    a.gz = -a.s;
+    a.lap = real(2) * (cur.lin + a.s) - real(4) * cur.c;
+    a.dx = cur.dx;
+    a.dy = cur.dy;
+    a.s = cur.s;
 }
 
 // PAIR: stage A moves two adjacent x sites per thread with 2-vector loads
@@ -239,10 +261,12 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
     constexpr bool PREFETCH = sizeof(real) == 4;
     if (PREFETCH) issue();
 
-    // carried stencil parts of the stage-B items: planes p-2 (lo) and p-1 (mid)
-    PlaneParts<real> pl_lo[Lay::NB], pl_mid[Lay::NB];
-    // carried body-force parts of the tile site: U0(q-1), U-(q-1), U-(q-2)
-    real u0_1[3] = {0, 0, 0}, um_1[3] = {0, 0, 0}, um_2[3] = {0, 0, 0};
+    // carried stencil state of the stage-B items (plane p-1 accumulated)
+    StencilAcc<real> acc[Lay::NB];
+#pragma unroll
+    for (int m = 0; m < Lay::NB; ++m) acc[m] = StencilAcc<real>{0, 0, 0, 0, 0, 0, 0};
+    // carried body force of the tile site: -(U0(q-1) + U-(q-2)) and -U-(q-1)
+    real gacc1[3] = {0, 0, 0}, gacc2[3] = {0, 0, 0};
     // equilibrium scheme: G, lap of plane p-1 assembled in stage B
     real Geq[3] = {0, 0, 0}, lapeq = 0;
 
@@ -321,7 +345,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                 const PlaneParts<real> cur = plane_parts(rho_p, b_rc[m], RX);
                 if (assemble_q) {
                     real G[3], lap;
-                    assemble(pl_lo[m], pl_mid[m], cur, G, lap);
+                    finish(acc[m], cur, G, lap);
                     if constexpr (FORCING) {
                         const real g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
                         const real hk = real(0.5) * pk * g2;
@@ -340,8 +364,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                         lapeq = lap;
                     }
                 }
-                pl_lo[m] = pl_mid[m];
-                pl_mid[m] = cur;
+                start(acc[m], cur);
             }
         }
         if constexpr (FORCING) __syncthreads();
@@ -393,10 +416,9 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                 // g(q-1) = -(U+(q) + U0(q-1) + U-(q-2))   (Eq. 28)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    gf[c] = -(up[c] + u0_1[c] + um_2[c]);
-                    um_2[c] = um_1[c];
-                    um_1[c] = um[c];
-                    u0_1[c] = u0[c];
+                    gf[c] = gacc1[c] - up[c];
+                    gacc1[c] = gacc2[c] - u0[c];
+                    gacc2[c] = -um[c];
                 }
             }
         }

@@ -372,6 +372,7 @@ struct Tile2DArgs {
     int nx, ny;
     int pair;            // 1: two sites per halo load (nx even, 32-bit arithmetic)
     double a, b, T, kappa, omega, nu;
+    float fa, fb, fT, fkappa, fomega, fnu;   // their float32 roundings
     float pref, rsum;
     unsigned int* status;
 };
@@ -396,8 +397,9 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
     const int nx = args.nx, ny = args.ny;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const real pa = real(args.a), pb = real(args.b), pT = real(args.T), pk = real(args.kappa);
-    const real om = real(args.omega), nu = real(args.nu);
+    const real pa = arg_param<real>(args.a, args.fa), pb = arg_param<real>(args.b, args.fb);
+    const real pT = arg_param<real>(args.T, args.fT), pk = arg_param<real>(args.kappa, args.fkappa);
+    const real om = arg_param<real>(args.omega, args.fomega), nu = arg_param<real>(args.nu, args.fnu);
     const real pref = real(args.pref), rsum = real(args.rsum);
     const long long pitch = args.pitch;
 
