@@ -38,8 +38,8 @@ KERNEL_SOURCES = ["step3d.cuh", "step_kernel.cuh", "storage.cuh", "lattice.cuh"]
 # fingerprint of the kernel sources they were measured on and the storage.
 # A changed kernel has a new fingerprint and reports traffic = null.
 NCU_TRAFFIC = {
-    ("e3d83f4e399a", "f16dev", 128): 137.67e6,   # 97.36 MB read + 40.31 MB written
-    ("e3d83f4e399a", "f32", 128): 302.64e6,      # 188.85 MB read + 113.79 MB written
+    ("8338080b03d7", "f16dev", 128): 136.90e6,   # 97.16 MB read + 39.74 MB written
+    ("8338080b03d7", "f32", 128): 304.36e6,      # 190.94 MB read + 113.42 MB written
 }
 
 
