@@ -10,6 +10,17 @@ SCHEME = {"equilibrium": 0, "forcing": 1}
 _built = None
 
 
+def sigma_continuum(T, kappa, a=A_VDW, b=B_VDW):
+    """Planar-interface tension of psi + kappa/2 |grad rho|^2 (psi from Eq. 2):
+    sigma = int_{rho_g}^{rho_l} sqrt(2 kappa (psi - mu rho + p)) drho at coexistence."""
+    from scipy.integrate import quad
+    rl, rg = O.coexistence(a, b, T)
+    mu = O.mu0(rl, a, b, T)
+    p = O.p0(rl, a, b, T)
+    psi = lambda r: r * T * np.log(r / (1 - b * r)) - a * r * r - r * T
+    return quad(lambda r: np.sqrt(2 * kappa * max(psi(r) - mu * r + p, 0.0)), rg, rl, limit=200)[0]
+
+
 def library():
     """Build (if stale) and load liblb.so; returns the binding module."""
     global _built

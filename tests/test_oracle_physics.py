@@ -13,9 +13,9 @@ import os
 
 import numpy as np
 import pytest
-from scipy.integrate import quad
 
 from oracle import lb_oracle as O
+from tests.helpers import sigma_continuum
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 A_VDW, B_VDW = 9.0 / 49.0, 2.0 / 21.0
@@ -23,11 +23,7 @@ A_VDW, B_VDW = 9.0 / 49.0, 2.0 / 21.0
 
 def _sigma_continuum(T, kappa):
     """Planar-interface tension of psi + kappa/2 |grad rho|^2 (psi from Eq. 2)."""
-    rl, rg = O.coexistence(A_VDW, B_VDW, T)
-    mu = O.mu0(rl, A_VDW, B_VDW, T)
-    p = O.p0(rl, A_VDW, B_VDW, T)
-    psi = lambda r: r * T * np.log(r / (1 - B_VDW * r)) - A_VDW * r * r - r * T
-    return quad(lambda r: np.sqrt(2 * kappa * max(psi(r) - mu * r + p, 0.0)), rg, rl, limit=200)[0]
+    return sigma_continuum(T, kappa)
 
 
 def _tangential_force(wkw=None, skw=None, n=64, R=20.0, width=3.0):
