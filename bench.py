@@ -42,6 +42,39 @@ NCU_TRAFFIC = {
     ("8338080b03d7", "f32", 128): 304.36e6,      # 190.94 MB read + 113.42 MB written
 }
 
+# Executed floating-point operations per lattice update of the step kernel,
+# from ncu's per-opcode instruction counts of one launch divided by the sites
+# (FFMA, DFMA, FADD2 = 2 flops; FADD, FMUL, DADD, DMUL = 1), keyed like
+# NCU_TRAFFIC.  They include the halo recomputation, so they are the work the
+# FP units do, not an algorithmic minimum.
+NCU_FLOPS = {
+    ("8338080b03d7", "f16dev", 128): 484.1,   # FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1 per site
+    ("8338080b03d7", "f32", 128): 484.1,      # the same counts
+    ("8338080b03d7", "f64", 128): 525.6,      # DFMA 129.0, DADD 197.4, DMUL 70.2 per site
+}
+# FP64-pipe instructions per lattice update of the float64 step (DFMA, DADD,
+# DMUL, DSETP, F2F): each occupies the pipe like one FMA, so their rate against
+# half the FMA flop rate is the pipe's utilisation.
+NCU_FP64_PIPE_OPS = {("8338080b03d7", "f64", 128): 401.7}
+
+
+def alu_roofline(fp: str, storage: str, n: int, glups: float, fma: dict | None):
+    """Executed flops per second of the step kernel against the GPU's measured
+    FMA rate (lb_fma_peak; float64 units for float64 storage, float32 otherwise)."""
+    flop = NCU_FLOPS.get((fp, storage, n))
+    if flop is None or not fma:
+        return None
+    prec = "f64" if storage == "f64" else "f32"
+    achieved = flop * glups * 1e9 / 1e12
+    out = {"bound": "alu", "precision": prec, "flop_per_lu": flop, "achieved": achieved, "peak": fma[prec],
+           "unit": "TFLOP/s", "frac": achieved / fma[prec],
+           "peak_source": f"lb_fma_peak {prec} (measured in this run: FMA chains on every SM)"}
+    ops = NCU_FP64_PIPE_OPS.get((fp, storage, n))
+    if ops is not None:
+        out["fp64_pipe_ops_per_lu"] = ops
+        out["pipe_frac"] = ops * glups * 1e9 / (fma[prec] * 1e12 / 2)
+    return out
+
 
 def kernel_fingerprint() -> str:
     import hashlib
@@ -274,6 +307,9 @@ def run_native(args):
     t_launch = ms_local / args.steps / 1e3
     achieved = bpl * sites / t_launch / 1e9
     traffic = NCU_TRAFFIC.get((fp, args.storage, n))
+    # FMA rates of this GPU (float64 and float32), best of three short launches
+    fma = {"f64": max(lb.fma_peak(0) for _ in range(3)), "f32": max(lb.fma_peak(1) for _ in range(3))}
+    alu = alu_roofline(fp, args.storage, n, sites / t_launch / 1e9, fma)
 
     # end to end through the C ABI with host buffers (pinned): upload the initial
     # density, run the steps, download rho and u
@@ -317,6 +353,7 @@ def run_native(args):
                                "roofline": {"bound": "hbm", "achieved": vach, "peak": peak, "unit": "GB/s",
                                             "frac": vach / peak, "bytes_per_lu": vb,
                                             "traffic": NCU_TRAFFIC.get((fp, sname, n))},
+                               "alu_roofline": alu_roofline(fp, sname, n, sites / (vms / vsteps / 1e3) / 1e9, fma),
                                "max_v": vst["max_v"]}
 
     # time to steady state (second half of the metric): plain float64, one
@@ -364,6 +401,8 @@ def run_native(args):
                          "frac": achieved / peak, "traffic": traffic, "bytes_per_lu": bpl,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                          "kernel_fingerprint": fp},
+            "alu_roofline": alu,
+            "fma_peak_tflops": fma,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

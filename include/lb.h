@@ -331,6 +331,21 @@ lb_status lb_ws3_decode(int nx, int ny, int nz, const double* rho_tanh, double r
 lb_status lb_field_stats_noalloc(const double* rho, const double* u, const double* v, int dim, long long n,
                                  double* out, void* cuda_stream);
 
+/* ---- FMA rate (measurement helper; no counterpart in the paper) --------------
+ *
+ * lb_fma_peak measures the fused multiply-add rate of the current GPU, the
+ * denominator of the ALU roofline of the step kernels (the float64 step is
+ * bound by the FP64 units rather than by HBM).  precision: 0 = float64,
+ * 1 = float32.  It launches 4 CTAs of 256 threads per SM; every thread runs 8
+ * independent chains of iters FMAs each.  The launch is timed with CUDA
+ * events on the legacy default stream and the call returns after it, with
+ * the rate in TFLOP/s (2 flops per FMA) in *tflops.  A warm-up launch of at
+ * most 64 iterations precedes it.  It allocates and frees one element of
+ * device memory.  iters outside [1, 2^24], another precision or a NULL tflops
+ * return LB_EINVAL; a CUDA failure returns LB_ECUDA.  Pick iters so that the
+ * launch runs for milliseconds (float64 ~4000, float32 ~2e5 on a GB300). */
+lb_status lb_fma_peak(int precision, int iters, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -119,6 +119,7 @@ _SIGNATURES = {
                                 _DPTR]),
     "lb_field_stats_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_longlong,
                                          C.c_void_p, C.c_void_p]),
+    "lb_fma_peak": (C.c_int, [C.c_int, C.c_int, _DPTR]),
 }
 
 
@@ -165,6 +166,18 @@ def field_stats_noalloc(rho_ptr: int, u_ptr: int, v_ptr: int, dim: int, n: int, 
     _check(load_library().lb_field_stats_noalloc(C.c_void_p(rho_ptr), C.c_void_p(u_ptr), C.c_void_p(v_ptr),
                                                  int(dim), int(n), C.c_void_p(out_ptr),
                                                  C.c_void_p(stream) if stream else None))
+
+
+F64_FMA_ITERS, F32_FMA_ITERS = 4000, 200000
+
+
+def fma_peak(precision: int, iters: int | None = None) -> float:
+    """lb_fma_peak: the GPU's FMA rate in TFLOP/s, precision 0 = float64, 1 = float32."""
+    if iters is None:
+        iters = F64_FMA_ITERS if precision == 0 else F32_FMA_ITERS
+    out = C.c_double()
+    _check(load_library().lb_fma_peak(int(precision), int(iters), C.byref(out)))
+    return out.value
 
 
 def version() -> str:

@@ -11,11 +11,13 @@ R the equimolar radius (3 V / 4 pi)^(1/3), V = (sum rho - rho_out N) /
 the GPU solver to a closed form.  In a closed box the drop gives mass to the
 vapour until the vapour's chemical potential matches the curved interface;
 below a size that depends on the box it evaporates completely (a drop of
-R = 12 does in 64^3), so the small drop of the scaling check (R = 14,
-ending near R = 12) sits in a 48^3 box.  Tolerances: the 2D oracle meets the
-same law within 4% at R = 20 (curvature corrections of order width / R);
-here 5% at R = 18, and dP R constant between the R = 14 and R = 22 drops
-within 3%; the 32- and 16-bit storage formats give dP R within 1% of
+R = 12 does in 64^3).  The interface at T = 0.56 (0.98 T_c) is several
+sites wide, so small drops show the curvature correction to the law:
+measured dP R / 2 sigma = 0.89 at R_e = 12.5 (R = 14 in 48^3), 0.969 at
+16.4, 0.976 at 21.3.  Tolerances: the 2D oracle meets the same law within
+4% at R = 20; here 5% at R = 18 (R_e 16.4), dP R constant within 3%
+between R_e ~ 16 and ~ 29 (R = 30 in 96^3), the R_e 12.5 drop below both
+and within 15%; the 32- and 16-bit storage formats give dP R within 1% of
 float64.  D2Q9 (dP =
 sigma / R, area instead of volume): a 128^2 box, R = 20 and 30, 10^4 steps,
 the same bounds.
@@ -64,10 +66,13 @@ def test_laplace_law_3d_float64():
 
 
 def test_laplace_pressure_scales_as_inverse_radius_3d():
-    dP1, R1 = laplace(0, 14.0, 48)
-    dP2, R2 = laplace(0, 22.0, 64)
-    print(f"dP R: {dP1 * R1:.5e} (R_e {R1:.3f}), {dP2 * R2:.5e} (R_e {R2:.3f})")
-    assert abs(dP1 * R1 / (dP2 * R2) - 1) < 0.03
+    sigma = sigma_continuum(T, KAPPA)
+    runs = [laplace(0, 14.0, 48), laplace(0, 18.0, 64), laplace(0, 30.0, 96)]
+    r = [dP * R_e / (2 * sigma) for dP, R_e in runs]
+    print("dP R / 2 sigma:", ", ".join(f"{x:.4f} (R_e {R_e:.2f})" for x, (_, R_e) in zip(r, runs)))
+    assert abs(r[1] / r[2] - 1) < 0.03
+    assert abs(r[2] - 1) < 0.05
+    assert r[0] < min(r[1], r[2]) and abs(r[0] - 1) < 0.15
 
 
 @pytest.mark.parametrize("storage", [1, 2, 3], ids=["f32", "f16dev", "bf16dev"])

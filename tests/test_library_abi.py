@@ -76,3 +76,11 @@ def test_missing_library_fails_loudly(tmp_path):
             lb.load_library(str(tmp_path / "nope.so"))
     finally:
         lb._lib = saved
+
+
+def test_fma_peak_arguments_rejected_before_device_work():
+    lb = library()
+    for args in ((2, 100), (0, 0), (1, (1 << 24) + 1)):
+        with pytest.raises(lb.LBError) as e:
+            lb.fma_peak(*args)
+        assert e.value.status == 1
