@@ -27,6 +27,7 @@ ones.  All arithmetic runs in the library; this module moves arrays between
 the calls and reads the clock.
 
   python -m paper_0710_5470_gb300.steady [--count 16] [--warm]   (one JSON line)
+  python -m paper_0710_5470_gb300.steady --sweep [--count 256]   (the whole sweep, batched ways only)
 """
 from __future__ import annotations
 
@@ -203,19 +204,67 @@ def experiment(count=16, seed=0, every=100, max_steps=200000, band=0.05, tol_rho
     return out
 
 
+def _sweep_summary(res, sites):
+    """Wall time, lattice updates done (sum over instances of the steps it ran
+    x its sites) and their rate, and the retirement counts of a batched run."""
+    st = res["status"]
+    lu = sum(int(n) * int(k) for n, k in zip(res["steps"], sites))
+    ok = [k for k, s in enumerate(st) if s == 0]
+    return {"seconds": res["seconds"], "instances": len(st), "converged": len(ok),
+            "unstable": sum(s == 4 for s in st), "not_converged": sum(s == 5 for s in st),
+            "lattice_updates": lu, "mlups": lu / res["seconds"] / 1e6, "batch_steps": res["batch_steps"],
+            "mean_steps_converged": float(np.mean([res["steps"][k] for k in ok])) if ok else None}
+
+
+def sweep(count=256, seed=0, every=100, max_steps=200000, band=0.05, tol_rho=1e-3, hold=10,
+          arms=("f64", "f16dev", "f32")):
+    """The whole parameter sweep (inputs.sweep_instances(seed, count)), one
+    batch per way.  float64 to the tol test (max|du| < 1e-10 per ``every``
+    steps, at most ``max_steps``) gives the reference steady states; each
+    way in ``arms`` (float64 included, for the like-for-like comparison) then
+    runs the instances that converged in float64 to the reference test.  Per way: wall time from solver creation to the last
+    instance retired, lattice updates done and their rate, retirement counts,
+    and (reduced storage) the accuracy against the float64 steady states."""
+    from . import inputs
+    inst = W.instances_from_sweep(inputs.sweep_instances(seed=seed, count=count))
+    sites = [d["nx"] * d["ny"] for d in inst]
+    f64 = fast(inst, storage=lb.F64, tol=1e-10, every=every, max_steps=max_steps)
+    out = {"sweep": {"seed": seed, "count": count, "sites": int(sum(sites)), "every": every,
+                     "max_steps": max_steps},
+           "test": {"tol_f64": 1e-10, "band": band, "tol_rho": tol_rho, "hold": hold},
+           "batch_f64_tol": _sweep_summary(f64, sites)}
+    ok = [k for k, s in enumerate(f64["status"]) if s == 0]
+    refs = [(f64["umax"][k], f64["rho_max"][k], f64["rho_min"][k]) for k in ok]
+    ref = {"final": [f64["final"][k] for k in ok], "status": [0] * len(ok)}
+    for a in arms:
+        r = fast([inst[k] for k in ok], storage=ARMS[a], every=every, max_steps=max_steps, refs=refs, band=band,
+                 tol_rho=tol_rho, hold=hold)
+        summ = _sweep_summary(r, [sites[k] for k in ok])
+        c = [x for x in compare(ref, r) if x]
+        for key in ("max_u_rel_err", "rho_max_err", "rho_min_err"):
+            summ[key + "_max"] = max(x[key] for x in c) if c else None
+        out["batch_" + a + "_ref"] = summ
+    return out
+
+
 def main():
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    p.add_argument("--count", type=int, default=16)
+    p.add_argument("--count", type=int, default=None, help="instances (default 16; 256 with --sweep)")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--every", type=int, default=100)
     p.add_argument("--max-steps", type=int, default=200000)
     p.add_argument("--tol-rho", type=float, default=1e-3)
     p.add_argument("--warm", action="store_true")
+    p.add_argument("--sweep", action="store_true",
+                   help="the whole sweep (default 256 instances), one batch per way (sweep())")
     a = p.parse_args()
     from . import build
     build.build()
     lb.load_library()
-    print(json.dumps(experiment(a.count, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho, warm=a.warm)), flush=True)
+    if a.sweep:
+        print(json.dumps(sweep(a.count or 256, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho)), flush=True)
+        return
+    print(json.dumps(experiment(a.count or 16, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho, warm=a.warm)), flush=True)
 
 
 if __name__ == "__main__":

@@ -154,3 +154,19 @@ def test_maximum_instance_count_matches_single_contexts():
             ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
             ctx.step(12)
             assert np.array_equal(ctx.get_populations(), f), k
+
+
+def test_whole_sweep_driver_small():
+    """steady.sweep on the first 4 sweep instances: the float64 batch gives the
+    references, the reduced-storage batches run the converged ones to the
+    reference test; counts and update totals are consistent."""
+    library()
+    from paper_0710_5470_gb300 import steady
+    res = steady.sweep(count=4, seed=0, max_steps=30000, arms=("f16dev",))
+    f64, f16 = res["batch_f64_tol"], res["batch_f16dev_ref"]
+    assert f64["instances"] == 4
+    assert f64["converged"] + f64["unstable"] + f64["not_converged"] == 4
+    assert f16["instances"] == f64["converged"]
+    assert f64["lattice_updates"] > 0 and f64["mlups"] > 0
+    if f16["converged"]:
+        assert f16["max_u_rel_err_max"] < 0.1
