@@ -65,6 +65,17 @@ __host__ __device__ __forceinline__ int wrapi(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
+// wrapi for the per-site offsets of the tile kernels: one compare-and-add
+// covers v in [-n, 2n) (a lattice offset at most n outside [0, n)); anything
+// further out (lattices narrower than the halo) takes the integer modulo.
+// Same result as wrapi for every v.
+__host__ __device__ __forceinline__ int wrap_near(int v, int n) {
+    if (v < 0) v += n;
+    else if (v >= n) v -= n;
+    if (unsigned(v) >= unsigned(n)) v = wrapi(v, n);
+    return v;
+}
+
 // Sum of a[B], ..., a[E-1] as a balanced tree (short dependency chains).
 template <int B, int E, class real>
 __device__ __forceinline__ real tree_sum(const real* a) {
@@ -412,7 +423,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
             const int k = tid + m * NT;
             if (k < NIT) {
                 const int rx = (k % (RX / 2)) * 2, ry = k / (RX / 2);
-                const size_t q = size_t(wrapi(y0 - HY + ry, ny)) * nx + wrapi(x0 - HX + rx, nx);
+                const size_t q = size_t(wrap_near(y0 - HY + ry, ny)) * nx + wrap_near(x0 - HX + rx, nx);
                 pair_t<real> f2[Q];
                 S::dec0x2(S::ld0x2(args.src, q), f2[0].x, f2[0].y);
                 static_for<1, Q>([&](auto I) {
@@ -436,7 +447,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
             const int k = tid + m * NT;
             if (k < RN) {
                 const int rx = k % RX, ry = k / RX;
-                const size_t q = size_t(wrapi(y0 - HY + ry, ny)) * nx + wrapi(x0 - HX + rx, nx);
+                const size_t q = size_t(wrap_near(y0 - HY + ry, ny)) * nx + wrap_near(x0 - HX + rx, nx);
                 real f[Q];
                 f[0] = S::dec0(S::ld0(args.src, q));
                 static_for<1, Q>([&](auto I) {
@@ -537,8 +548,8 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
         if (!(rho > real(0)) || !(rho < real(1e30))) atomicOr(args.status, 1u);
         real out[Q];
         collide<L, FORCING, real>(f, rho, G, lap, g, pa, pb, pT, pk, om, nu, pref, rsum, out);
-        const int xw[3] = {wrapi(xs - 1, nx), xs, wrapi(xs + 1, nx)};
-        const int yr[3] = {wrapi(ys - 1, ny) * nx, ys * nx, wrapi(ys + 1, ny) * nx};
+        const int xw[3] = {wrap_near(xs - 1, nx), xs, wrap_near(xs + 1, nx)};
+        const int yr[3] = {wrap_near(ys - 1, ny) * nx, ys * nx, wrap_near(ys + 1, ny) * nx};
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             const size_t idx = size_t(yr[1 + L::ey(i)] + xw[1 + L::ex(i)]);

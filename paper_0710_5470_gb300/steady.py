@@ -28,6 +28,7 @@ the calls and reads the clock.
 
   python -m paper_0710_5470_gb300.steady [--count 16] [--warm]   (one JSON line)
   python -m paper_0710_5470_gb300.steady --sweep [--count 256]   (the whole sweep, batched ways only)
+  python -m paper_0710_5470_gb300.steady --throughput [--storage f16dev] [--steps 200]   (batched step rate)
 """
 from __future__ import annotations
 
@@ -247,6 +248,31 @@ def sweep(count=256, seed=0, every=100, max_steps=200000, band=0.05, tol_rho=1e-
     return out
 
 
+def throughput(storage=lb.F16DEV, steps=200, count=256, seed=0, scheme=lb.FORCING, autotune_steps=5):
+    """Batched step rate on the lattice sizes of the sweep
+    (inputs.sweep_instances(seed, count)) at parameters where every instance
+    is stable (T = 0.55, kappa = 0.01, tau = 1): wall clock around ``steps``
+    steps after autotuning and 10 warm-up steps, closed by a read of the
+    batch's check buffer (a stream synchronisation).  Returns the sites,
+    the chosen tile and the rate in GLUPS."""
+    from . import inputs
+    inst = W.instances_from_sweep(inputs.sweep_instances(seed=seed, count=count))
+    for d in inst:
+        d.update(T=0.55, kappa=0.01, tau=1.0)
+    sites = sum(d["nx"] * d["ny"] for d in inst)
+    with lb.Batch(inst, W.A_VDW, W.B_VDW, scheme=scheme, storage=storage) as bt:
+        bt.init_drops(2.0)
+        tile = bt.autotune(autotune_steps) if autotune_steps > 0 else None
+        bt.step(10)
+        bt.last_check()
+        t0 = time.perf_counter()
+        bt.step(steps)
+        bt.last_check()
+        dt = time.perf_counter() - t0
+    return {"instances": count, "sites": sites, "steps": steps, "tile": tile, "seconds": dt,
+            "glups": sites * steps / dt / 1e9}
+
+
 def main():
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     p.add_argument("--count", type=int, default=None, help="instances (default 16; 256 with --sweep)")
@@ -257,10 +283,17 @@ def main():
     p.add_argument("--warm", action="store_true")
     p.add_argument("--sweep", action="store_true",
                    help="the whole sweep (default 256 instances), one batch per way (sweep())")
+    p.add_argument("--throughput", action="store_true",
+                   help="batched step rate on the sweep's sizes at stable parameters (throughput())")
+    p.add_argument("--storage", default="f16dev", choices=list(ARMS), help="storage of --throughput")
+    p.add_argument("--steps", type=int, default=200, help="timed steps of --throughput")
     a = p.parse_args()
     from . import build
     build.build()
     lb.load_library()
+    if a.throughput:
+        print(json.dumps(throughput(ARMS[a.storage], a.steps, a.count or 256, a.seed)), flush=True)
+        return
     if a.sweep:
         print(json.dumps(sweep(a.count or 256, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho)), flush=True)
         return
