@@ -133,6 +133,11 @@ struct lb_ctx {
     double* p2_rho = nullptr;   // N
     double* p2_gl = nullptr;    // 3N: d_x rho, d_y rho, lap rho
     double* p2_mp = nullptr;    // 2N: M'_xx, M'_xy
+    // CUDA graphs of GRAPH_STEPS fused steps, one per starting buffer, captured on
+    // a private stream and launched on `stream` (lb_step with nsteps >= GRAPH_STEPS)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+    bool graph_failed = false;
 };
 
 namespace {
@@ -177,6 +182,31 @@ lb_status record(lb_ctx* c, cudaError_t e, const char* where) {
     if (e == cudaSuccess) return LB_OK;
     c->sticky = LB_ECUDA;
     return cuda_fail(e, where);
+}
+
+constexpr int GRAPH_STEPS = 64;
+
+// Captures GRAPH_STEPS launches of launch_one, starting from buffer c->cur, into
+// an executable graph (on the context's private capture stream).
+template <class F>
+cudaError_t capture_steps(lb_ctx* c, F& launch_one, cudaGraphExec_t* exec) {
+    cudaError_t e = cudaSuccess;
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    int cur = c->cur;
+    cudaError_t le = cudaSuccess;
+    for (int j = 0; j < GRAPH_STEPS && le == cudaSuccess; ++j) {
+        le = launch_one(cur, c->cap_stream);
+        cur = 1 - cur;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    return e;
 }
 
 lb_status ensure_work(lb_ctx* c) {
@@ -374,6 +404,9 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->p2_rho);
     cudaFree(c->p2_gl);
     cudaFree(c->p2_mp);
+    for (cudaGraphExec_t g : c->step_graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
     return LB_OK;
 }
@@ -539,19 +572,53 @@ lb_status lb_step(lb_ctx* c, int nsteps) {
     for (int i = 0; i < lbk::MAXQ; ++i) a.fref[i] = c->fref[i];
     a.pref = c->pref;
     a.rsum = c->rsum;
-    for (int k = 0; k < nsteps; ++k) {
+    // one fused step from buffer `cur` into the other, on stream st
+    auto launch_one = [&](int cur, cudaStream_t st) -> cudaError_t {
         for (int i = 0; i < c->Q; ++i) {
-            a.src[i] = c->fbuf + pop_offset(c, i, c->cur);
-            a.dst[i] = c->fbuf + pop_offset(c, i, 1 - c->cur);
+            a.src[i] = c->fbuf + pop_offset(c, i, cur);
+            a.dst[i] = c->fbuf + pop_offset(c, i, 1 - cur);
         }
         a.src_base = a.src[0];
         a.dst_base = a.dst[0];
         a.pitch = (long long)c->pitch;
-        cudaError_t e = c->free_params
-                            ? lbk::free2d_step(c->fw, phys2(c), c->p.scheme == LB_SCHEME_FORCING, pop_base(c, c->cur),
-                                               pop_base(c, 1 - c->cur), (long long)c->pitch, c->p.nx, c->p.ny,
-                                               c->p2_rho, c->p2_gl, c->p2_mp, c->d_status, c->stream)
-                            : c->ks.step(a, c->grid, c->stream);
+        return c->free_params
+                   ? lbk::free2d_step(c->fw, phys2(c), c->p.scheme == LB_SCHEME_FORCING, pop_base(c, cur),
+                                      pop_base(c, 1 - cur), (long long)c->pitch, c->p.nx, c->p.ny, c->p2_rho,
+                                      c->p2_gl, c->p2_mp, c->d_status, st)
+                   : c->ks.step(a, c->grid, st);
+    };
+    int k = 0;
+    // long runs: replay a captured graph of GRAPH_STEPS steps (an even count, so a
+    // replay ends in the buffer it started from).  The graph is captured after one
+    // ordinary launch (which sets the kernel's attributes) and kept for the
+    // context's lifetime: the buffers, work list and parameters it holds are fixed.
+    // If the capture fails the steps run as ordinary launches (the same kernels).
+    if (!c->free_params && !c->graph_failed && nsteps > GRAPH_STEPS) {
+        if (!c->step_graph[c->cur]) {
+            cudaError_t e = launch_one(c->cur, c->stream);
+            if (e != cudaSuccess) return record(c, e, "step kernel");
+            c->cur = 1 - c->cur;
+            ++c->step;
+            ++k;
+            if (!c->step_graph[c->cur]) {
+                cudaGraphExec_t exec = nullptr;
+                if (capture_steps(c, launch_one, &exec) == cudaSuccess) {
+                    c->step_graph[c->cur] = exec;
+                } else {
+                    cudaGetLastError();
+                    c->graph_failed = true;
+                }
+            }
+        }
+        cudaGraphExec_t g = c->step_graph[c->cur];
+        for (; g && k + GRAPH_STEPS <= nsteps; k += GRAPH_STEPS) {
+            cudaError_t e = cudaGraphLaunch(g, c->stream);
+            if (e != cudaSuccess) return record(c, e, "step graph launch");
+            c->step += GRAPH_STEPS;
+        }
+    }
+    for (; k < nsteps; ++k) {
+        cudaError_t e = launch_one(c->cur, c->stream);
         if (e != cudaSuccess) return record(c, e, "step kernel");
         c->cur = 1 - c->cur;
         ++c->step;
