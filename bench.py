@@ -38,8 +38,8 @@ KERNEL_SOURCES = ["step3d.cuh", "step_kernel.cuh", "storage.cuh", "lattice.cuh"]
 # fingerprint of the kernel sources they were measured on and the storage.
 # A changed kernel has a new fingerprint and reports traffic = null.
 NCU_TRAFFIC = {
-    ("8338080b03d7", "f16dev", 128): 136.90e6,   # 97.16 MB read + 39.74 MB written
-    ("8338080b03d7", "f32", 128): 304.36e6,      # 190.94 MB read + 113.42 MB written
+    ("0a56c3ba8029", "f16dev", 128): 137.92e6,   # 97.35 MB read + 40.57 MB written
+    ("0a56c3ba8029", "f32", 128): 306.32e6,      # 191.48 MB read + 114.84 MB written
 }
 
 # Executed floating-point operations per lattice update of the step kernel,
@@ -48,14 +48,14 @@ NCU_TRAFFIC = {
 # NCU_TRAFFIC.  They include the halo recomputation, so they are the work the
 # FP units do, not an algorithmic minimum.
 NCU_FLOPS = {
-    ("8338080b03d7", "f16dev", 128): 484.1,   # FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1 per site
-    ("8338080b03d7", "f32", 128): 484.1,      # the same counts
-    ("8338080b03d7", "f64", 128): 525.6,      # DFMA 129.0, DADD 197.4, DMUL 70.2 per site
+    ("0a56c3ba8029", "f16dev", 128): 484.1,   # FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1 per site
+    ("0a56c3ba8029", "f32", 128): 484.1,      # the same counts
+    ("0a56c3ba8029", "f64", 128): 525.6,      # DFMA 129.0, DADD 197.4, DMUL 70.2 per site
 }
 # FP64-pipe instructions per lattice update of the float64 step (DFMA, DADD,
 # DMUL, DSETP, F2F): each occupies the pipe like one FMA, so their rate against
 # half the FMA flop rate is the pipe's utilisation.
-NCU_FP64_PIPE_OPS = {("8338080b03d7", "f64", 128): 401.7}
+NCU_FP64_PIPE_OPS = {("0a56c3ba8029", "f64", 128): 401.7}
 
 
 def alu_roofline(fp: str, storage: str, n: int, glups: float, fma: dict | None):
@@ -96,7 +96,7 @@ def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=4000)
-    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=100)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--storage", default="f16dev", choices=list(BYTES_POP))
     p.add_argument("--edge", type=int, default=WORKLOAD["n"], help="lattice edge (default 128)")
@@ -247,14 +247,16 @@ def run_reference(args):
 
 
 def time_steps(ctx, stream, steps, dist=None):
-    """CUDA-event time (ms) of exactly `steps` launches on the context's stream."""
+    """CUDA-event time (ms) of exactly `steps` fused steps, one kernel launch
+    each, run by one lb_step call on the context's stream (lb_step replays
+    its captured graphs of 64 steps; they are captured in the warm-up when
+    it is longer than 64 steps, else at the start of this call)."""
     import torch
     barrier(dist)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(steps):
-        ctx.step(1)
+    ctx.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(dist)

@@ -269,6 +269,8 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
     real gacc1[3] = {0, 0, 0}, gacc2[3] = {0, 0, 0};
     // equilibrium scheme: G, lap of plane p-1 assembled in stage B
     real Geq[3] = {0, 0, 0}, lapeq = 0;
+    // a density that is not positive and finite at any collided site (reported once at the end)
+    bool bad = false;
 
     for (int p = pstart; p < pend; ++p) {
         const int it = p - pstart;
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
                 G[2] = Geq[2];
                 lap = lapeq;
             }
-            if (!(rho > real(0)) || !(rho < real(1e30))) atomicOr(args.status, 1u);
+            bad |= !(rho > real(0)) || !(rho < real(1e30));
             real out[Q];
             collide<L, FORCING, real>(f, rho, G, lap, gf, pa, pb, pT, pk, om, nu, pref, rsum, out);
             static_for<0, Q>([&](auto I) {
@@ -470,6 +472,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
         }
         if constexpr (!Lay::OPEN) __syncthreads();
     }
+    if (bad) atomicOr(args.status, 1u);
 }
 
 }  // namespace lbk
