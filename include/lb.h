@@ -138,7 +138,10 @@ lb_status lb_get_populations(lb_ctx* ctx, double* f);
 /* Advance nsteps >= 0 time steps of Eq. 4: one fused kernel per step
  * (moments, stencils, equilibrium, force, BGK, streaming).  Asynchronous on
  * the context's stream; a non-finite density raises the context's status,
- * reported by the next synchronising call. */
+ * reported by the next synchronising call.  With nsteps > 64 the steps run
+ * as replays of a CUDA graph of 64 kernel launches (captured once per
+ * starting buffer on a private stream of the context, after one ordinary
+ * launch) plus ordinary launches for the rest; the results are identical. */
 lb_status lb_step(lb_ctx* ctx, int nsteps);
 
 /* Wait for queued work; returns the context's status. */
