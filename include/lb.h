@@ -135,6 +135,16 @@ lb_status lb_init_fields(lb_ctx* ctx, const double* rho, const double* u);
 lb_status lb_set_populations(lb_ctx* ctx, const double* f);
 lb_status lb_get_populations(lb_ctx* ctx, double* f);
 
+/* Read the populations of a box of the periodic lattice: sites (x0 + x, y0 + y, z0 + z)
+ * wrapped into the lattice, 0 <= x < bx, 0 <= y < by, 0 <= z < bz, decoded to float64
+ * into f (caller-owned host array of Q*bx*by*bz doubles, layout [i][z][y][x] of the
+ * box).  For lattices too large to read whole.  Origins in [0, n) and sizes in [1, n]
+ * per axis (n the lattice size; D2Q9: z0 = 0, bz = 1), at most 2^LB_BOX_MAX_LOG2_SITES
+ * sites; otherwise LB_EINVAL.  Allocates and frees a device staging buffer of the
+ * box's size and synchronises the context's stream. */
+#define LB_BOX_MAX_LOG2_SITES 24
+lb_status lb_get_populations_box(lb_ctx* ctx, int x0, int y0, int z0, int bx, int by, int bz, double* f);
+
 /* Advance nsteps >= 0 time steps of Eq. 4: one fused kernel per step
  * (moments, stencils, equilibrium, force, BGK, streaming).  Asynchronous on
  * the context's stream; a non-finite density raises the context's status,

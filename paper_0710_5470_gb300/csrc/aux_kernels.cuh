@@ -175,6 +175,24 @@ __global__ void get_pops_kernel(PopPtrs src, size_t n, double* out) {
     }
 }
 
+// Populations of the box [x0, x0 + bx) x [y0, y0 + by) x [z0, z0 + bz) of the
+// periodic lattice (coordinates wrapped), decoded to float64, [i][z][y][x] of the box.
+template <class L, class S>
+__global__ void get_box_kernel(PopPtrs src, Grid3 g, int x0, int y0, int z0, int bx, int by, int bz, double* out) {
+    const size_t n = size_t(bx) * by * bz;
+    for (size_t k = blockIdx.x * size_t(blockDim.x) + threadIdx.x; k < n; k += size_t(gridDim.x) * blockDim.x) {
+        const int x = int(k % bx), y = int((k / bx) % by), z = int(k / (size_t(bx) * by));
+        // origins are in [0, n) and box sizes at most n: one subtraction wraps (64-bit sums)
+        long long xx = (long long)x0 + x, yy = (long long)y0 + y, zz = (long long)z0 + z;
+        if (xx >= g.nx) xx -= g.nx;
+        if (yy >= g.ny) yy -= g.ny;
+        if (zz >= g.nz) zz -= g.nz;
+        const size_t idx = (size_t(zz) * g.ny + size_t(yy)) * g.nx + size_t(xx);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) out[i * n + k] = double(S::load(i, src.p[i], idx, src.fref[i]));
+    }
+}
+
 template <class L, class S>
 __global__ void set_pops_kernel(PopPtrs dst, size_t n, const double* in) {
     for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {

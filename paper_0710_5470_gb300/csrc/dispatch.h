@@ -22,6 +22,8 @@ struct LbKernelSet {
     cudaError_t (*velocity_v)(const double* rho, const double* u, const double* mp, lbk::Grid3, double* v,
                               cudaStream_t) = nullptr;
     cudaError_t (*get_pops)(const lbk::PopPtrs&, size_t n, double* out, cudaStream_t) = nullptr;
+    cudaError_t (*get_box)(const lbk::PopPtrs&, lbk::Grid3, const int (&origin)[3], const int (&box)[3], double* out,
+                           cudaStream_t) = nullptr;
     cudaError_t (*set_pops)(const lbk::PopPtrs&, size_t n, const double* in, cudaStream_t) = nullptr;
 };
 

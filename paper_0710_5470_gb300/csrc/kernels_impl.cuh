@@ -76,6 +76,12 @@ struct Launchers {
         velocity_v_kernel<L><<<lbk_aux_blocks(n), 256, 0, st>>>(rho, u, mp, g, v);
         return cudaGetLastError();
     }
+    static cudaError_t get_box(const PopPtrs& p, Grid3 g, const int (&o)[3], const int (&b)[3], double* out,
+                               cudaStream_t st) {
+        const size_t n = size_t(b[0]) * b[1] * b[2];
+        get_box_kernel<L, S><<<lbk_aux_blocks(n), 256, 0, st>>>(p, g, o[0], o[1], o[2], b[0], b[1], b[2], out);
+        return cudaGetLastError();
+    }
     static cudaError_t get_pops(const PopPtrs& p, size_t n, double* out, cudaStream_t st) {
         get_pops_kernel<L, S><<<lbk_aux_blocks(n), 256, 0, st>>>(p, n, out);
         return cudaGetLastError();
@@ -99,6 +105,7 @@ struct Launchers {
         k.mprime = &mprime;
         k.velocity_v = &velocity_v;
         k.get_pops = &get_pops;
+        k.get_box = &get_box;
         k.set_pops = &set_pops;
         return k;
     }

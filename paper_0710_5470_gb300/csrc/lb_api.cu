@@ -209,19 +209,34 @@ cudaError_t capture_steps(lb_ctx* c, F& launch_one, cudaGraphExec_t* exec) {
     return e;
 }
 
-lb_status ensure_work(lb_ctx* c) {
+// The density staging array alone (the initialisation paths need no more).
+lb_status ensure_rho(lb_ctx* c) {
     if (c->w_rho) return LB_OK;
+    cudaError_t e = cudaMalloc(&c->w_rho, c->N * sizeof(double));
+    if (e != cudaSuccess) {
+        c->w_rho = nullptr;
+        return fail(LB_ENOMEM, std::string("density array: ") + cudaGetErrorString(e));
+    }
+    return LB_OK;
+}
+
+// All float64 field and reduction arrays (lb_fields, lb_stats_get, velocity uploads).
+lb_status ensure_work(lb_ctx* c) {
+    lb_status s = ensure_rho(c);
+    if (s != LB_OK) return s;
+    if (c->w_part) return LB_OK;
     const size_t n = c->N;
     const int nmc = c->D == 3 ? 6 : 3;
     c->stat_blocks = int(std::min<size_t>(1024, (n + lbk::STAT_THREADS - 1) / lbk::STAT_THREADS));
     if (c->stat_blocks < 1) c->stat_blocks = 1;
-    cudaError_t e;
-    if ((e = cudaMalloc(&c->w_rho, n * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&c->w_u, 3 * n * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&c->w_v, 3 * n * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&c->w_mp, nmc * n * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&c->w_part, (size_t(c->stat_blocks) + 1) * lbk::NSTAT * sizeof(double))) != cudaSuccess)
+    cudaError_t e = cudaSuccess;
+    if ((!c->w_u && (e = cudaMalloc(&c->w_u, 3 * n * sizeof(double))) != cudaSuccess) ||
+        (!c->w_v && (e = cudaMalloc(&c->w_v, 3 * n * sizeof(double))) != cudaSuccess) ||
+        (!c->w_mp && (e = cudaMalloc(&c->w_mp, nmc * n * sizeof(double))) != cudaSuccess) ||
+        (e = cudaMalloc(&c->w_part, (size_t(c->stat_blocks) + 1) * lbk::NSTAT * sizeof(double))) != cudaSuccess) {
+        c->w_part = nullptr;
         return fail(LB_ENOMEM, std::string("work arrays: ") + cudaGetErrorString(e));
+    }
     return LB_OK;
 }
 
@@ -479,7 +494,7 @@ lb_status lb_init_drops(lb_ctx* c, int ndrops, const double* centres, const doub
     if (!(width > 0)) return fail(LB_EINVAL, "width must be positive");
     for (int k = 0; k < ndrops; ++k)
         if (!(radii[k] > 0)) return fail(LB_EINVAL, "drop radii must be positive");
-    if ((s = ensure_work(c)) != LB_OK) return s;
+    if ((s = ensure_rho(c)) != LB_OK) return s;
     double* d_drops = nullptr;
     const size_t nd = size_t(ndrops) * (c->D + 1);
     cudaError_t e = cudaSuccess;
@@ -508,7 +523,7 @@ lb_status lb_init_fields(lb_ctx* c, const double* rho, const double* u) {
     lb_status s = check_ctx(c);
     if (s != LB_OK) return s;
     if (!rho) return fail(LB_EINVAL, "null density");
-    if ((s = ensure_work(c)) != LB_OK) return s;
+    if ((s = (u ? ensure_work(c) : ensure_rho(c))) != LB_OK) return s;
     cudaError_t e = cudaMemcpyAsync(c->w_rho, rho, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && u)
         e = cudaMemcpyAsync(c->w_u, u, size_t(c->D) * c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
@@ -541,6 +556,30 @@ lb_status lb_get_populations(lb_ctx* c, double* f) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f, c->w_io, size_t(c->Q) * c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return record(c, e, "get populations");
+    return sync_status(c);
+}
+
+lb_status lb_get_populations_box(lb_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* f) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!f) return fail(LB_EINVAL, "null output");
+    if (bx < 1 || by < 1 || bz < 1 || bx > c->p.nx || by > c->p.ny || bz > c->p.nz)
+        return fail(LB_EINVAL, "box sizes must be in [1, lattice size]");
+    if (x0 < 0 || y0 < 0 || z0 < 0 || x0 >= c->p.nx || y0 >= c->p.ny || z0 >= c->p.nz)
+        return fail(LB_EINVAL, "box origin must lie in the lattice");
+    const size_t n = size_t(bx) * by * bz;
+    if (n > (size_t(1) << LB_BOX_MAX_LOG2_SITES)) return fail(LB_EINVAL, "box larger than LB_BOX_MAX_LOG2_SITES");
+    if (!c->initialised) return fail(LB_ESTATE, "state not initialised");
+    double* d = nullptr;
+    const size_t bytes = size_t(c->Q) * n * sizeof(double);
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return fail(LB_ENOMEM, std::string("box staging: ") + cudaGetErrorString(e));
+    const int o[3] = {x0, y0, z0}, b[3] = {bx, by, bz};
+    e = c->ks.get_box(pop_ptrs(c, c->cur), grid3(c), o, b, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return record(c, e, "get population box");
     return sync_status(c);
 }
 

@@ -120,6 +120,7 @@ _SIGNATURES = {
     "lb_field_stats_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_longlong,
                                          C.c_void_p, C.c_void_p]),
     "lb_fma_peak": (C.c_int, [C.c_int, C.c_int, _DPTR]),
+    "lb_get_populations_box": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _DPTR]),
 }
 
 
@@ -245,6 +246,15 @@ class Context:
     def get_populations(self) -> np.ndarray:
         out = np.empty((self.q,) + self.shape, dtype=np.float64)
         _check(self._lib.lb_get_populations(self._h, _dptr(out)))
+        return out
+
+    def get_populations_box(self, origin, size) -> np.ndarray:
+        """lb_get_populations_box: float64 populations of the periodic box at
+        origin (x0, y0[, z0]) with size (bx, by[, bz]); shape (Q, bz, by, bx)."""
+        o = (tuple(origin) + (0,))[:3]
+        b = (tuple(size) + (1,))[:3]
+        out = np.empty((self.q, b[2], b[1], b[0]), dtype=np.float64)
+        _check(self._lib.lb_get_populations_box(self._h, *(int(v) for v in o), *(int(v) for v in b), _dptr(out)))
         return out
 
     def step(self, n: int = 1):
