@@ -85,3 +85,15 @@ def test_d2q9_46000_squared():
                (n - B // 2, n - B // 2),
                (n - B, n - B)]
     _check_boxes(lb, lb.D2Q9, (n, n), origins)
+
+
+@pytest.mark.parametrize("n,cuts", [(256, (64, 128, 192)), (224, (74, 149))], ids=["256c4", "224c3"])
+def test_d3q19_uniform_chunks_across_chunk_boundaries(n, cuts):
+    """Lattices with fewer than two resident slots per tile (224^3, 256^3 on 152 SMs) split
+    every column into equal z chunks; boxes straddling the chunk boundaries (and the drop
+    interface along x) check the steps there."""
+    lb = library()
+    R = 0.3 * n
+    xi = int(n / 2 + R) - B // 2
+    origins = [(xi, n // 2 - B // 2, z - B // 2) for z in cuts] + [(0, 0, cuts[0] - B // 2)]
+    _check_boxes(lb, lb.D3Q19, (n, n, n), origins)
