@@ -40,6 +40,8 @@ KERNEL_SOURCES = ["step3d.cuh", "step_kernel.cuh", "storage.cuh", "lattice.cuh"]
 NCU_TRAFFIC = {
     ("0a56c3ba8029", "f16dev", 128): 137.92e6,   # 97.35 MB read + 40.57 MB written
     ("0a56c3ba8029", "f32", 128): 306.32e6,      # 191.48 MB read + 114.84 MB written
+    ("0a56c3ba8029", "bf16dev", 128): 135.55e6,  # 97.01 MB read + 38.54 MB written
+    ("0a56c3ba8029", "f64", 128): 637.08e6,      # 357.15 MB read + 279.94 MB written
 }
 
 # Executed floating-point operations per lattice update of the step kernel,
