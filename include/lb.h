@@ -344,6 +344,19 @@ lb_status lb_ws3_decode(int nx, int ny, int nz, const double* rho_tanh, double r
 lb_status lb_field_stats_noalloc(const double* rho, const double* u, const double* v, int dim, long long n,
                                  double* out, void* cuda_stream);
 
+/* ---- D3Q19 work list (host-only inspection helper; no counterpart in the paper) ----
+ *
+ * lb_work_list returns the CTA work list that lb_create builds for the D3Q19
+ * step (a lattice split into column tiles of tile_x x tile_y sites and z chunks):
+ * 4 ints (x0, y0, z0, z1) per CTA, in launch order, for a GPU with `sms` SMs and
+ * `ctas_per_sm` resident CTAs of the step kernel per SM (2 for the 32-bit kernels
+ * on a GB300, tiles 32 x 8; float64: tiles 32 x 4).  *count receives the number
+ * of CTAs; if out is not NULL, the first min(count, capacity) entries are written
+ * to it (caller-owned, 4 * capacity ints).  Runs on the host only (no CUDA call).
+ * Non-positive sizes, more than 2^31 - 1 sites or a NULL count return LB_EINVAL. */
+lb_status lb_work_list(int sms, int ctas_per_sm, int nx, int ny, int nz, int tile_x, int tile_y, int* out,
+                       int capacity, int* count);
+
 /* ---- FMA rate (measurement helper; no counterpart in the paper) --------------
  *
  * lb_fma_peak measures the fused multiply-add rate of the current GPU, the

@@ -184,6 +184,49 @@ lb_status record(lb_ctx* c, cudaError_t e, const char* where) {
     return cuda_fail(e, where);
 }
 
+// The D3Q19 step's work list: one (x0, y0, z0, z1) per CTA, a column tile of
+// tx x ty sites and a chunk [z0, z1) of its planes, in launch order.  With at
+// least two resident slots per tile (small lattices) the list fills exactly the
+// resident slots: each tile gets slots / tiles chunks, the remainder one more (no
+// chunk under 4 planes).  Otherwise every tile gets the same number c of chunks:
+// the smallest c whose estimated efficiency (W / ceil(W)) * L / (L + 4) is within
+// 0.02 of the best, W = CTAs per SM, L = chunk length, 4 the halo planes a chunk
+// loads in addition (measured on GB300: 224^3 c = 3, 256^3 c = 4, 320^3 c = 3 are
+// 13-17% faster than one chunk per tile).  CTAs are listed longest chunk first so
+// that the first wave puts one long CTA on every SM and the second wave pairs it
+// with a short one.  CTAs resident together march at the same time, so the halo
+// rows neighbouring tiles share are read close together (from L2).
+std::vector<int4> build_work_list(long long sms, long long occ, int nx, int ny, int nz, int tx, int ty) {
+    sms = std::max(sms, 1LL);
+    occ = std::max(occ, 1LL);
+    const int gx = (nx + tx - 1) / tx, gy = (ny + ty - 1) / ty;
+    const long long slots = sms * occ;
+    const long long tiles = (long long)gx * gy;
+    const int maxc = std::max(1, nz / 4);
+    long long uniform_c = 0;
+    if (2 * tiles > slots) {
+        const long long cmax = std::max(1, nz / 16);
+        auto eff = [&](long long cc) {
+            const double W = double(cc * tiles) / double(sms), L = double(nz) / double(cc);
+            return W / std::ceil(W) * L / (L + 4.0);
+        };
+        double best = 0.0;
+        for (long long cc = 1; cc <= cmax; ++cc) best = std::max(best, eff(cc));
+        for (uniform_c = 1; uniform_c < cmax && eff(uniform_c) < best - 0.02; ++uniform_c) {
+        }
+    }
+    std::vector<int4> work;
+    for (long long t = 0; t < tiles; ++t) {
+        long long ct = uniform_c ? uniform_c : slots / tiles + (t < slots % tiles ? 1 : 0);
+        ct = std::max(1LL, std::min<long long>(ct, maxc));
+        const int x0 = int(t % gx) * tx, y0 = int(t / gx) * ty;
+        for (long long k = 0; k < ct; ++k)
+            work.push_back(make_int4(x0, y0, int(k * nz / ct), int((k + 1) * nz / ct)));
+    }
+    std::stable_sort(work.begin(), work.end(), [](const int4& u, const int4& v) { return u.w - u.z > v.w - v.z; });
+    return work;
+}
+
 constexpr int GRAPH_STEPS = 64;
 
 // Captures GRAPH_STEPS launches of launch_one, starting from buffer c->cur, into
@@ -375,40 +418,7 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     c->lz = 1;
     c->grid = dim3(gx, gy, 1);
     if (c->D == 3) {
-        // Work list of (tile, z chunk).  With at least two tiles' worth of slots per tile
-        // pair (small lattices) the list fills exactly the resident slots: each tile gets
-        // slots / tiles chunks, the remainder one more (no chunk under 4 planes).  Otherwise
-        // every tile gets the same number c of chunks: the smallest c whose estimated
-        // efficiency (W / ceil(W)) * L / (L + 4) is within 0.02 of the best, W = CTAs per SM,
-        // L = chunk length, 4 the halo planes a chunk loads in addition (measured on GB300:
-        // 224^3 c = 3, 256^3 c = 4, 320^3 c = 3 are 13-17% faster than one chunk per tile).  CTAs are listed longest
-        // chunk first so that the first wave puts one long CTA on every SM and the second
-        // wave pairs it with a short one.  CTAs resident together march at the same time, so
-        // the halo rows neighbouring tiles share are read close together (from L2).
-        const long long slots = (long long)std::max(sms, 1) * occ;
-        const long long tiles = (long long)gx * gy;
-        const int maxc = std::max(1, p->nz / 4);
-        long long uniform_c = 0;
-        if (2 * tiles > slots) {
-            const long long cmax = std::max(1, p->nz / 16);
-            auto eff = [&](long long cc) {
-                const double W = double(cc * tiles) / std::max(sms, 1), L = double(p->nz) / cc;
-                return W / std::ceil(W) * L / (L + 4.0);
-            };
-            double best = 0.0;
-            for (long long cc = 1; cc <= cmax; ++cc) best = std::max(best, eff(cc));
-            for (uniform_c = 1; uniform_c < cmax && eff(uniform_c) < best - 0.02; ++uniform_c) {
-            }
-        }
-        std::vector<int4> work;
-        for (long long t = 0; t < tiles; ++t) {
-            long long ct = uniform_c ? uniform_c : slots / tiles + (t < slots % tiles ? 1 : 0);
-            ct = std::min<long long>(ct, maxc);
-            const int x0 = int(t % gx) * c->ks.tx, y0 = int(t / gx) * c->ks.ty;
-            for (long long k = 0; k < ct; ++k)
-                work.push_back(make_int4(x0, y0, int(k * p->nz / ct), int((k + 1) * p->nz / ct)));
-        }
-        std::stable_sort(work.begin(), work.end(), [](const int4& u, const int4& v) { return u.w - u.z > v.w - v.z; });
+        const std::vector<int4> work = build_work_list(sms, occ, p->nx, p->ny, p->nz, c->ks.tx, c->ks.ty);
         c->lz = work.front().w - work.front().z;
         if (cudaMalloc(&c->d_work, work.size() * sizeof(int4)) != cudaSuccess ||
             cudaMemcpy(c->d_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -574,6 +584,25 @@ lb_status lb_get_populations(lb_ctx* c, double* f) {
         e = cudaMemcpyAsync(f, c->w_io, size_t(c->Q) * c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return record(c, e, "get populations");
     return sync_status(c);
+}
+
+lb_status lb_work_list(int sms, int ctas_per_sm, int nx, int ny, int nz, int tile_x, int tile_y, int* out,
+                       int capacity, int* count) {
+    if (!count) return fail(LB_EINVAL, "null count");
+    if (sms < 1 || ctas_per_sm < 1 || nx < 1 || ny < 1 || nz < 1 || tile_x < 1 || tile_y < 1 ||
+        (long long)nx * ny * nz > 0x7fffffffLL)
+        return fail(LB_EINVAL, "sizes must be positive (at most 2^31 - 1 sites)");
+    const std::vector<int4> w = build_work_list(sms, ctas_per_sm, nx, ny, nz, tile_x, tile_y);
+    if (w.size() > size_t(0x7fffffff)) return fail(LB_EINVAL, "work list too long");
+    *count = int(w.size());
+    if (out)
+        for (size_t k = 0; k < w.size() && k < size_t(std::max(capacity, 0)); ++k) {
+            out[4 * k] = w[k].x;
+            out[4 * k + 1] = w[k].y;
+            out[4 * k + 2] = w[k].z;
+            out[4 * k + 3] = w[k].w;
+        }
+    return LB_OK;
 }
 
 lb_status lb_get_populations_box(lb_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* f) {

@@ -120,6 +120,8 @@ _SIGNATURES = {
     "lb_field_stats_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_longlong,
                                          C.c_void_p, C.c_void_p]),
     "lb_fma_peak": (C.c_int, [C.c_int, C.c_int, _DPTR]),
+    "lb_work_list": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                               C.POINTER(C.c_int)]),
     "lb_get_populations_box": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _DPTR]),
 }
 
@@ -167,6 +169,19 @@ def field_stats_noalloc(rho_ptr: int, u_ptr: int, v_ptr: int, dim: int, n: int, 
     _check(load_library().lb_field_stats_noalloc(C.c_void_p(rho_ptr), C.c_void_p(u_ptr), C.c_void_p(v_ptr),
                                                  int(dim), int(n), C.c_void_p(out_ptr),
                                                  C.c_void_p(stream) if stream else None))
+
+
+def work_list(sms: int, ctas_per_sm: int, shape, tile=(32, 8)) -> np.ndarray:
+    """lb_work_list: the D3Q19 step's CTA work list for a lattice (nx, ny, nz) on a GPU
+    with `sms` SMs, as an int array of (x0, y0, z0, z1) rows in launch order (host only)."""
+    nx, ny, nz = (int(v) for v in shape)
+    n = C.c_int()
+    lib = load_library()
+    _check(lib.lb_work_list(sms, ctas_per_sm, nx, ny, nz, tile[0], tile[1], None, 0, C.byref(n)))
+    out = np.empty((n.value, 4), dtype=np.int32)
+    _check(lib.lb_work_list(sms, ctas_per_sm, nx, ny, nz, tile[0], tile[1], out.ctypes.data_as(C.c_void_p),
+                            n.value, C.byref(n)))
+    return out
 
 
 F64_FMA_ITERS, F32_FMA_ITERS = 4000, 200000
