@@ -221,11 +221,14 @@ def test_f32_storage_tolerance(lat, scheme, shape):
     assert max(np.abs(v_g[a] - v[a]).max() for a in range(len(v))) < 1e-6
 
 
-@pytest.mark.parametrize("storage,tol_rho,tol_v", [(F16DEV, 1e-4, 2e-5), (BF16DEV, 1e-3, 2e-4)])
+@pytest.mark.parametrize("storage,tol_rho,tol_v", [(F16DEV, 3e-5, 1e-5), (BF16DEV, 2e-4, 6e-5)])
 @pytest.mark.parametrize("lat,scheme,shape", CASES)
 def test_deviation_storage_tolerance(lat, scheme, shape, storage, tol_rho, tol_v):
     """fp16 / bf16 deviation storage (f_0 float32), 100 steps from the rounded
-    start: rho within tol_rho relative, v within tol_v absolute."""
+    start: rho within tol_rho relative, v within tol_v absolute.  Each step
+    rounds every deviation to the format (11 / 8 significant bits); measured
+    maxima over these cases on GB300: fp16 rho 1.3e-5, v 3.1e-6; bf16 rho
+    7.8e-5, v 2.5e-5; the bounds leave a factor ~2.5."""
     got, want, rho_g, rho, v_g, v = _reduced_case(lat, scheme, storage, shape, 100)
     assert rel_inf(rho_g, rho) < tol_rho
     assert max(np.abs(v_g[a] - v[a]).max() for a in range(len(v))) < tol_v
