@@ -79,7 +79,11 @@ def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, sche
          refs=None, band=0.05, tol_rho=1e-3, hold=10, autotune_steps=5, stream=None):
     """All instances in one batch with the given storage, tanh start or the
     network's prediction (ws); reference test when refs is given.  Same
-    return layout as ``plain`` plus the time of the warm-start prediction."""
+    return layout as ``plain`` plus the time of the warm-start prediction.
+    With a warm start the tanh start stays the fallback: instances that went
+    unstable or missed the test from the predicted start run again from the
+    tanh start in a second batch; their steps and wall time add to the first
+    (``fallback`` = how many)."""
     t0 = time.perf_counter()
     with lb.Batch(instances, W.A_VDW, W.B_VDW, scheme=scheme, storage=storage, stream=stream) as bt:
         if refs is not None:
@@ -98,9 +102,27 @@ def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, sche
         seconds = time.perf_counter() - t0
         _, um, hi, lo = bt.last_check()
         final = [bt.fields(k) for k in range(len(instances))]
-    return {"seconds": seconds, "steps": list(s), "status": list(st), "umax": [float(v) for v in um],
+    s, st, um, hi, lo = list(s), list(st), list(um), list(hi), list(lo)
+    failed = [k for k, v in enumerate(st) if v != 0] if ws is not None else []
+    if failed:
+        t1 = time.perf_counter()
+        sub_refs = [refs[k] for k in failed] if refs is not None else None
+        with lb.Batch([instances[k] for k in failed], W.A_VDW, W.B_VDW, scheme=scheme, storage=storage,
+                      stream=stream) as bt:
+            if sub_refs is not None:
+                _set_refs(bt, sub_refs, band, tol_rho, hold)
+            bt.init_drops(2.0)
+            s2, st2, total2 = bt.run_to_steady(tol=tol, every=every, max_steps=max_steps)
+            seconds += time.perf_counter() - t1
+            _, um2, hi2, lo2 = bt.last_check()
+            for j, k in enumerate(failed):
+                s[k] = (max_steps if s[k] < 0 else s[k]) + s2[j] if s2[j] >= 0 else s2[j]
+                st[k], um[k], hi[k], lo[k] = st2[j], um2[j], hi2[j], lo2[j]
+                final[k] = bt.fields(j)
+        total += total2
+    return {"seconds": seconds, "steps": s, "status": st, "umax": [float(v) for v in um],
             "rho_max": [float(v) for v in hi], "rho_min": [float(v) for v in lo], "final": final,
-            "predict_seconds": t_pred, "batch_steps": total}
+            "predict_seconds": t_pred, "batch_steps": total, "fallback": len(failed)}
 
 
 def _centre(rho):

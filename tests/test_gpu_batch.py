@@ -170,3 +170,28 @@ def test_whole_sweep_driver_small():
     assert f64["lattice_updates"] > 0 and f64["mlups"] > 0
     if f16["converged"]:
         assert f16["max_u_rel_err_max"] < 0.1
+
+
+class _NaNNetwork:
+    """Stands in for a warm-start network whose prediction is unusable."""
+
+    def predict_sym(self, x):
+        return np.full((3,) + x.shape[1:], np.nan, dtype=np.float32)
+
+
+def test_warm_start_falls_back_to_tanh_start():
+    """An unusable predicted start makes its instances unstable; steady.fast
+    reruns them from the tanh start and they reach the steady-state test."""
+    library()
+    from paper_0710_5470_gb300 import lb, steady
+    inst = [dict(nx=48, ny=48, T=0.55, kappa=0.01, tau=1.0, radius=12.0),
+            dict(nx=40, ny=56, T=0.54, kappa=0.012, tau=0.9, radius=10.0)]
+    res = steady.fast(inst, storage=lb.F64, tol=1e-8, every=50, max_steps=40000, ws=_NaNNetwork(),
+                      autotune_steps=0)
+    assert res["fallback"] == 2
+    assert res["status"] == [0, 0]
+    ref = steady.fast(inst, storage=lb.F64, tol=1e-8, every=50, max_steps=40000, autotune_steps=0)
+    assert ref["status"] == [0, 0] and ref["fallback"] == 0
+    for k in range(2):
+        assert res["steps"][k] >= ref["steps"][k]
+        assert np.abs(res["final"][k][0] - ref["final"][k][0]).max() < 1e-6
