@@ -62,7 +62,6 @@ parity unpinned: the paper prints no step-level numbers.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 import numpy as np
