@@ -106,6 +106,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-steady", action="store_true")
+    p.add_argument("--scheme", default="forcing", choices=["forcing", "equilibrium"],
+                   help="collision scheme (the headline workload is the forcing scheme)")
     return p.parse_args()
 
 
@@ -197,11 +199,11 @@ def whole_job(dist, world: int, sites_per_rank: int, steps: int, ms_local: float
     return ms, sites_per_rank * steps * world / (ms / 1e3) / 1e6
 
 
-def oracle_sample(n_edge: int, steps: int):
+def oracle_sample(n_edge: int, steps: int, scheme: str = "forcing"):
     """FP64 oracle on an n_edge^3 periodic box holding the same drop scaled to
     the box (R = 30/128 of the edge): returns (MLUPS, seconds, sites*steps)."""
     from oracle import lb_oracle as O
-    m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme="forcing")
+    m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme=scheme)
     rl, rg = O.coexistence(A_VDW, B_VDW, WORKLOAD["T"])
     R = WORKLOAD["R"] * n_edge / WORKLOAD["n"]
     rho0 = O.drop_density((n_edge,) * 3, [(n_edge / 2,) * 3], [R], rl, rg, WORKLOAD["width"])
@@ -225,7 +227,7 @@ def run_reference(args):
     rate = 0.25e6                                     # oracle LU/s, measured order of magnitude
     edge = int(max(8, min(args.edge, round((budget * rate) ** (1 / 3)))))
     from oracle import lb_oracle as O
-    m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme="forcing")
+    m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme=args.scheme)
     rl, rg = O.coexistence(A_VDW, B_VDW, WORKLOAD["T"])
     R = WORKLOAD["R"] * edge / WORKLOAD["n"]
     f = O.init_equilibrium(O.drop_density((edge,) * 3, [(edge / 2,) * 3], [R], rl, rg, WORKLOAD["width"]), m)
@@ -237,11 +239,11 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     mlups = edge ** 3 * args.steps / dt / 1e6
     sample = f"{args.steps} oracle steps on a {edge}^3 box (drop scaled to the box), FP64 numpy"
-    line = {"impl": "reference", "metric": "MLUPS (D3Q19 128^3 free-energy LB step, forcing scheme)",
+    line = {"impl": "reference", "metric": f"MLUPS (D3Q19 128^3 free-energy LB step, {args.scheme} scheme)",
             "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"D3Q19 {WORKLOAD['n']}^3 drop R=30, forcing, T=0.55, kappa=0.01, tau=1",
+            "config": {"workload": f"D3Q19 {WORKLOAD['n']}^3 drop R=30, {args.scheme} scheme, T=0.55, kappa=0.01, tau=1",
                        "sample_edge": edge},
             "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -265,9 +267,10 @@ def time_steps(ctx, stream, steps, dist=None):
     return ev0.elapsed_time(ev1)
 
 
-def make_ctx(lb, storage: str, n: int, stream):
+def make_ctx(lb, storage: str, n: int, stream, scheme: str = "forcing"):
     ctx = lb.Context(lb.D3Q19, (n, n, n), A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"],
-                     scheme=lb.FORCING, storage=lb.STORAGE_NAMES[storage], stream=stream.cuda_stream)
+                     scheme=lb.FORCING if scheme == "forcing" else lb.EQUILIBRIUM,
+                     storage=lb.STORAGE_NAMES[storage], stream=stream.cuda_stream)
     R = WORKLOAD["R"] * n / WORKLOAD["n"]
     ctx.init_drops([(n / 2,) * 3], [R], WORKLOAD["width"])
     return ctx, R
@@ -293,7 +296,7 @@ def run_native(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     fp = kernel_fingerprint()
 
-    ctx, R = make_ctx(lb, args.storage, n, stream)
+    ctx, R = make_ctx(lb, args.storage, n, stream, args.scheme)
     ctx.step(args.warmup)
     ctx.synchronize()
     clocks = ClockSampler(local)
@@ -310,10 +313,12 @@ def run_native(args):
     bpl = bytes_per_lu(args.storage)
     t_launch = ms_local / args.steps / 1e3
     achieved = bpl * sites / t_launch / 1e9
-    traffic = NCU_TRAFFIC.get((fp, args.storage, n))
+    # the ncu tables hold the forcing-scheme kernel
+    forcing = args.scheme == "forcing"
+    traffic = NCU_TRAFFIC.get((fp, args.storage, n)) if forcing else None
     # FMA rates of this GPU (float64 and float32), best of three short launches
     fma = {"f64": max(lb.fma_peak(0) for _ in range(3)), "f32": max(lb.fma_peak(1) for _ in range(3))}
-    alu = alu_roofline(fp, args.storage, n, sites / t_launch / 1e9, fma)
+    alu = alu_roofline(fp, args.storage, n, sites / t_launch / 1e9, fma) if forcing else None
 
     # end to end through the C ABI with host buffers (pinned): upload the initial
     # density, run the steps, download rho and u
@@ -343,7 +348,7 @@ def run_native(args):
         for sname in BYTES_POP:
             if sname == args.storage:
                 continue
-            vctx, _ = make_ctx(lb, sname, n, stream)
+            vctx, _ = make_ctx(lb, sname, n, stream, args.scheme)
             vsteps = max(1, args.steps // (20 if sname == "f64" else 1))
             vctx.step(min(args.warmup, 5) if sname == "f64" else args.warmup)
             vctx.synchronize()
@@ -356,8 +361,9 @@ def run_native(args):
                                "ms_per_step": vms / vsteps,
                                "roofline": {"bound": "hbm", "achieved": vach, "peak": peak, "unit": "GB/s",
                                             "frac": vach / peak, "bytes_per_lu": vb,
-                                            "traffic": NCU_TRAFFIC.get((fp, sname, n))},
-                               "alu_roofline": alu_roofline(fp, sname, n, sites / (vms / vsteps / 1e3) / 1e9, fma),
+                                            "traffic": NCU_TRAFFIC.get((fp, sname, n)) if forcing else None},
+                               "alu_roofline": alu_roofline(fp, sname, n, sites / (vms / vsteps / 1e3) / 1e9,
+                                                            fma) if forcing else None,
                                "max_v": vst["max_v"]}
 
     # time to steady state (second half of the metric): plain float64, one
@@ -387,17 +393,17 @@ def run_native(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         edge = n
-        v, dt, lu = oracle_sample(edge, 5)
+        v, dt, lu = oracle_sample(edge, 5, args.scheme)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": f"5 FP64 oracle steps (numpy, one thread) on the full {edge}^3 drop workload ({dt:.1f} s)"}
 
     if rank == 0:
         line = {
-            "metric": "MLUPS (D3Q19 128^3 free-energy LB step, forcing scheme)",
+            "metric": f"MLUPS (D3Q19 {n}^3 free-energy LB step, {args.scheme} scheme)",
             "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage != "f64" else "f64", "data": "synthetic",
-            "config": {"workload": f"D3Q19 {n}^3 periodic, one drop R={R:g}, forcing scheme, T=0.55, "
+            "config": {"workload": f"D3Q19 {n}^3 periodic, one drop R={R:g}, {args.scheme} scheme, T=0.55, "
                                    f"kappa=0.01, tau=1.0", "storage": args.storage,
                        "l2": "inputs larger than L2: the two population buffers exceed the 126 MB L2",
                        "parallelism": f"{world} independent replica(s)"},
