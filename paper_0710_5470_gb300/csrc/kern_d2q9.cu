@@ -7,9 +7,9 @@ template <bool F>
 static LbKernelSet pick(int storage) {
     switch (storage) {
         case 0: return Launchers<D2Q9, F, StF64, 32, 8>::make();
-        case 1: return Launchers<D2Q9, F, StF32, 32, 16>::make();
-        case 2: return Launchers<D2Q9, F, StF16, 32, 16>::make();
-        case 3: return Launchers<D2Q9, F, StBF16, 32, 16>::make();
+        case 1: return Launchers<D2Q9, F, StF32, 32, 8>::make();
+        case 2: return Launchers<D2Q9, F, StF16, 32, 8>::make();
+        case 3: return Launchers<D2Q9, F, StBF16, 32, 8>::make();
     }
     return LbKernelSet{};
 }
