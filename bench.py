@@ -7,10 +7,12 @@ kappa = 0.01, tau = 1.0 (synthetic drop, tanh profile of width 2).
 A step is one time step of the whole lattice (one fused kernel launch).
 
 Prints one JSON line: MLUPS (million lattice updates per second, whole job),
-the HBM roofline of the step kernel, an end-to-end number through the C ABI
-with host buffers, and the FP64 CPU oracle timed on a bounded sample.
+the HBM and ALU rooflines of the step kernel, an end-to-end number through
+the C ABI with host buffers, the FP64 CPU oracle timed on a bounded sample,
+and the time to steady state of a batched drop sweep against plain float64.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f16dev|bf16dev|f32|f64]
+                  [--edge E] [--scheme forcing|equilibrium]
   python bench.py --impl reference ...     (the oracle, timed on the host cores)
 Multi-GPU (N > 1, torchrun): independent replicas, one per GPU (weak scaling).
 """
