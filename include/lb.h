@@ -121,7 +121,10 @@ lb_status lb_get_coexistence(const lb_ctx* ctx, double* rho_l, double* rho_g);
  * centre k; then f = f^eq(rho0, u = 0) of the context's scheme (Eqs. 5, 6),
  * gradients taken with the stencils.  centres: ndrops*dim doubles (x, y[, z]);
  * radii: ndrops doubles > 0.  ndrops = 0 gives uniform gas.  Resets the step
- * counter. */
+ * counter.  The first initialisation allocates one float64 per site (the
+ * density); lb_fields / lb_stats_get and velocity uploads later allocate the
+ * other float64 field arrays (13 doubles per site in all, kept until
+ * lb_destroy). */
 lb_status lb_init_drops(lb_ctx* ctx, int ndrops, const double* centres, const double* radii,
                         double width);
 
