@@ -229,9 +229,12 @@ def experiment(count=16, seed=0, every=100, max_steps=200000, band=0.05, tol_rho
 
 def _sweep_summary(res, sites):
     """Wall time, lattice updates done (sum over instances of the steps it ran
-    x its sites) and their rate, and the retirement counts of a batched run."""
+    x its sites; the whole batch for an instance stopped by the cap) and their
+    rate, and the retirement counts of a batched run."""
     st = res["status"]
-    lu = sum(int(n) * int(k) for n, k in zip(res["steps"], sites))
+    # an instance still running at the cap reports -1 steps: it ran the whole batch
+    ran = [int(n) if n >= 0 else int(res["batch_steps"]) for n in res["steps"]]
+    lu = sum(n * int(k) for n, k in zip(ran, sites))
     ok = [k for k, s in enumerate(st) if s == 0]
     return {"seconds": res["seconds"], "instances": len(st), "converged": len(ok),
             "unstable": sum(s == 4 for s in st), "not_converged": sum(s == 5 for s in st),
