@@ -140,6 +140,12 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out: str) -> dict:
+        """Median SM clock, maximum SM clock and the throttle reasons seen in
+        nvidia-smi CSV lines of FIELDS (noheader, nounits)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.splitlines():
