@@ -510,7 +510,7 @@ lb_status lb_ws_features(int nx, int ny, const double* rho_tanh, double rho_l, d
 
 lb_status lb_ws_decode(int nx, int ny, const double* rho_tanh, double rho_l, double rho_g, const float* y, double* rho,
                        double* u) {
-    if (!rho_tanh || !y || nx < 1 || ny < 1) return fail(LB_EINVAL, "bad arguments");
+    if (!rho_tanh || !y || nx < 1 || ny < 1 || !(rho_l > rho_g)) return fail(LB_EINVAL, "bad arguments");
     const size_t N = size_t(nx) * ny;
     const double span = rho_l - rho_g, mid = 0.5 * (rho_l + rho_g);
     // The prediction must describe the same drop: its mass is the tanh start's.
