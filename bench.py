@@ -34,7 +34,7 @@ WORKLOAD = dict(lattice="D3Q19", n=128, R=30.0, scheme="forcing", T=0.55, kappa=
 BYTES_POP = {"f64": (8, 8), "f32": (4, 4), "f16dev": (4, 2), "bf16dev": (4, 2)}   # (f_0, f_i) bytes
 
 
-KERNEL_SOURCES = ["step3d.cuh", "step_kernel.cuh", "storage.cuh", "lattice.cuh"]
+KERNEL_SOURCES = ["step3d.cuh", "step3d_pk.cuh", "kern_d3q19_pk.cu", "step_kernel.cuh", "storage.cuh", "lattice.cuh"]
 # DRAM bytes (read + write) per launch of the D3Q19 forcing step kernel at
 # 128^3, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
 # fingerprint of the kernel sources they were measured on and the storage.
@@ -90,8 +90,19 @@ def kernel_fingerprint() -> str:
 
 
 def bytes_per_lu(storage: str, q: int = 19) -> int:
-    """Algorithmic HBM bytes per lattice update: one read and one write of
-    every stored population (rho is recomputed on chip, never stored)."""
+    """Algorithmic HBM bytes per lattice update of the survey's roofline: one
+    read and one write of every stored population plus one read and one write
+    of the density, B = 2 Q s_f + 2 s_rho (s_rho = 4, or 8 for float64):
+    88 B for 16-bit deviations (f_0 float32), 160 B float32, 320 B float64."""
+    b0, bi = BYTES_POP[storage]
+    s_rho = 8 if storage == "f64" else 4
+    return 2 * (b0 + (q - 1) * bi) + 2 * s_rho
+
+
+def bytes_moved_per_lu(storage: str, q: int = 19) -> int:
+    """Bytes per lattice update this design moves: the populations once in and
+    once out (the density is recomputed on chip and never stored): 80 B for
+    16-bit deviations, 152 B float32, 304 B float64."""
     b0, bi = BYTES_POP[storage]
     return 2 * (b0 + (q - 1) * bi)
 
@@ -305,6 +316,7 @@ def run_native(args):
     fp = kernel_fingerprint()
 
     ctx, R = make_ctx(lb, args.storage, n, stream, args.scheme)
+    kinfo = ctx.kernel_info()
     ctx.step(args.warmup)
     ctx.synchronize()
     clocks = ClockSampler(local)
@@ -417,9 +429,12 @@ def run_native(args):
                        "parallelism": f"{world} independent replica(s)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "bytes_per_lu": bpl,
+                         "bytes_moved_per_lu": bytes_moved_per_lu(args.storage),
+                         "frac_of_moved": achieved * bytes_moved_per_lu(args.storage) / bpl / peak,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                          "kernel_fingerprint": fp},
             "alu_roofline": alu,
+            "kernel": kinfo,
             "fma_peak_tflops": fma,
             "cpu_baseline": cpu,
             "e2e": e2e,

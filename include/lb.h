@@ -192,6 +192,14 @@ lb_status lb_shape(const lb_ctx* ctx, long long* n_sites, int* q);
  * callers that stage inputs in device memory themselves. */
 lb_status lb_device_state(lb_ctx* ctx, void** dptr, size_t* bytes);
 
+/* Launch form of the context's fused step kernel (Eq. 4 per site, one launch
+ * per time step): a short description written into name (at most cap bytes,
+ * NUL-terminated; name may be NULL), the CTA's column tile (tile_x x tile_y
+ * sites), threads per CTA, dynamic shared memory per CTA, and the number of
+ * CTAs per launch.  Any output pointer may be NULL. */
+lb_status lb_kernel_info(const lb_ctx* ctx, char* name, size_t cap, int* tile_x, int* tile_y, int* threads,
+                         size_t* smem, int* ctas);
+
 /* ------------------------------------------------------------------------
  * Batched sweeps of independent D2Q9 drop runs (parameter sweeps of the
  * Sec. IV test problem).  Every instance has its own lattice size, T, kappa

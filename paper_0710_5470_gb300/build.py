@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblb.so")
-SOURCES = ["kern_d2q9.cu", "kern_d3q19.cu", "kern_batch.cu", "lb_api.cu", "cnn.cu", "cnn3d.cu", "noalloc.cu",
+SOURCES = ["kern_d2q9.cu", "kern_d3q19.cu", "kern_d3q19_pk.cu", "kern_batch.cu", "lb_api.cu", "cnn.cu", "cnn3d.cu", "noalloc.cu",
            "param2d.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -7,13 +7,18 @@
 
 struct LbKernelSet {
     int tx = 0, ty = 0;           // CTA tile of the fused step
+    int threads = 0;              // threads per CTA of the fused step
     size_t smem = 0;              // dynamic shared memory of the fused step
+    const char* name = "";        // kernel form (reported by lb_kernel_info)
     const void* step_fn = nullptr;
     cudaError_t (*step)(const lbk::StepArgs&, dim3 grid, cudaStream_t) = nullptr;
     // the same step with one site per load (any nx); `step` moves two sites
     // per load in its halo stage and needs an even nx when this flag is set
     const void* step1_fn = nullptr;
     cudaError_t (*step1)(const lbk::StepArgs&, dim3 grid, cudaStream_t) = nullptr;
+    int tx1 = 0, ty1 = 0, threads1 = 0;   // tile, threads and shared memory of step1
+    size_t smem1 = 0;
+    const char* name1 = "";
     bool step_pair_needs_even_nx = false;
     cudaError_t (*init_feq)(const double* rho, const double* u, const lbk::PopPtrs&, lbk::Grid3, lbk::Phys,
                             cudaStream_t) = nullptr;

@@ -14,6 +14,10 @@ static LbKernelSet pick(int storage) {
     return LbKernelSet{};
 }
 
+LbKernelSet lbk_pk_forcing(int storage, LbKernelSet base);   // kern_d3q19_pk.cu
+
 LbKernelSet lbk_kernels_d3q19(int scheme, int storage) {
-    return scheme == 1 ? pick<true>(storage) : pick<false>(storage);
+    if (scheme != 1) return pick<false>(storage);
+    LbKernelSet k = pick<true>(storage);
+    return storage == 0 ? k : lbk_pk_forcing(storage, k);
 }

@@ -1,0 +1,65 @@
+// Instantiations of the two-sites-per-thread D3Q19 forcing step (step3d_pk.cuh).
+#include <cstdlib>
+
+#include "dispatch.h"
+#include "step3d_pk.cuh"
+
+using namespace lbk;
+
+namespace {
+
+template <class S, int TX, int TY, int MINB, int PF, bool MIXED>
+struct PKLaunch {
+    using Lay = LayoutPK<TX, TY, PairIO<S>::RAW16>;
+    static const void* fn() { return reinterpret_cast<const void*>(step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED>); }
+    static cudaError_t step(const StepArgs& a, dim3 grid, cudaStream_t st) {
+        static int attr_done = 0;
+        if (!attr_done) {
+            cudaError_t e = cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(Lay::BYTES));
+            if (e != cudaSuccess) return e;
+            attr_done = 1;
+        }
+        step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED><<<grid, Lay::NTH, Lay::BYTES, st>>>(a);
+        return cudaGetLastError();
+    }
+    static void apply(LbKernelSet& k, const char* name) {
+        k.tx = TX;
+        k.ty = TY;
+        k.threads = Lay::NTH;
+        k.smem = Lay::BYTES;
+        k.step_fn = fn();
+        k.step = &step;
+        k.step_pair_needs_even_nx = true;
+        k.name = name;
+    }
+};
+
+}  // namespace
+
+// The pair kernel for the forcing scheme with 16-bit deviation storage
+// (storage 2, 3) in place of `step` of `base` (an even nx is required;
+// base.step1, one site per thread, stays the fallback).  float32 storage keeps
+// the one-site-per-thread tile kernel (measured faster for it on GB300: the
+// float32 stash of a pair does not fit three CTAs per SM).  LB_D3_VARIANT
+// selects another tile / prefetch form of the pair kernel for measurements;
+// LB_D3_VARIANT=0 keeps the tile kernel.
+LbKernelSet lbk_pk_forcing(int storage, LbKernelSet k) {
+    const char* env = std::getenv("LB_D3_VARIANT");
+    const int v = env ? std::atoi(env) : -1;
+    if (v == 0) return k;
+    if (storage == 2) {
+        switch (v) {
+            case 1: PKLaunch<StF16, 64, 8, 2, 0, true>::apply(k, "pairs 64x8, mixed adds"); break;
+            case 2: PKLaunch<StF16, 64, 8, 2, 2, true>::apply(k, "pairs 64x8, prefetch all, mixed adds"); break;
+            case 4: PKLaunch<StF16, 64, 8, 1, 2, true>::apply(k, "pairs 64x8, one CTA per SM, prefetch all"); break;
+            case 8: PKLaunch<StF16, 32, 8, 3, 2, true>::apply(k, "pairs 32x8, 3 CTAs per SM, prefetch all"); break;
+            case 10: PKLaunch<StF16, 64, 12, 1, 2, true>::apply(k, "pairs 64x12, prefetch all"); break;
+            default: PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched"); break;
+        }
+    } else if (storage == 3) {
+        PKLaunch<StBF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
+    } else if (storage == 1 && v > 0) {
+        PKLaunch<StF32, 32, 8, 2, 0, false>::apply(k, "pairs 32x8");
+    }
+    return k;
+}

@@ -92,9 +92,13 @@ struct Launchers {
     }
     static LbKernelSet make() {
         LbKernelSet k;
-        k.tx = TX;
-        k.ty = TY;
+        k.tx = k.tx1 = TX;
+        k.ty = k.ty1 = TY;
+        k.threads = k.threads1 = TX * TY;
         k.smem = K::bytes();
+        k.smem1 = K1::bytes();
+        k.name = PAIRED ? "tile, two sites per halo load" : "tile, one site per thread";
+        k.name1 = "tile, one site per thread";
         k.step_fn = K::fn();
         k.step = &step;
         k.step1_fn = K1::fn();

@@ -395,6 +395,11 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     if (c->ks.step_pair_needs_even_nx && (p->nx % 2 != 0 || std::getenv("LB_NO_PAIR"))) {
         c->ks.step = c->ks.step1;
         c->ks.step_fn = c->ks.step1_fn;
+        c->ks.tx = c->ks.tx1;
+        c->ks.ty = c->ks.ty1;
+        c->ks.threads = c->ks.threads1;
+        c->ks.smem = c->ks.smem1;
+        c->ks.name = c->ks.name1;
     }
 
     cudaError_t e = cudaMalloc(&c->fbuf, 2 * c->buf_bytes);
@@ -409,7 +414,7 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(c->ks.step_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c->ks.smem));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->ks.step_fn, c->ks.tx * c->ks.ty, c->ks.smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->ks.step_fn, c->ks.threads, c->ks.smem) !=
             cudaSuccess || occ < 1)
         occ = 1;
     cudaGetLastError();
@@ -488,6 +493,21 @@ lb_status lb_shape(const lb_ctx* c, long long* n_sites, int* q) {
     if (!c) return fail(LB_EINVAL, "null context");
     if (n_sites) *n_sites = (long long)c->N;
     if (q) *q = c->Q;
+    return LB_OK;
+}
+
+lb_status lb_kernel_info(const lb_ctx* c, char* name, size_t cap, int* tile_x, int* tile_y, int* threads,
+                         size_t* smem, int* ctas) {
+    if (!c) return fail(LB_EINVAL, "null context");
+    if (name && cap > 0) {
+        std::snprintf(name, cap, "%s", c->free_params ? "run-time free parameters (three float64 kernels)"
+                                                       : c->ks.name);
+    }
+    if (tile_x) *tile_x = c->ks.tx;
+    if (tile_y) *tile_y = c->ks.ty;
+    if (threads) *threads = c->ks.threads;
+    if (smem) *smem = c->ks.smem;
+    if (ctas) *ctas = int(c->grid.x * c->grid.y * c->grid.z);
     return LB_OK;
 }
 

@@ -74,6 +74,8 @@ _SIGNATURES = {
     "lb_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "lb_set_free_params": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lb_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    "lb_kernel_info": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "lb_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(lb_instance),
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "lb_batch_destroy": (C.c_int, [C.c_void_p]),
@@ -309,6 +311,16 @@ class Context:
         _check(self._lib.lb_stats_get(self._h, C.byref(s)))
         return {"mass": s.mass, "momentum": list(s.momentum)[: self.dim], "max_u": s.max_u, "max_v": s.max_v,
                 "min_rho": s.min_rho, "max_rho": s.max_rho, "step": s.step, "status": s.status}
+
+    def kernel_info(self) -> dict:
+        """lb_kernel_info: launch form of the fused step kernel."""
+        buf = C.create_string_buffer(128)
+        tx, ty, th, ctas = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        sm = C.c_size_t()
+        _check(self._lib.lb_kernel_info(self._h, buf, 128, C.byref(tx), C.byref(ty), C.byref(th), C.byref(sm),
+                                        C.byref(ctas)))
+        return {"form": buf.value.decode(), "tile": [tx.value, ty.value], "threads": th.value,
+                "smem_bytes": sm.value, "ctas": ctas.value}
 
     def device_state(self):
         p, nb = C.c_void_p(), C.c_size_t()

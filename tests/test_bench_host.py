@@ -26,8 +26,12 @@ def test_clock_parser():
 
 
 def test_bytes_per_lattice_update():
-    assert [bench.bytes_per_lu(s) for s in ("f16dev", "bf16dev", "f32", "f64")] == [80, 80, 152, 304]
-    assert bench.bytes_per_lu("f16dev", q=9) == 40 and bench.bytes_per_lu("f64", q=9) == 144
+    """The roofline's algorithmic bytes B = 2 Q s_f + 2 s_rho (populations and
+    the density read and written once), and the bytes the fused step moves
+    (populations only; the density never leaves the chip)."""
+    assert [bench.bytes_per_lu(s) for s in ("f16dev", "bf16dev", "f32", "f64")] == [88, 88, 160, 320]
+    assert [bench.bytes_moved_per_lu(s) for s in ("f16dev", "bf16dev", "f32", "f64")] == [80, 80, 152, 304]
+    assert bench.bytes_moved_per_lu("f16dev", q=9) == 40 and bench.bytes_moved_per_lu("f64", q=9) == 144
 
 
 def test_alu_roofline_arithmetic():

@@ -238,10 +238,13 @@ def test_deviation_storage_tolerance(lat, scheme, shape, storage, tol_rho, tol_v
 @pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
 @pytest.mark.parametrize("shape", [(66, 20, 9), (2, 5, 3)])
 def test_paired_halo_loads_are_bit_identical(storage, scheme, shape, monkeypatch):
-    """With an even nx the halo stage loads two adjacent sites per access; it
-    must give exactly the one-site form's result (same arithmetic, same
-    order), over ragged tiles and a lattice narrower than one pair of halo
-    columns."""
+    """With an even nx the tile kernel's halo stage loads two adjacent sites
+    per access; it must give exactly the one-site form's result (same
+    arithmetic, same order), over ragged tiles and a lattice narrower than one
+    pair of halo columns.  (LB_D3_VARIANT=0 selects the tile kernel for the
+    forcing scheme, whose default with 16-bit storage is the pair kernel,
+    checked against the oracle in test_pair_kernel_parity.)"""
+    monkeypatch.setenv("LB_D3_VARIANT", "0")
     lb = library()
     m = oracle_model("D3Q19", scheme)
     f0 = drop_populations(m, shape, 0.3 * min(shape), perturb=1e-3, seed=9)
@@ -280,3 +283,36 @@ def test_paired_halo_loads_are_bit_identical_2d(storage, scheme, shape, monkeypa
             outs.append(ctx.get_populations())
     assert np.isfinite(outs[0]).all()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("storage,tol_f,tol_rho", [(F16DEV, 1e-5, 1e-5), (BF16DEV, 8e-5, 6e-5), (F32, 2e-6, 2e-6)])
+@pytest.mark.parametrize("variant", ["default", "1", "2", "4", "8", "10"])
+@pytest.mark.parametrize("shape", [(68, 20, 12), (2, 3, 3), (130, 10, 40), (64, 16, 9)])
+def test_pair_kernel_parity(shape, variant, storage, tol_f, tol_rho, monkeypatch):
+    """The D3Q19 forcing-scheme pair kernel (two x sites per thread, packed
+    float32 pairs) in every tile / prefetch form, one and five steps from the
+    same rounded state as the oracle: every population within tol_f of
+    max|f| and rho within tol_rho relative (one rounding of the collided
+    deviations to the format per step; ragged tiles in x and y, a lattice
+    narrower than one pair of halo columns, several z chunks)."""
+    if variant == "default":
+        monkeypatch.delenv("LB_D3_VARIANT", raising=False)
+    else:
+        monkeypatch.setenv("LB_D3_VARIANT", variant)
+    lb = library()
+    m = oracle_model("D3Q19", "forcing")
+    f0 = drop_populations(m, shape, 0.3 * min(shape), perturb=1e-3, seed=5)
+    for steps in (1, 5):
+        with make_ctx(lb, "D3Q19", "forcing", shape, storage=storage) as ctx:
+            ctx.set_populations(f0)
+            start = ctx.get_populations()
+            ctx.step(steps)
+            got = ctx.get_populations()
+            rho_g, _, _ = ctx.fields(want_v=False)
+            form = ctx.kernel_info()["form"]
+        if storage != F32 or variant != "default":
+            assert form.startswith("pairs"), form
+        want = O.run(start, m, steps)
+        rho = want.sum(axis=0)
+        assert rel_inf(got, want) < tol_f * steps, (steps, rel_inf(got, want))
+        assert rel_inf(rho_g, rho) < tol_rho * steps
