@@ -7,10 +7,29 @@
 
 namespace lbk {
 
+// Population arrays of one buffer.  aos = 0: population i is one array,
+// element q at p[i] + q * size.  aos = 1 (16-bit deviations, nx a multiple of
+// 32): populations 1..18 are interleaved in blocks of 32 sites (the 18 rows
+// of 32 values of a block contiguous, 1152 bytes), p[i] points at population
+// i's row of block 0, and element q is at half index aos_index(q) from it;
+// population 0 stays one float32 array.
 struct PopPtrs {
     char* p[MAXQ];
     float fref[MAXQ];
+    int aos = 0;
 };
+
+constexpr int AOS_SITES = 32;                        // sites per block
+constexpr int AOS_BLOCK_HALVES = 18 * AOS_SITES;     // 16-bit values per block
+
+__host__ __device__ __forceinline__ size_t aos_index(size_t q) {
+    return (q / AOS_SITES) * AOS_BLOCK_HALVES + (q % AOS_SITES);
+}
+
+// element index of population i at site q in its array pointer's units
+__host__ __device__ __forceinline__ size_t pop_index(const PopPtrs& pp, int i, size_t q) {
+    return (pp.aos && i > 0) ? aos_index(q) : q;
+}
 
 struct Grid3 {
     int nx, ny, nz;
@@ -97,7 +116,7 @@ __global__ void init_feq_kernel(const double* rho, const double* u, PopPtrs dst,
         equilibrium<L, FORCING, double>(r, j, uu, G, lap, ph.a, ph.b, ph.T, ph.kappa, ph.nu, feq);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
-            S::store(i, dst.p[i], idx, typename S::real(feq[i]), dst.fref[i]);
+            S::store(i, dst.p[i], pop_index(dst, i, idx), typename S::real(feq[i]), dst.fref[i]);
     }
 }
 
@@ -110,7 +129,7 @@ __global__ void moments_kernel(PopPtrs src, Grid3 g, double* rho, double* u) {
         double r = 0.0;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            f[i] = double(S::load(i, src.p[i], idx, src.fref[i]));
+            f[i] = double(S::load(i, src.p[i], pop_index(src, i, idx), src.fref[i]));
             r += f[i];
         }
         double j[3];
@@ -171,7 +190,7 @@ template <class L, class S>
 __global__ void get_pops_kernel(PopPtrs src, size_t n, double* out) {
     for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) out[i * n + idx] = double(S::load(i, src.p[i], idx, src.fref[i]));
+        for (int i = 0; i < L::Q; ++i) out[i * n + idx] = double(S::load(i, src.p[i], pop_index(src, i, idx), src.fref[i]));
     }
 }
 
@@ -189,7 +208,7 @@ __global__ void get_box_kernel(PopPtrs src, Grid3 g, int x0, int y0, int z0, int
         if (zz >= g.nz) zz -= g.nz;
         const size_t idx = (size_t(zz) * g.ny + size_t(yy)) * g.nx + size_t(xx);
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) out[i * n + k] = double(S::load(i, src.p[i], idx, src.fref[i]));
+        for (int i = 0; i < L::Q; ++i) out[i * n + k] = double(S::load(i, src.p[i], pop_index(src, i, idx), src.fref[i]));
     }
 }
 
@@ -198,7 +217,7 @@ __global__ void set_pops_kernel(PopPtrs dst, size_t n, const double* in) {
     for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
-            S::store(i, dst.p[i], idx, typename S::real(in[i * n + idx]), dst.fref[i]);
+            S::store(i, dst.p[i], pop_index(dst, i, idx), typename S::real(in[i * n + idx]), dst.fref[i]);
     }
 }
 

@@ -10,6 +10,7 @@ struct LbKernelSet {
     int threads = 0;              // threads per CTA of the fused step
     size_t smem = 0;              // dynamic shared memory of the fused step
     const char* name = "";        // kernel form (reported by lb_kernel_info)
+    bool aos = false;             // `step` needs the interleaved 16-bit layout (PopPtrs aos = 1)
     const void* step_fn = nullptr;
     cudaError_t (*step)(const lbk::StepArgs&, dim3 grid, cudaStream_t) = nullptr;
     // the same step with one site per load (any nx); `step` moves two sites
@@ -34,7 +35,7 @@ struct LbKernelSet {
 
 // scheme: 0 equilibrium, 1 forcing; storage: lb_storage value.
 LbKernelSet lbk_kernels_d2q9(int scheme, int storage);
-LbKernelSet lbk_kernels_d3q19(int scheme, int storage);
+LbKernelSet lbk_kernels_d3q19(int scheme, int storage, int nx);
 
 // Grid size of the grid-stride auxiliary kernels.
 inline unsigned lbk_aux_blocks(size_t n) {

@@ -14,10 +14,10 @@ static LbKernelSet pick(int storage) {
     return LbKernelSet{};
 }
 
-LbKernelSet lbk_pk_forcing(int storage, LbKernelSet base);   // kern_d3q19_pk.cu
+LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet base);   // kern_d3q19_pk.cu
 
-LbKernelSet lbk_kernels_d3q19(int scheme, int storage) {
+LbKernelSet lbk_kernels_d3q19(int scheme, int storage, int nx) {
     if (scheme != 1) return pick<false>(storage);
     LbKernelSet k = pick<true>(storage);
-    return storage == 0 ? k : lbk_pk_forcing(storage, k);
+    return storage == 0 ? k : lbk_pk_forcing(storage, nx, k);
 }

@@ -8,10 +8,10 @@ using namespace lbk;
 
 namespace {
 
-template <class S, int TX, int TY, int MINB, int PF, bool MIXED>
+template <class S, int TX, int TY, int MINB, int PF, bool MIXED, bool AOS = false>
 struct PKLaunch {
     using Lay = LayoutPK<TX, TY, PairIO<S>::RAW16>;
-    static const void* fn() { return reinterpret_cast<const void*>(step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED>); }
+    static const void* fn() { return reinterpret_cast<const void*>(step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED, AOS>); }
     static cudaError_t step(const StepArgs& a, dim3 grid, cudaStream_t st) {
         static int attr_done = 0;
         if (!attr_done) {
@@ -19,7 +19,7 @@ struct PKLaunch {
             if (e != cudaSuccess) return e;
             attr_done = 1;
         }
-        step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED><<<grid, Lay::NTH, Lay::BYTES, st>>>(a);
+        step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED, AOS><<<grid, Lay::NTH, Lay::BYTES, st>>>(a);
         return cudaGetLastError();
     }
     static void apply(LbKernelSet& k, const char* name) {
@@ -31,6 +31,7 @@ struct PKLaunch {
         k.step = &step;
         k.step_pair_needs_even_nx = true;
         k.name = name;
+        k.aos = AOS;
     }
 };
 
@@ -43,10 +44,12 @@ struct PKLaunch {
 // float32 stash of a pair does not fit three CTAs per SM).  LB_D3_VARIANT
 // selects another tile / prefetch form of the pair kernel for measurements;
 // LB_D3_VARIANT=0 keeps the tile kernel.
-LbKernelSet lbk_pk_forcing(int storage, LbKernelSet k) {
+LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet k) {
     const char* env = std::getenv("LB_D3_VARIANT");
     const int v = env ? std::atoi(env) : -1;
     if (v == 0) return k;
+    // the interleaved 16-bit layout needs whole blocks in every row
+    const bool aos = nx % AOS_SITES == 0;
     if (storage == 2) {
         switch (v) {
             case 1: PKLaunch<StF16, 64, 8, 2, 0, true>::apply(k, "pairs 64x8, mixed adds"); break;
@@ -54,10 +57,27 @@ LbKernelSet lbk_pk_forcing(int storage, LbKernelSet k) {
             case 4: PKLaunch<StF16, 64, 8, 1, 2, true>::apply(k, "pairs 64x8, one CTA per SM, prefetch all"); break;
             case 8: PKLaunch<StF16, 32, 8, 3, 2, true>::apply(k, "pairs 32x8, 3 CTAs per SM, prefetch all"); break;
             case 10: PKLaunch<StF16, 64, 12, 1, 2, true>::apply(k, "pairs 64x12, prefetch all"); break;
-            default: PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched"); break;
+            case 9: PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched"); break;
+            case 14:
+                if (aos) PKLaunch<StF16, 32, 8, 3, 2, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
+                else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
+                break;
+            case 16:
+                if (aos) PKLaunch<StF16, 64, 12, 1, 2, true, true>::apply(k, "pairs 64x12, interleaved blocks, prefetch all");
+                else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
+                break;
+            case 15:
+                if (aos) PKLaunch<StF16, 32, 8, 3, 1, true, true>::apply(k, "pairs 32x8, interleaved blocks, own pair prefetched");
+                else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
+                break;
+            default:
+                if (aos) PKLaunch<StF16, 32, 8, 3, 2, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
+                else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
+                break;
         }
     } else if (storage == 3) {
-        PKLaunch<StBF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
+        if (aos) PKLaunch<StBF16, 32, 8, 3, 2, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
+        else PKLaunch<StBF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
     } else if (storage == 1 && v > 0) {
         PKLaunch<StF32, 32, 8, 2, 0, false>::apply(k, "pairs 32x8");
     }

@@ -107,6 +107,7 @@ struct lb_ctx {
     size_t buf_bytes = 0;    // bytes of one population buffer
     char* fbuf = nullptr;    // two buffers back to back
     int cur = 0;
+    bool aos = false;        // populations 1..Q-1 in the interleaved block layout (PopPtrs aos)
     double rho_l = 0, rho_g = 0;
     float fref[lbk::MAXQ] = {};
     float pref = 0.0f, rsum = 0.0f;
@@ -143,11 +144,14 @@ struct lb_ctx {
 namespace {
 
 size_t pop_offset(const lb_ctx* c, int i, int buf) {
-    // buffer layout: population 0 first, then 1..Q-1; each array padded to `pitch`
+    // buffer layout: population 0 first, then 1..Q-1; each array padded to
+    // `pitch`, or (aos) populations 1..Q-1 interleaved in blocks of
+    // AOS_SITES sites, population i's row of block 0 at (i - 1) * 2 * AOS_SITES
     size_t off = 0;
     const int elem0 = (c->p.storage == LB_F64) ? 8 : 4;
     const int elemi = (c->p.storage == LB_F64) ? 8 : (c->p.storage == LB_F32 ? 4 : 2);
-    if (i > 0) off = c->pitch * elem0 + size_t(i - 1) * c->pitch * elemi;
+    if (i > 0)
+        off = c->pitch * elem0 + (c->aos ? size_t(i - 1) * 2 * lbk::AOS_SITES : size_t(i - 1) * c->pitch * elemi);
     return size_t(buf) * c->buf_bytes + off;
 }
 
@@ -157,6 +161,7 @@ lbk::PopPtrs pop_ptrs(const lb_ctx* c, int buf) {
         pp.p[i] = c->fbuf + pop_offset(c, i, buf);
         pp.fref[i] = c->fref[i];
     }
+    pp.aos = c->aos ? 1 : 0;
     return pp;
 }
 
@@ -388,7 +393,7 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     const int elem0 = p->storage == LB_F64 ? 8 : 4;
     const int elemi = p->storage == LB_F64 ? 8 : (p->storage == LB_F32 ? 4 : 2);
     c->buf_bytes = c->pitch * (elem0 + size_t(c->Q - 1) * elemi);
-    c->ks = c->D == 2 ? lbk_kernels_d2q9(p->scheme, p->storage) : lbk_kernels_d3q19(p->scheme, p->storage);
+    c->ks = c->D == 2 ? lbk_kernels_d2q9(p->scheme, p->storage) : lbk_kernels_d3q19(p->scheme, p->storage, p->nx);
     if (!c->ks.step) { delete c; return fail(LB_EINVAL, "no kernel for this combination"); }
     // two sites per halo load need an even nx; LB_NO_PAIR selects the
     // one-site form (same arithmetic) everywhere, for comparison
@@ -400,7 +405,10 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
         c->ks.threads = c->ks.threads1;
         c->ks.smem = c->ks.smem1;
         c->ks.name = c->ks.name1;
+        c->ks.aos = false;
     }
+    // the interleaved layout holds whole blocks of sites (pitch is a multiple of 128)
+    c->aos = c->ks.aos && c->p.storage >= LB_F16DEV && c->pitch % lbk::AOS_SITES == 0;
 
     cudaError_t e = cudaMalloc(&c->fbuf, 2 * c->buf_bytes);
     if (e != cudaSuccess) { delete c; return fail(LB_ENOMEM, std::string("population buffers: ") + cudaGetErrorString(e)); }

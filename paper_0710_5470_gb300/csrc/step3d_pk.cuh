@@ -102,6 +102,8 @@ struct PairIO<StF16> {
     __device__ __forceinline__ static void st1(char* p, unsigned e, float v) {
         reinterpret_cast<__half*>(p)[e] = __float2half_rn(v);
     }
+    __device__ __forceinline__ static void st2p(char* p, P2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
+    __device__ __forceinline__ static void st1p(char* p, float v) { *reinterpret_cast<__half*>(p) = __float2half_rn(v); }
     // rho = (rsum + f_0) + (d_1 + ... + d_9) + (d_10 + ... + d_18), each run of
     // nine summed in order into a float32 accumulator
     __device__ __forceinline__ static P2 rho(float2 f0, const W (&d)[18], float rsum) {
@@ -132,6 +134,10 @@ struct PairIO<StBF16> {
     __device__ __forceinline__ static void st1(char* p, unsigned e, float v) {
         reinterpret_cast<__nv_bfloat16*>(p)[e] = __float2bfloat16_rn(v);
     }
+    __device__ __forceinline__ static void st2p(char* p, P2 v) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
+    }
+    __device__ __forceinline__ static void st1p(char* p, float v) { *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v); }
     __device__ __forceinline__ static P2 rho(float2 f0, const W (&d)[18], float rsum) {
         const P2 a = pp(rsum) + P2{f0};
         float a0 = a.v.x, a1 = a.v.y, b0 = 0.0f, b1 = 0.0f;
@@ -318,10 +324,19 @@ struct LayoutPK {
     __host__ __device__ static constexpr int mp_index(int sx, int sy) { return (sx & 1) * (SY * SXH) + sy * SXH + (sx >> 1); }
 };
 
+// Byte offset of site q in the interleaved 16-bit layout (PopPtrs aos = 1):
+// blocks of AOS_SITES sites, 18 rows of AOS_SITES values each.
+__host__ __device__ __forceinline__ unsigned aos_bytes(unsigned q) {
+    return (q / AOS_SITES) * (2 * AOS_BLOCK_HALVES) + (q % AOS_SITES) * 2;
+}
+
 // PF: items whose next-plane loads are issued one plane ahead into registers
 // (0 none, 1 the own pair, 2 every item); the others load at the start of
 // stage A.  MIXED: densities by mixed-precision adds (16-bit storage).
-template <class S, int TX, int TY, int MINB, int PF, bool MIXED>
+// AOS: populations 1..18 in the interleaved block layout (nx a multiple of
+// AOS_SITES): one address per site, the 18 rows at fixed offsets from it;
+// args.src[1] / args.dst[1] point at the first block.
+template <class S, int TX, int TY, int MINB, int PF, bool MIXED, bool AOS = false>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const StepArgs args) {
     using L = D3Q19;
     using IO = PairIO<S>;
@@ -331,6 +346,8 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
     constexpr int H = Lay::H, HX = Lay::HX, TXP = Lay::TXP, NTH = Lay::NTH;
     constexpr int RX = Lay::RX, RXP = Lay::RXP, SX = Lay::SX;
     constexpr int NAH = Lay::NAH, NBR = Lay::NBR;
+    static_assert(!AOS || RAW16, "interleaved layout: 16-bit storage only");
+    constexpr int ROWB = 2 * AOS_SITES;             // bytes of one population row of a block
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* rho_s = reinterpret_cast<float*>(smem_raw + Lay::OFF_RHO);
@@ -418,6 +435,11 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
         if (v == vol) v = 0;
     };
 
+    // interleaved layout: byte offset of each item within its plane (planes
+    // start on a block: nx * ny is a multiple of AOS_SITES)
+    unsigned a_h[1 + NAH];
+#pragma unroll
+    for (int m = 0; m < 1 + NAH; ++m) a_h[m] = AOS ? aos_bytes(a_in[m]) : 0u;
     // raw populations of the items of plane ld_off
     float2 r0[1 + NAH];
     Wd ri[1 + NAH][18];
@@ -427,10 +449,16 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
             if (m >= mb && m < me && (m == 0 || a_rs[m] >= 0)) {
                 const unsigned q = unsigned(ld_off) + a_in[m];
                 r0[m] = reinterpret_cast<const float2*>(args.src[0])[q >> 1];
-                static_for<1, 19>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    ri[m][i - 1] = IO::ld(args.src[i], q);
-                });
+                if constexpr (AOS) {
+                    const char* b = args.src[1] + (size_t(unsigned(ld_off)) / AOS_SITES) * (2 * AOS_BLOCK_HALVES) + a_h[m];
+#pragma unroll
+                    for (int i = 1; i < 19; ++i) ri[m][i - 1] = *reinterpret_cast<const unsigned*>(b + (i - 1) * ROWB);
+                } else {
+                    static_for<1, 19>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        ri[m][i - 1] = IO::ld(args.src[i], q);
+                    });
+                }
             }
         }
     };
@@ -461,10 +489,10 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
                     *reinterpret_cast<float2*>(rho_w + a_rs[m]) = r.v;
                     if (m == 0) {
                         // thread-private stash of the own pair: raw populations and (rho, j)
-                        P2 j[3];
-                        pair_momentum<S>(ri[0], j);
                         float2* mo = mom_s + slot * 4 * NTH + tid;
                         mo[0] = r.v;
+                        P2 j[3];
+                        pair_momentum<S>(ri[0], j);
                         mo[NTH] = j[0].v;
                         mo[2 * NTH] = j[1].v;
                         mo[3 * NTH] = j[2].v;
@@ -579,14 +607,11 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
             const int slot = (it - 2) % Lay::NST;
             const float2* mo = mom_s + slot * 4 * NTH + tid;
             const P2 rho = P2{mo[0]};
-            const P2 j[3] = {P2{mo[NTH]}, P2{mo[2 * NTH]}, P2{mo[3 * NTH]}};
             const P2 G[3] = {Gc[0], Gc[1], Gc[2]};
             const P2 lap = lapc;
             if (own) bad |= !(rho.v.x > 0.f) || !(rho.v.x < 1e30f) || !(rho.v.y > 0.f) || !(rho.v.y < 1e30f);
-            PairColl K;
-            K.prep(rho, j, G, lap, gf, ph);
             const unsigned char* st = stash + size_t(slot) * Lay::STW * 4 * NTH;
-            // raw stashed populations: w[0], w[1] = f_0 pair, then one word per population
+            // raw stashed populations: the f_0 pair, then one word per population
             Wd w[19];
             float2 f0;
             if constexpr (RAW16) {
@@ -606,21 +631,52 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
 #pragma unroll
                 for (int i = 1; i < 19; ++i) w[i] = s2[i * NTH];
             }
+            const P2 j[3] = {P2{mo[NTH]}, P2{mo[2 * NTH]}, P2{mo[3 * NTH]}};
+            PairColl K;
+            K.prep(rho, j, G, lap, gf, ph);
             if (own) {
                 // push f*_i(r) to r + e_i: populations with e_x = 0 as aligned pairs,
                 // the others site by site
+                // interleaved layout: block-row byte offsets of the destination
+                // planes (64-bit) and rows, block byte offsets of the x columns
+                size_t zb[3] = {0, 0, 0};
+                unsigned yb[3] = {0, 0, 0}, cb[4] = {0, 0, 0, 0};
+                if constexpr (AOS) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        zb[k] = size_t(unsigned(zr[k])) / AOS_SITES * (2 * AOS_BLOCK_HALVES);
+                        yb[k] = yr[k] / AOS_SITES * (2 * AOS_BLOCK_HALVES);
+                    }
+                    cb[0] = aos_bytes(xm1);
+                    cb[1] = aos_bytes(xc);
+                    cb[2] = aos_bytes(xc + 1);
+                    cb[3] = aos_bytes(xp2);
+                }
                 auto store = [&](auto I, P2 v) {
                     constexpr int i = decltype(I)::value;
                     constexpr int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-                    const unsigned row = unsigned(zr[1 + ez]) + yr[1 + ey];
-                    if constexpr (ex == 0) {
-                        IO::st2(args.dst[i], row + xc, v);
-                    } else if constexpr (ex == 1) {
-                        IO::st1(args.dst[i], row + xc + 1, v.v.x);
-                        IO::st1(args.dst[i], row + xp2, v.v.y);
+                    if constexpr (AOS) {
+                        char* b = args.dst[1] + zb[1 + ez] + yb[1 + ey] + (i - 1) * ROWB;
+                        if constexpr (ex == 0) {
+                            IO::st2p(b + cb[1], v);
+                        } else if constexpr (ex == 1) {
+                            IO::st1p(b + cb[2], v.v.x);
+                            IO::st1p(b + cb[3], v.v.y);
+                        } else {
+                            IO::st1p(b + cb[0], v.v.x);
+                            IO::st1p(b + cb[1], v.v.y);
+                        }
                     } else {
-                        IO::st1(args.dst[i], row + xm1, v.v.x);
-                        IO::st1(args.dst[i], row + xc, v.v.y);
+                        const unsigned row = unsigned(zr[1 + ez]) + yr[1 + ey];
+                        if constexpr (ex == 0) {
+                            IO::st2(args.dst[i], row + xc, v);
+                        } else if constexpr (ex == 1) {
+                            IO::st1(args.dst[i], row + xc + 1, v.v.x);
+                            IO::st1(args.dst[i], row + xp2, v.v.y);
+                        } else {
+                            IO::st1(args.dst[i], row + xm1, v.v.x);
+                            IO::st1(args.dst[i], row + xc, v.v.y);
+                        }
                     }
                 };
                 const P2 o0 = fma(K.omw, P2{f0}, K.c0);
