@@ -387,28 +387,29 @@ def run_native(args):
                                "max_v": vst["max_v"]}
 
     # time to steady state (second half of the metric): plain float64, one
-    # instance per launch, against one batch in fp16-deviation storage, both
-    # stopped by the same reference test (float64 steady max|u| within 5%,
-    # bulk densities within 1e-3, 10 consecutive checks)
+    # instance per launch, to max|u(t) - u(t - 100)| < 1e-10, against one batch
+    # in fp16-deviation storage stopped by its own self-contained test (max|u|
+    # and bulk densities settled; no steady values known in advance); accuracy
+    # of the fast steady states afterwards against the float64 ones
     tts = None
     if rank == 0 and world == 1 and not args.no_steady:
         from paper_0710_5470_gb300 import steady
-        ex = steady.experiment(count=16, seed=0, arms=("f16dev",))
-        fast_s = ex["batch_f16dev"]["seconds"]
+        ex = steady.experiment_self(count=16, seed=0, arms=("f16dev",))
+        fa = ex["batch_f16dev_self"]
+        pl = ex["plain_f64_tol"]
         tts = {"workload": "first 16 instances of the D2Q9 drop sweep seed 0 (side 64-384, T 0.50-0.56, "
-                           "kappa 0.002-0.03, tau 0.6-1.5, one centred drop, forcing scheme); the "
-                           f"{ex['sweep']['converged_f64']} whose float64 run converges "
-                           f"({ex['sweep']['unstable_f64']} unstable, {ex['sweep']['not_converged_f64']} not "
-                           "converged in 2e5 steps)",
-               "test": "max|u| within 5% and max/min rho within 1e-3 of the float64 steady values for 10 "
-                       "consecutive checks, every 100 steps",
-               "plain_f64_s": ex["plain_f64_ref"]["seconds"], "fast_s": fast_s,
-               "speedup": ex["plain_f64_ref"]["seconds"] / fast_s,
-               "fast": "one batch, fp16-deviation storage, CUDA-graph replay, autotuned tile",
-               "plain_f64_to_du_1e-10_s": ex["plain_f64_tol"]["seconds"],
-               "converged": {"plain": ex["plain_f64_ref"]["converged"], "fast": ex["batch_f16dev"]["converged"]},
-               "accuracy_fast": {k: ex["batch_f16dev"].get(k) for k in ("max_u_rel_err_max", "rho_max_err_max",
-                                                                        "rho_min_err_max")}}
+                           "kappa 0.002-0.03, tau 0.6-1.5, one centred drop, forcing scheme)",
+               "plain": "float64, one instance per batch, tanh start, to max|u(t) - u(t-100)| < 1e-10",
+               "fast": "one batch, fp16-deviation storage, CUDA-graph replay, autotuned tile, stopped when "
+                       "max|u| changes by < 5e-4 of itself and max/min rho by < 1e-5 per 100 steps for 10 "
+                       "consecutive checks (lb_batch_set_self_test; no reference values)",
+               "plain_f64_s": pl["seconds"], "fast_s": fa["seconds"], "speedup": pl["seconds"] / fa["seconds"],
+               "converged": {"plain": pl["converged"], "fast": fa["converged"]},
+               "mean_steps": {"plain": pl["mean_steps"], "fast": fa["mean_steps"]},
+               "accuracy_fast": {"max_u_rel_err_max": fa.get("max_u_rel_err_max"),
+                                 "rho_max_err_max": fa.get("rho_max_err_max"),
+                                 "rho_min_err_max": fa.get("rho_min_err_max"),
+                                 "within_5pct_of_f64_max_u": f"{fa['within_5pct']} of {fa['compared']}"}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -84,8 +84,14 @@ typedef struct {
     double max_u;         /* max_r |u|, u the lattice velocity of Eq. 3 */
     double max_v;         /* max_r |v|, v = u + g/(2 rho) (Eq. 40); = max_u for the equilibrium scheme */
     double min_rho, max_rho;
-    long long step;       /* time steps taken since the last init */
+    long long step;       /* time steps taken since the last init (or the step of an imported state) */
     int status;           /* lb_status of the context */
+    double dP;            /* p0(rho at the inside probe) - p0(rho at the outside probe): the pressure
+                             jump across the interface of Sec. IV (Eq. 2); probes: lb_set_probes */
+    double max_du;        /* max_r |u(r) - u_prev(r)|, u_prev the u of the previous lb_stats_get on this
+                             context: the steady-state test of Sec. IV runs; -1 on the first call after an
+                             init, a population or state import */
+    long long du_steps;   /* steps between this call and that previous call (0 when max_du = -1) */
 } lb_stats;
 
 /* Library version string (static storage). */
@@ -164,8 +170,42 @@ lb_status lb_synchronize(lb_ctx* ctx);
  * = u for the equilibrium scheme).  Any output may be NULL.  Synchronises. */
 lb_status lb_fields(lb_ctx* ctx, double* rho, double* u, double* v);
 
-/* float64 reductions of the current state (see lb_stats).  Synchronises. */
+/* float64 reductions of the current state (see lb_stats).  Synchronises.
+ * Keeps a float64 copy of u (dim * N doubles, allocated by the first call)
+ * as the reference of the next call's max_du. */
 lb_status lb_stats_get(lb_ctx* ctx, lb_stats* out);
+
+/* Probe sites of lb_stats.dP: inside[3], outside[3] = (x, y, z), each in
+ * [0, n) per axis (z = 0 for D2Q9); LB_EINVAL otherwise.  lb_create sets
+ * inside = (nx/2, ny/2, nz/2), outside = (0, 0, 0) (a centred drop);
+ * lb_init_drops sets inside = the site nearest to the first drop centre and
+ * outside = the site farthest (periodic minimum image) from every centre,
+ * searched on a grid of step ceil(n/64) per axis. */
+lb_status lb_set_probes(lb_ctx* ctx, const int* inside, const int* outside);
+lb_status lb_get_probes(const lb_ctx* ctx, int* inside, int* outside);
+
+/* ---- Checkpoint / restart (no counterpart in the paper) ---------------------
+ *
+ * lb_get_state exports the raw stored state: a fixed header (magic "LBGBSTA1",
+ * version 1, lattice, nx, ny, nz, scheme, storage, population layout, the step
+ * counter, the parameter hash of lb_params_hash and the payload size) followed
+ * by the bytes of the current population buffer exactly as stored (float64 /
+ * float32 / fp16 or bf16 deviations, in the context's layout).  buf = NULL:
+ * *bytes receives the size needed; otherwise *bytes is the capacity of the
+ * caller-owned host buffer buf (LB_EINVAL if smaller) and receives the size
+ * written.  Synchronises.  LB_ESTATE before the first init.
+ * lb_set_state imports such a buffer into a context created with the same
+ * lb_params (LB_EINVAL if the header, the parameter hash or the size differ),
+ * sets the step counter from it and clears the context's device status; the
+ * next steps continue the exported run bit for bit (N + N steps with an
+ * export and import in between equal 2N steps).  Synchronises. */
+lb_status lb_get_state(lb_ctx* ctx, void* buf, size_t* bytes);
+lb_status lb_set_state(lb_ctx* ctx, const void* buf, size_t bytes);
+
+/* 64-bit FNV-1a hash of the parameters that define a run (lattice, sizes,
+ * scheme, storage, a, b, T, kappa, tau, rho_ref); host only.  LB_EINVAL for
+ * an invalid parameter set (the checks of lb_create). */
+lb_status lb_params_hash(const lb_params* p, unsigned long long* hash);
 
 /* Free parameters of the D2Q9 model (Sec. III, Eq. 16): the diagonal weights w^p_{5-8} (pressure),
  * w^t_{5-8} (interface term) and w^xx_{5-8} (M term) of the equilibrium, and the diagonal
@@ -189,7 +229,12 @@ lb_status lb_set_free_params(lb_ctx* ctx, const lb_free_params* params);
 lb_status lb_shape(const lb_ctx* ctx, long long* n_sites, int* q);
 
 /* Device pointer of the current population buffer and its byte size, for
- * callers that stage inputs in device memory themselves. */
+ * callers that stage inputs in device memory themselves.  Layout: population
+ * 0 as one array of pitch = N rounded up to a multiple of 128 elements, then
+ * populations 1..Q-1, each one array of pitch elements; except for D3Q19
+ * forcing-scheme contexts with fp16 / bf16 deviation storage and nx a multiple
+ * of 32, whose populations 1..18 are interleaved in blocks of 32 sites (the 18
+ * rows of 32 values of a block contiguous, 1152 bytes; site q in block q/32). */
 lb_status lb_device_state(lb_ctx* ctx, void** dptr, size_t* bytes);
 
 /* Launch form of the context's fused step kernel (Eq. 4 per site, one launch
@@ -249,6 +294,17 @@ lb_status lb_batch_set_reference(lb_batch* batch, int k, double umax_ref, double
 /* Parameters of the reference test (defaults band 0.05, tol_rho 1e-3, hold 10); LB_EINVAL for a
  * negative band or tol_rho or hold < 1. */
 lb_status lb_batch_set_band(lb_batch* batch, double band, double tol_rho, int hold);
+/* Self-contained steady-state test for instances without a reference (the
+ * paper defines no test; Sec. IV runs to a fixed time): an instance is steady
+ * once, for `hold` consecutive checks, its max|u| changed by at most
+ * rtol_u * max|u| and its max rho and min rho by at most tol_rho since the
+ * previous check.  It needs no steady values known in advance, and its
+ * thresholds can sit above the rounding floor of reduced storage, whose
+ * max|u(t) - u(t - every)| never falls below ~1e-8.  rtol_u = 0 switches it off
+ * (the max|u(t) - u(t - every)| < tol test of lb_batch_run_to_steady).  Resets
+ * every instance's count of consecutive checks.  LB_EINVAL for negative or
+ * non-finite thresholds or hold < 1. */
+lb_status lb_batch_set_self_test(lb_batch* batch, double rtol_u, double tol_rho, int hold);
 /* max|u(t) - u(t - every)|, max|u|, max rho and min rho of each instance at its last check (0 before
  * the first check; frozen at retirement).  Any output may be NULL.  Synchronises. */
 lb_status lb_batch_last_check(lb_batch* batch, double* du, double* umax, double* rho_max, double* rho_min);

@@ -3,6 +3,7 @@
 // population import/export and float64 reductions.  None of these is on the
 // per-step path; they read and write global memory directly.
 #pragma once
+#include "field_reduce.cuh"
 #include "step_kernel.cuh"
 
 namespace lbk {
@@ -222,58 +223,7 @@ __global__ void set_pops_kernel(PopPtrs dst, size_t n, const double* in) {
 }
 
 // ---------------------------------------------------------------- reductions
-// Per-block partials of: mass, momentum[3], max|u|, max|v|, min rho, max rho.
-constexpr int NSTAT = 8;
-constexpr int STAT_THREADS = 256;
-
-static __global__ void __launch_bounds__(STAT_THREADS)
-    stats_partial_kernel(const double* rho, const double* u, const double* v, int dim, size_t n, double* partial) {
-    __shared__ double sh[NSTAT][STAT_THREADS];
-    double acc[NSTAT] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1e300, -1e300};
-    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < n; idx += size_t(gridDim.x) * blockDim.x) {
-        const double r = rho[idx];
-        acc[0] += r;
-        double u2 = 0.0, v2 = 0.0;
-        for (int c = 0; c < dim; ++c) {
-            const double uc = u[c * n + idx], vc = v[c * n + idx];
-            acc[1 + c] += r * uc;
-            u2 += uc * uc;
-            v2 += vc * vc;
-        }
-        acc[4] = fmax(acc[4], sqrt(u2));
-        acc[5] = fmax(acc[5], sqrt(v2));
-        acc[6] = fmin(acc[6], r);
-        acc[7] = fmax(acc[7], r);
-    }
-    for (int k = 0; k < NSTAT; ++k) sh[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = STAT_THREADS / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
-            sh[4][threadIdx.x] = fmax(sh[4][threadIdx.x], sh[4][threadIdx.x + s]);
-            sh[5][threadIdx.x] = fmax(sh[5][threadIdx.x], sh[5][threadIdx.x + s]);
-            sh[6][threadIdx.x] = fmin(sh[6][threadIdx.x], sh[6][threadIdx.x + s]);
-            sh[7][threadIdx.x] = fmax(sh[7][threadIdx.x], sh[7][threadIdx.x + s]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < NSTAT; ++k) partial[size_t(blockIdx.x) * NSTAT + k] = sh[k][0];
-}
-
-// Folds the per-block partials in block order (deterministic).
-static __global__ void stats_final_kernel(const double* partial, int nblocks, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double acc[NSTAT] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1e300, -1e300};
-    for (int b = 0; b < nblocks; ++b) {
-        const double* p = partial + size_t(b) * NSTAT;
-        for (int k = 0; k < 4; ++k) acc[k] += p[k];
-        acc[4] = fmax(acc[4], p[4]);
-        acc[5] = fmax(acc[5], p[5]);
-        acc[6] = fmin(acc[6], p[6]);
-        acc[7] = fmax(acc[7], p[7]);
-    }
-    for (int k = 0; k < NSTAT; ++k) out[k] = acc[k];
-}
+// The float64 field reductions of lb_stats_get: field_reduce.cuh.
+constexpr int STAT_THREADS = FR_THREADS;
 
 }  // namespace lbk

@@ -123,8 +123,17 @@ __global__ void __launch_bounds__(TX* TY) batch_check_kernel(BatchState bs, cons
 // band * (its reference) of the reference and (with reference densities) max
 // rho and min rho within tol_rho of theirs, for `hold` consecutive checks.
 // One block; instances are visited in order, so the list is deterministic.
+// Convergence check after `every` steps, per active instance, in this order:
+//  - a reference set (lb_batch_set_reference): max|u| within band of it and the
+//    bulk densities within tol_rho of it for `hold` consecutive checks;
+//  - else, with self_rtol > 0 (lb_batch_set_self_test): the instance's own
+//    observables settled - max|u| changed by at most self_rtol of itself and
+//    max rho, min rho by at most self_tol_rho since the previous check, for
+//    self_hold consecutive checks (needs no steady values known in advance);
+//  - else max|u(t) - u(t - every)| < tol.
 __global__ void batch_finalize_kernel(BatchState bs, double tol, int every, long long min_steps, double band,
-                                      double tol_rho, int hold) {
+                                      double tol_rho, int hold, double self_rtol, double self_tol_rho,
+                                      int self_hold) {
     __shared__ int offs[1025];
     __shared__ long long g;
     if (threadIdx.x == 0) {
@@ -138,6 +147,7 @@ __global__ void batch_finalize_kernel(BatchState bs, double tol, int every, long
             const double um = __longlong_as_double((long long)bs.maxu[k]);
             const double hi = __longlong_as_double((long long)bs.maxrho[k]);
             const double lo = __longlong_as_double((long long)bs.minrho[k]);
+            const double prev_um = bs.last[4 * k + 1], prev_hi = bs.last[4 * k + 2], prev_lo = bs.last[4 * k + 3];
             bs.last[4 * k] = du;
             bs.last[4 * k + 1] = um;
             bs.last[4 * k + 2] = hi;
@@ -150,6 +160,12 @@ __global__ void batch_finalize_kernel(BatchState bs, double tol, int every, long
                 const int c = in ? bs.inband[k] + 1 : 0;
                 bs.inband[k] = c;
                 done = c >= hold;
+            } else if (self_rtol > 0.0) {
+                const bool in = fabs(um - prev_um) <= self_rtol * um && fabs(hi - prev_hi) <= self_tol_rho &&
+                                fabs(lo - prev_lo) <= self_tol_rho;
+                const int c = in ? bs.inband[k] + 1 : 0;
+                bs.inband[k] = c;
+                done = c >= self_hold;
             } else {
                 done = du < tol;
             }

@@ -130,6 +130,8 @@ struct lb_batch {
     int* d_inband = nullptr;
     double band = 0.05, tol_rho = 1e-3;
     int hold = 10;
+    double self_rtol = 0.0, self_tol_rho = 0.0;   // lb_batch_set_self_test (0: off)
+    int self_hold = 10;
     long long* d_steps = nullptr;
     long long* d_gstep = nullptr;
     double* d_uprev = nullptr;
@@ -143,6 +145,8 @@ struct lb_batch {
     int graph_tile = -1;
     double graph_band = -1, graph_tol_rho = -1;
     int graph_hold = -1;
+    double graph_self_rtol = -1, graph_self_tol_rho = -1;
+    int graph_self_hold = -1;
 };
 
 namespace {
@@ -468,7 +472,8 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
     // one graph: `every` steps, the convergence check, retirement and work-list rebuild
     if (!B->graph || B->graph_every != every || B->graph_tol != tol || B->graph_min != min_steps ||
         B->graph_tile != B->tile || B->graph_band != B->band || B->graph_hold != B->hold ||
-        B->graph_tol_rho != B->tol_rho) {
+        B->graph_tol_rho != B->tol_rho || B->graph_self_rtol != B->self_rtol ||
+        B->graph_self_tol_rho != B->self_tol_rho || B->graph_self_hold != B->self_hold) {
         if (B->graph) cudaGraphExecDestroy(B->graph);
         B->graph = nullptr;
         cudaGraph_t g;
@@ -477,7 +482,8 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
         const BatchState bs = state_of(B);
         for (int s = 0; s < every; ++s) B->k.step(bs, B->buf, s & 1, B->max_items, B->stream);
         B->k.check(bs, B->buf, 0, B->max_items, B->stream);
-        batch_finalize_kernel<<<1, 1024, 0, B->stream>>>(bs, tol, every, min_steps, B->band, B->tol_rho, B->hold);
+        batch_finalize_kernel<<<1, 1024, 0, B->stream>>>(bs, tol, every, min_steps, B->band, B->tol_rho, B->hold,
+                                                         B->self_rtol, B->self_tol_rho, B->self_hold);
         e = cudaStreamEndCapture(B->stream, &g);
         if (e != cudaSuccess) return cuda_err(e, "end capture");
         e = cudaGraphInstantiate(&B->graph, g, 0);
@@ -490,6 +496,9 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
         B->graph_band = B->band;
         B->graph_tol_rho = B->tol_rho;
         B->graph_hold = B->hold;
+        B->graph_self_rtol = B->self_rtol;
+        B->graph_self_tol_rho = B->self_tol_rho;
+        B->graph_self_hold = B->self_hold;
     }
     // the device step counter continues from the host one
     cudaError_t e = cudaMemcpyAsync(B->d_gstep, &B->gstep, sizeof(long long), cudaMemcpyHostToDevice, B->stream);
@@ -535,6 +544,18 @@ lb_status lb_batch_set_band(lb_batch* B, double band, double tol_rho, int hold) 
     B->band = band;
     B->tol_rho = tol_rho;
     B->hold = hold;
+    return LB_OK;
+}
+
+lb_status lb_batch_set_self_test(lb_batch* B, double rtol_u, double tol_rho, int hold) {
+    if (!B || !(rtol_u >= 0.0) || !(tol_rho >= 0.0) || hold < 1 || !std::isfinite(rtol_u) || !std::isfinite(tol_rho))
+        return fail(LB_EINVAL, "need finite rtol_u >= 0, tol_rho >= 0 and hold >= 1");
+    B->self_rtol = rtol_u;
+    B->self_tol_rho = tol_rho;
+    B->self_hold = hold;
+    cudaError_t e = cudaMemsetAsync(B->d_inband, 0, B->n * sizeof(int), B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return cuda_err(e, "batch self test");
     return LB_OK;
 }
 

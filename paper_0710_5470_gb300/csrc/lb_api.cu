@@ -120,6 +120,12 @@ struct lb_ctx {
     bool initialised = false;
     long long step = 0;
     lb_status sticky = LB_OK;
+    // pressure probes of lb_stats dP (x, y, z of the inside and outside sites)
+    int probe_in[3] = {0, 0, 0}, probe_out[3] = {0, 0, 0};
+    // velocity field of the previous lb_stats_get (max_du) and its step
+    double* w_uprev = nullptr;
+    bool uprev_valid = false;
+    long long uprev_step = 0;
     // lazily allocated work arrays (fields, reductions)
     double* w_rho = nullptr;
     double* w_u = nullptr;
@@ -275,13 +281,13 @@ lb_status ensure_work(lb_ctx* c) {
     if (c->w_part) return LB_OK;
     const size_t n = c->N;
     const int nmc = c->D == 3 ? 6 : 3;
-    c->stat_blocks = int(std::min<size_t>(1024, (n + lbk::STAT_THREADS - 1) / lbk::STAT_THREADS));
+    c->stat_blocks = int(std::min<size_t>(1024, (n + lbk::FR_THREADS - 1) / lbk::FR_THREADS));
     if (c->stat_blocks < 1) c->stat_blocks = 1;
     cudaError_t e = cudaSuccess;
     if ((!c->w_u && (e = cudaMalloc(&c->w_u, 3 * n * sizeof(double))) != cudaSuccess) ||
         (!c->w_v && (e = cudaMalloc(&c->w_v, 3 * n * sizeof(double))) != cudaSuccess) ||
         (!c->w_mp && (e = cudaMalloc(&c->w_mp, nmc * n * sizeof(double))) != cudaSuccess) ||
-        (e = cudaMalloc(&c->w_part, (size_t(c->stat_blocks) + 1) * lbk::NSTAT * sizeof(double))) != cudaSuccess) {
+        (e = cudaMalloc(&c->w_part, (size_t(c->stat_blocks) + 1) * lbk::FR_NQ * sizeof(double))) != cudaSuccess) {
         c->w_part = nullptr;
         return fail(LB_ENOMEM, std::string("work arrays: ") + cudaGetErrorString(e));
     }
@@ -348,6 +354,82 @@ lb_status validate(const lb_params* p) {
     if (p->rho_ref < 0 || (p->rho_ref > 0 && p->rho_ref * p->b >= 1.0)) return fail(LB_EINVAL, "rho_ref out of range");
     return LB_OK;
 }
+
+// Pressure probes of a drop configuration: inside = the site nearest to the
+// first drop's centre; outside = the site farthest (periodic minimum image)
+// from every centre, searched on a grid of step ceil(n/64) per axis (every
+// site when n <= 64), the first such site in x-fastest order.
+void set_drop_probes(lb_ctx* c, int ndrops, const double* centres) {
+    const int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    const int D = c->D;
+    for (int a = 0; a < 3; ++a) {
+        long long v = a < D ? (long long)std::llround(centres[a]) : 0;
+        v %= n[a];
+        if (v < 0) v += n[a];
+        c->probe_in[a] = int(v);
+    }
+    int step[3], best[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) step[a] = std::max(1, (n[a] + 63) / 64);
+    double best_d = -1.0;
+    for (int z = 0; z < n[2]; z += step[2])
+        for (int y = 0; y < n[1]; y += step[1])
+            for (int x = 0; x < n[0]; x += step[0]) {
+                const int xyz[3] = {x, y, z};
+                double dmin = 1e300;
+                for (int k = 0; k < ndrops; ++k) {
+                    double d2 = 0.0;
+                    for (int a = 0; a < D; ++a) {
+                        double dd = std::fabs(xyz[a] - centres[k * D + a]);
+                        dd = std::fmod(dd, double(n[a]));
+                        dd = std::min(dd, n[a] - dd);
+                        d2 += dd * dd;
+                    }
+                    dmin = std::min(dmin, d2);
+                }
+                if (dmin > best_d) {
+                    best_d = dmin;
+                    best[0] = x;
+                    best[1] = y;
+                    best[2] = z;
+                }
+            }
+    for (int a = 0; a < 3; ++a) c->probe_out[a] = best[a];
+}
+
+// 64-bit FNV-1a over the bytes of the values that define a context's dynamics
+// and its state layout.
+struct Fnv {
+    unsigned long long h = 1469598103934665603ULL;
+    template <class T>
+    void add(const T& v) {
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+        for (size_t i = 0; i < sizeof(T); ++i) {
+            h ^= b[i];
+            h *= 1099511628211ULL;
+        }
+    }
+};
+
+unsigned long long params_hash(const lb_params* p) {
+    Fnv f;
+    const int ints[6] = {p->lattice, p->nx, p->ny, p->nz, p->scheme, p->storage};
+    const double dbl[6] = {p->a, p->b, p->T, p->kappa, p->tau, p->rho_ref};
+    for (int v : ints) f.add(v);
+    for (double v : dbl) f.add(v);
+    return f.h;
+}
+
+// Header of an exported state (lb_get_state); the raw population buffer follows it.
+struct StateHeader {
+    char magic[8];                 // "LBGBSTA1"
+    unsigned int version;          // 1
+    unsigned int header_bytes;     // sizeof(StateHeader)
+    int lattice, nx, ny, nz, scheme, storage, aos, pad;
+    long long step;
+    unsigned long long params_hash;
+    unsigned long long payload_bytes;
+};
+constexpr char STATE_MAGIC[8] = {'L', 'B', 'G', 'B', 'S', 'T', 'A', '1'};
 
 }  // namespace
 
@@ -440,6 +522,9 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
         }
         c->grid = dim3(unsigned(work.size()), 1, 1);
     }
+    c->probe_in[0] = p->nx / 2;
+    c->probe_in[1] = p->ny / 2;
+    c->probe_in[2] = p->nz / 2;
     *out = c;
     return LB_OK;
 }
@@ -455,6 +540,7 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->w_mp);
     cudaFree(c->w_part);
     cudaFree(c->w_io);
+    cudaFree(c->w_uprev);
     cudaFree(c->d_work);
     cudaFree(c->p2_rho);
     cudaFree(c->p2_gl);
@@ -539,6 +625,7 @@ static lb_status init_from_device_rho(lb_ctx* c, const double* d_rho, const doub
     if (e != cudaSuccess) return record(c, e, "status reset");
     c->initialised = true;
     c->step = 0;
+    c->uprev_valid = false;
     return sync_status(c);
 }
 
@@ -569,6 +656,7 @@ lb_status lb_init_drops(lb_ctx* c, int ndrops, const double* centres, const doub
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) { cudaFree(d_drops); return record(c, e, "drop density"); }
+    if (ndrops > 0) set_drop_probes(c, ndrops, centres);
     s = init_from_device_rho(c, c->w_rho, nullptr);
     cudaFree(d_drops);
     return s;
@@ -598,6 +686,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f) {
     if (e != cudaSuccess) return record(c, e, "set populations");
     c->initialised = true;
     c->step = 0;
+    c->uprev_valid = false;
     return sync_status(c);
 }
 
@@ -765,14 +854,30 @@ lb_status lb_stats_get(lb_ctx* c, lb_stats* out) {
     if (!out) return fail(LB_EINVAL, "null output");
     if (!c->initialised) return fail(LB_ESTATE, "state not initialised");
     if ((s = compute_fields(c, true)) != LB_OK) return s;
+    const size_t du = size_t(c->D) * c->N;
+    if (!c->w_uprev) {
+        cudaError_t e = cudaMalloc(&c->w_uprev, du * sizeof(double));
+        if (e != cudaSuccess) {
+            c->w_uprev = nullptr;
+            return fail(LB_ENOMEM, std::string("previous velocity field: ") + cudaGetErrorString(e));
+        }
+        c->uprev_valid = false;
+    }
     double* part = c->w_part;
-    double* res = c->w_part + size_t(c->stat_blocks) * lbk::NSTAT;
-    lbk::stats_partial_kernel<<<c->stat_blocks, lbk::STAT_THREADS, 0, c->stream>>>(c->w_rho, c->w_u, c->w_v, c->D,
-                                                                                   c->N, part);
-    lbk::stats_final_kernel<<<1, 32, 0, c->stream>>>(part, c->stat_blocks, res);
-    double h[lbk::NSTAT];
+    double* res = c->w_part + size_t(c->stat_blocks) * lbk::FR_NQ;
+    lbk::fr_partial_kernel<lbk::FR_NQ><<<c->stat_blocks, lbk::FR_THREADS, 0, c->stream>>>(
+        c->w_rho, c->w_u, c->w_v, c->uprev_valid ? c->w_uprev : nullptr, c->D, (long long)c->N, 0, part);
+    lbk::fr_final_kernel<lbk::FR_NQ><<<1, 32, 0, c->stream>>>(part, c->stat_blocks, res);
+    double h[lbk::FR_NQ], rp[2];
+    const size_t in = (size_t(c->probe_in[2]) * c->p.ny + c->probe_in[1]) * c->p.nx + c->probe_in[0];
+    const size_t ou = (size_t(c->probe_out[2]) * c->p.ny + c->probe_out[1]) * c->p.nx + c->probe_out[0];
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rp[0], c->w_rho + in, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rp[1], c->w_rho + ou, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    // this state's velocity becomes the reference of the next call's max_du
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->w_uprev, c->w_u, du * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return record(c, e, "stats");
     s = sync_status(c);
     std::memset(out, 0, sizeof(*out));
@@ -786,7 +891,105 @@ lb_status lb_stats_get(lb_ctx* c, lb_stats* out) {
     out->max_rho = h[7];
     out->step = c->step;
     out->status = int(c->sticky);
+    out->dP = p0_vdw(rp[0], c->p.a, c->p.b, c->p.T) - p0_vdw(rp[1], c->p.a, c->p.b, c->p.T);
+    out->max_du = c->uprev_valid ? h[8] : -1.0;
+    out->du_steps = c->uprev_valid ? c->step - c->uprev_step : 0;
+    c->uprev_valid = true;
+    c->uprev_step = c->step;
     return s;
+}
+
+lb_status lb_set_probes(lb_ctx* c, const int* inside, const int* outside) {
+    if (!c) return fail(LB_EINVAL, "null context");
+    if (!inside || !outside) return fail(LB_EINVAL, "null probe");
+    const int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+    for (int a = 0; a < 3; ++a)
+        if (inside[a] < 0 || inside[a] >= n[a] || outside[a] < 0 || outside[a] >= n[a])
+            return fail(LB_EINVAL, "probe sites must lie in the lattice");
+    for (int a = 0; a < 3; ++a) {
+        c->probe_in[a] = inside[a];
+        c->probe_out[a] = outside[a];
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_probes(const lb_ctx* c, int* inside, int* outside) {
+    if (!c || !inside || !outside) return fail(LB_EINVAL, "null argument");
+    for (int a = 0; a < 3; ++a) {
+        inside[a] = c->probe_in[a];
+        outside[a] = c->probe_out[a];
+    }
+    return LB_OK;
+}
+
+lb_status lb_params_hash(const lb_params* p, unsigned long long* hash) {
+    if (!p || !hash) return fail(LB_EINVAL, "null argument");
+    lb_status s = validate(p);
+    if (s != LB_OK) return s;
+    *hash = params_hash(p);
+    return LB_OK;
+}
+
+lb_status lb_get_state(lb_ctx* c, void* buf, size_t* bytes) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!bytes) return fail(LB_EINVAL, "null size");
+    const size_t need = sizeof(StateHeader) + c->buf_bytes;
+    if (!buf) {
+        *bytes = need;
+        return LB_OK;
+    }
+    if (!c->initialised) return fail(LB_ESTATE, "state not initialised");
+    if (*bytes < need) return fail(LB_EINVAL, "buffer smaller than the state (" + std::to_string(need) + " bytes)");
+    if ((s = sync_status(c)) != LB_OK) return s;
+    StateHeader h{};
+    std::memcpy(h.magic, STATE_MAGIC, 8);
+    h.version = 1;
+    h.header_bytes = sizeof(StateHeader);
+    h.lattice = c->p.lattice;
+    h.nx = c->p.nx;
+    h.ny = c->p.ny;
+    h.nz = c->p.nz;
+    h.scheme = c->p.scheme;
+    h.storage = c->p.storage;
+    h.aos = c->aos ? 1 : 0;
+    h.step = c->step;
+    h.params_hash = params_hash(&c->p);
+    h.payload_bytes = c->buf_bytes;
+    std::memcpy(buf, &h, sizeof(h));
+    cudaError_t e = cudaMemcpyAsync(static_cast<char*>(buf) + sizeof(h), c->fbuf + size_t(c->cur) * c->buf_bytes,
+                                    c->buf_bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return record(c, e, "state export");
+    *bytes = need;
+    return LB_OK;
+}
+
+lb_status lb_set_state(lb_ctx* c, const void* buf, size_t bytes) {
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!buf) return fail(LB_EINVAL, "null state");
+    if (bytes < sizeof(StateHeader)) return fail(LB_EINVAL, "state shorter than its header");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, STATE_MAGIC, 8) != 0 || h.version != 1 || h.header_bytes != sizeof(StateHeader))
+        return fail(LB_EINVAL, "not a state exported by lb_get_state (magic, version or header size)");
+    if (h.lattice != c->p.lattice || h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz ||
+        h.scheme != c->p.scheme || h.storage != c->p.storage || h.aos != (c->aos ? 1 : 0))
+        return fail(LB_EINVAL, "state of another lattice, scheme, storage or layout");
+    if (h.params_hash != params_hash(&c->p))
+        return fail(LB_EINVAL, "state exported with other physical parameters (parameter hash differs)");
+    if (h.payload_bytes != c->buf_bytes || bytes != sizeof(StateHeader) + c->buf_bytes)
+        return fail(LB_EINVAL, "state size does not match the context");
+    if (h.step < 0) return fail(LB_EINVAL, "negative step counter");
+    cudaError_t e = cudaMemcpyAsync(c->fbuf + size_t(c->cur) * c->buf_bytes, static_cast<const char*>(buf) + sizeof(h),
+                                    c->buf_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return record(c, e, "state import");
+    c->initialised = true;
+    c->step = h.step;
+    c->uprev_valid = false;
+    return sync_status(c);
 }
 
 }  // extern "C"

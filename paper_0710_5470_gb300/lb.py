@@ -45,7 +45,8 @@ class lb_params(C.Structure):
 class lb_stats(C.Structure):
     _fields_ = [("mass", C.c_double), ("momentum", C.c_double * 3), ("max_u", C.c_double),
                 ("max_v", C.c_double), ("min_rho", C.c_double), ("max_rho", C.c_double),
-                ("step", C.c_longlong), ("status", C.c_int)]
+                ("step", C.c_longlong), ("status", C.c_int), ("dP", C.c_double), ("max_du", C.c_double),
+                ("du_steps", C.c_longlong)]
 
 
 class lb_instance(C.Structure):
@@ -74,6 +75,11 @@ _SIGNATURES = {
     "lb_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "lb_set_free_params": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lb_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    "lb_set_probes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lb_get_probes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lb_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lb_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lb_params_hash": (C.c_int, [C.POINTER(lb_params), C.POINTER(C.c_ulonglong)]),
     "lb_kernel_info": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "lb_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(lb_instance),
@@ -87,6 +93,7 @@ _SIGNATURES = {
                                          C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "lb_batch_set_reference": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double]),
     "lb_batch_set_band": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int]),
+    "lb_batch_set_self_test": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int]),
     "lb_batch_last_check": (C.c_int, [C.c_void_p, _DPTR, _DPTR, _DPTR, _DPTR]),
     "lb_batch_fields": (C.c_int, [C.c_void_p, C.c_int, _DPTR, _DPTR]),
     "lb_batch_populations": (C.c_int, [C.c_void_p, C.c_int, _DPTR]),
@@ -196,6 +203,16 @@ def fma_peak(precision: int, iters: int | None = None) -> float:
     out = C.c_double()
     _check(load_library().lb_fma_peak(int(precision), int(iters), C.byref(out)))
     return out.value
+
+
+def params_hash(lattice: int, shape, a: float, b: float, T: float, kappa: float, tau: float,
+                scheme: int = EQUILIBRIUM, storage: int = F64, rho_ref: float = 0.0) -> int:
+    """lb_params_hash (host only)."""
+    nx, ny, nz = (tuple(shape) + (1,))[:3] if len(shape) == 2 else tuple(shape)
+    p = lb_params(lattice, nx, ny, nz, a, b, T, kappa, tau, scheme, storage, rho_ref)
+    h = C.c_ulonglong()
+    _check(load_library().lb_params_hash(C.byref(p), C.byref(h)))
+    return h.value
 
 
 def version() -> str:
@@ -310,7 +327,32 @@ class Context:
         s = lb_stats()
         _check(self._lib.lb_stats_get(self._h, C.byref(s)))
         return {"mass": s.mass, "momentum": list(s.momentum)[: self.dim], "max_u": s.max_u, "max_v": s.max_v,
-                "min_rho": s.min_rho, "max_rho": s.max_rho, "step": s.step, "status": s.status}
+                "min_rho": s.min_rho, "max_rho": s.max_rho, "step": s.step, "status": s.status, "dP": s.dP,
+                "max_du": s.max_du, "du_steps": s.du_steps}
+
+    def set_probes(self, inside, outside):
+        """lb_set_probes: (x, y[, z]) sites of the dP probes."""
+        i = (C.c_int * 3)(*((tuple(int(v) for v in inside) + (0,))[:3]))
+        o = (C.c_int * 3)(*((tuple(int(v) for v in outside) + (0,))[:3]))
+        _check(self._lib.lb_set_probes(self._h, i, o))
+
+    def probes(self):
+        i, o = (C.c_int * 3)(), (C.c_int * 3)()
+        _check(self._lib.lb_get_probes(self._h, i, o))
+        return tuple(i), tuple(o)
+
+    def get_state(self) -> bytes:
+        """lb_get_state: header + raw population buffer."""
+        n = C.c_size_t()
+        _check(self._lib.lb_get_state(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(self._lib.lb_get_state(self._h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def set_state(self, state: bytes):
+        """lb_set_state: import a state exported by a context with the same parameters."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(self._lib.lb_set_state(self._h, buf, len(state)))
 
     def kernel_info(self) -> dict:
         """lb_kernel_info: launch form of the fused step kernel."""
@@ -389,6 +431,11 @@ class Batch:
 
     def set_band(self, band: float = 0.05, tol_rho: float = 1e-3, hold: int = 10):
         _check(self._lib.lb_batch_set_band(self._h, band, tol_rho, hold))
+
+    def set_self_test(self, rtol_u: float = 1e-3, tol_rho: float = 1e-5, hold: int = 10):
+        """lb_batch_set_self_test: steady once max|u| and the bulk densities settle
+        (no reference values); rtol_u = 0 switches it off."""
+        _check(self._lib.lb_batch_set_self_test(self._h, float(rtol_u), float(tol_rho), int(hold)))
 
     def last_check(self):
         """(max|du|, max|u|, max rho, min rho) per instance at its last check."""

@@ -75,8 +75,18 @@ def plain(instances, tol=1e-10, every=100, max_steps=200000, scheme=lb.FORCING, 
             "umax": umax, "rho_max": rmax, "rho_min": rmin, "final": final}
 
 
+# Self-contained steady-state test per storage format (lb_batch_set_self_test):
+# (rtol of max|u|, tol of the bulk densities, consecutive checks), each per
+# check of 100 steps.  Set above the late-time check-to-check changes measured
+# on the first 16 sweep instances (forcing scheme, ~3e4 steps; GB300): max|u|
+# float64 1.7e-5, float32 1.8e-4, fp16 deviations 1.4e-4, bf16 deviations
+# ~1e-3; bulk densities 1e-6 (float32, fp16) to 1.5e-5 (bf16).
+SELF_TEST = {"f64": (5e-4, 1e-5, 10), "f32": (5e-4, 1e-5, 10), "f16dev": (5e-4, 1e-5, 10),
+             "bf16dev": (3e-3, 5e-5, 10)}
+
+
 def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, scheme=lb.FORCING, ws=None,
-         refs=None, band=0.05, tol_rho=1e-3, hold=10, autotune_steps=5, stream=None):
+         refs=None, band=0.05, tol_rho=1e-3, hold=10, autotune_steps=5, stream=None, self_test=None):
     """All instances in one batch with the given storage, tanh start or the
     network's prediction (ws); reference test when refs is given.  Same
     return layout as ``plain`` plus the time of the warm-start prediction.
@@ -88,6 +98,8 @@ def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, sche
     with lb.Batch(instances, W.A_VDW, W.B_VDW, scheme=scheme, storage=storage, stream=stream) as bt:
         if refs is not None:
             _set_refs(bt, refs, band, tol_rho, hold)
+        if self_test is not None:
+            bt.set_self_test(*self_test)
         bt.init_drops(2.0)
         t_pred = 0.0
         if ws is not None:
@@ -111,6 +123,8 @@ def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, sche
                       stream=stream) as bt:
             if sub_refs is not None:
                 _set_refs(bt, sub_refs, band, tol_rho, hold)
+            if self_test is not None:
+                bt.set_self_test(*self_test)
             bt.init_drops(2.0)
             s2, st2, total2 = bt.run_to_steady(tol=tol, every=every, max_steps=max_steps)
             seconds += time.perf_counter() - t1
@@ -227,6 +241,30 @@ def experiment(count=16, seed=0, every=100, max_steps=200000, band=0.05, tol_rho
     return out
 
 
+def experiment_self(count=16, seed=0, every=100, max_steps=200000, arms=("f16dev", "f32", "bf16dev")):
+    """Time to steady state with no reference values: plain float64 (one
+    instance per batch, tanh start) to max|u(t) - u(t - every)| < 1e-10,
+    against one batch per reduced format stopped by the format's own
+    self-contained test (SELF_TEST, lb_batch_set_self_test).  Accuracy of the
+    fast steady states afterwards against the float64 ones (compare), on the
+    instances converged in both."""
+    from . import inputs
+    inst = W.instances_from_sweep(inputs.sweep_instances(seed=seed, count=count))
+    ref = plain(inst, tol=1e-10, every=every, max_steps=max_steps)
+    out = {"sweep": {"seed": seed, "count": count, "sites": int(sum(d["nx"] * d["ny"] for d in inst))},
+           "test": {"tol_f64": 1e-10, "every": every, "self": {a: SELF_TEST[a] for a in arms}},
+           "plain_f64_tol": _summary("plain_f64_tol", ref)}
+    for a in arms:
+        r = fast(inst, storage=ARMS[a], every=every, max_steps=max_steps, self_test=SELF_TEST[a])
+        summ = _summary("batch_" + a, r, ref)
+        summ["speedup_vs_plain_f64_tol"] = ref["seconds"] / r["seconds"]
+        c = [x for x in compare(ref, r) if x]
+        summ["within_5pct"] = sum(x["max_u_rel_err"] <= 0.05 for x in c)
+        summ["compared"] = len(c)
+        out["batch_" + a + "_self"] = summ
+    return out
+
+
 def _sweep_summary(res, sites):
     """Wall time, lattice updates done (sum over instances of the steps it ran
     x its sites; the whole batch for an instance stopped by the cap) and their
@@ -306,6 +344,8 @@ def main():
     p.add_argument("--max-steps", type=int, default=200000)
     p.add_argument("--tol-rho", type=float, default=1e-3)
     p.add_argument("--warm", action="store_true")
+    p.add_argument("--self-test", action="store_true",
+                   help="no reference values: reduced formats stopped by their own test (experiment_self())")
     p.add_argument("--sweep", action="store_true",
                    help="the whole sweep (default 256 instances), one batch per way (sweep())")
     p.add_argument("--throughput", action="store_true",
@@ -321,6 +361,9 @@ def main():
         return
     if a.sweep:
         print(json.dumps(sweep(a.count or 256, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho)), flush=True)
+        return
+    if a.self_test:
+        print(json.dumps(experiment_self(a.count or 16, a.seed, a.every, a.max_steps)), flush=True)
         return
     print(json.dumps(experiment(a.count or 16, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho, warm=a.warm)), flush=True)
 

@@ -84,3 +84,24 @@ def test_fma_peak_arguments_rejected_before_device_work():
         with pytest.raises(lb.LBError) as e:
             lb.fma_peak(*args)
         assert e.value.status == 1
+
+
+def test_params_hash_is_stable_and_sensitive():
+    """lb_params_hash (host only): equal parameters give equal hashes; a change
+    of any one parameter (lattice size, scheme, storage, a, b, T, kappa, tau,
+    rho_ref) changes it; an invalid parameter set is rejected."""
+    lb = library()
+    base = dict(lattice=lb.D3Q19, shape=(16, 12, 8), a=A_VDW, b=B_VDW, T=0.55, kappa=0.01, tau=1.0,
+                scheme=lb.FORCING, storage=lb.F16DEV, rho_ref=0.0)
+    h0 = lb.params_hash(**base)
+    assert h0 == lb.params_hash(**base)
+    changes = [dict(shape=(16, 12, 9)), dict(shape=(18, 12, 8)), dict(scheme=lb.EQUILIBRIUM),
+               dict(storage=lb.BF16DEV), dict(a=A_VDW * (1 + 1e-15)), dict(T=0.55 + 1e-12), dict(kappa=0.0101),
+               dict(tau=0.9), dict(rho_ref=4.0), dict(lattice=lb.D2Q9, shape=(16, 12))]
+    seen = {h0}
+    for ch in changes:
+        h = lb.params_hash(**dict(base, **ch))
+        assert h not in seen, ch
+        seen.add(h)
+    with pytest.raises(lb.LBError):
+        lb.params_hash(**dict(base, tau=0.4))
