@@ -81,6 +81,8 @@ def plain(instances, tol=1e-10, every=100, max_steps=200000, scheme=lb.FORCING, 
 # on the first 16 sweep instances (forcing scheme, ~3e4 steps; GB300): max|u|
 # float64 1.7e-5, float32 1.8e-4, fp16 deviations 1.4e-4, bf16 deviations
 # ~1e-3; bulk densities 1e-6 (float32, fp16) to 1.5e-5 (bf16).
+DRIFT_LIMIT = W.DRIFT_LIMIT
+
 SELF_TEST = {"f64": (5e-4, 1e-5, 10), "f32": (5e-4, 1e-5, 10), "f16dev": (5e-4, 1e-5, 10),
              "bf16dev": (3e-3, 5e-5, 10)}
 
@@ -116,6 +118,16 @@ def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, sche
         final = [bt.fields(k) for k in range(len(instances))]
     s, st, um, hi, lo = list(s), list(st), list(um), list(hi), list(lo)
     failed = [k for k, v in enumerate(st) if v != 0] if ws is not None else []
+    # a predicted start can set the drop moving (the translation mode of the
+    # periodic lattice) or turn it into a stripe across the box (another steady
+    # state): such runs (warmstart.left_its_start) are not trusted and run
+    # again from the tanh start
+    drifted = []
+    if ws is not None:
+        for k, d in enumerate(instances):
+            if st[k] == 0 and W.left_its_start(final[k][0], d):
+                drifted.append(k)
+        failed = sorted(set(failed) | set(drifted))
     if failed:
         t1 = time.perf_counter()
         sub_refs = [refs[k] for k in failed] if refs is not None else None
@@ -136,7 +148,7 @@ def fast(instances, storage=lb.F32, tol=1e-10, every=100, max_steps=200000, sche
         total += total2
     return {"seconds": seconds, "steps": s, "status": st, "umax": [float(v) for v in um],
             "rho_max": [float(v) for v in hi], "rho_min": [float(v) for v in lo], "final": final,
-            "predict_seconds": t_pred, "batch_steps": total, "fallback": len(failed)}
+            "predict_seconds": t_pred, "batch_steps": total, "fallback": len(failed), "drifted": len(drifted)}
 
 
 def _centre(rho):
