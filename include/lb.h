@@ -202,6 +202,20 @@ lb_status lb_get_probes(const lb_ctx* ctx, int* inside, int* outside);
 lb_status lb_get_state(lb_ctx* ctx, void* buf, size_t* bytes);
 lb_status lb_set_state(lb_ctx* ctx, const void* buf, size_t bytes);
 
+/* ---- Index checks (no counterpart in the paper) ---------------------------
+ *
+ * A library built with -DLB_DEBUG_BOUNDS (paper_0710_5470_gb300.build,
+ * debug=True: _build_debug/liblb_debug.so) tests the site index of every
+ * global population access of the fused step kernels against the lattice
+ * before making it; an out-of-range access is skipped and the first one is
+ * recorded (no trap).  lb_debug_bounds returns whether this library has the
+ * checks (*checked = 1) and the first recorded violation since the last call
+ * (*violation: 0 if none, else bit 63 set, the kind of access in bits 48..55 -
+ * 1/2/3 pair-kernel load/store/shared write, 4/5 D3Q19 tile load/store, 6/7
+ * D2Q9 load/store - and the site index in bits 0..47), then clears it.
+ * Synchronises the device.  Either pointer may be NULL. */
+lb_status lb_debug_bounds(int* checked, unsigned long long* violation);
+
 /* 64-bit FNV-1a hash of the parameters that define a run (lattice, sizes,
  * scheme, storage, a, b, T, kappa, tau, rho_ref); host only.  LB_EINVAL for
  * an invalid parameter set (the checks of lb_create). */

@@ -615,3 +615,6 @@ lb_status lb_batch_info(const lb_batch* B, int* tile_x, int* tile_y, long long* 
 }
 
 }  // extern "C"
+
+// First recorded index violation of this unit's kernels (checked builds; see bounds.cuh).
+LB_BOUNDS_READER(lbk_bounds_batch)

@@ -17,3 +17,6 @@ static LbKernelSet pick(int storage) {
 LbKernelSet lbk_kernels_d2q9(int scheme, int storage) {
     return scheme == 1 ? pick<true>(storage) : pick<false>(storage);
 }
+
+// First recorded index violation of this unit's kernels (checked builds; see bounds.cuh).
+LB_BOUNDS_READER(lbk_bounds_d2q9)

@@ -21,3 +21,6 @@ LbKernelSet lbk_kernels_d3q19(int scheme, int storage, int nx) {
     LbKernelSet k = pick<true>(storage);
     return storage == 0 ? k : lbk_pk_forcing(storage, nx, k);
 }
+
+// First recorded index violation of this unit's kernels (checked builds; see bounds.cuh).
+LB_BOUNDS_READER(lbk_bounds_d3q19)

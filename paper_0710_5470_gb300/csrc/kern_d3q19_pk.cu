@@ -83,3 +83,6 @@ LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet k) {
     }
     return k;
 }
+
+// First recorded index violation of this unit's kernels (checked builds; see bounds.cuh).
+LB_BOUNDS_READER(lbk_bounds_d3pk)

@@ -433,6 +433,12 @@ constexpr char STATE_MAGIC[8] = {'L', 'B', 'G', 'B', 'S', 'T', 'A', '1'};
 
 }  // namespace
 
+// first recorded index violation of each kernel translation unit (bounds.cuh)
+unsigned long long lbk_bounds_d3q19();
+unsigned long long lbk_bounds_d3pk();
+unsigned long long lbk_bounds_d2q9();
+unsigned long long lbk_bounds_batch();
+
 extern "C" {
 
 const char* lb_version(void) { return "lbgb 0.1 (sm_103a)"; }
@@ -919,6 +925,15 @@ lb_status lb_get_probes(const lb_ctx* c, int* inside, int* outside) {
         inside[a] = c->probe_in[a];
         outside[a] = c->probe_out[a];
     }
+    return LB_OK;
+}
+
+lb_status lb_debug_bounds(int* checked, unsigned long long* violation) {
+    if (checked) *checked = lbk::kBoundsChecked ? 1 : 0;
+    unsigned long long v = 0;
+    for (unsigned long long w : {lbk_bounds_d3pk(), lbk_bounds_d3q19(), lbk_bounds_d2q9(), lbk_bounds_batch()})
+        if (!v) v = w;
+    if (violation) *violation = v;
     return LB_OK;
 }
 

@@ -21,6 +21,7 @@
 #pragma once
 #include <type_traits>
 
+#include "bounds.cuh"
 #include "step_kernel.cuh"
 
 namespace lbk {
@@ -247,6 +248,8 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
         for (int m = 0; m < NA; ++m) {
             if (a_in[m] >= 0) {
                 const size_t q = size_t(ld_off + a_in[m]);
+                LB_GUARD(q + (PAIR ? 1 : 0) < size_t(vol), BK_3D_LOAD, q, r0[m] = R0{};
+                         for (int i = 0; i < Q - 1; ++i) ri[m][i] = RI{}; continue)
                 if constexpr (PAIR) r0[m] = S::ld0x2(args.src[0], q);
                 else r0[m] = S::ld0(args.src[0], q);
                 static_for<1, Q>([&](auto I) {
@@ -461,6 +464,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(typename S::real) == 4 && TX *
             static_for<0, Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 const int idx = zr[1 + L::ez(i)] + yr[1 + L::ey(i)] + xw[1 + L::ex(i)];
+                LB_GUARD(idx >= 0 && idx < vol, BK_3D_STORE, idx, return)
                 if constexpr (i == 0) S::st0(args.dst[0], size_t(idx), out[0]);
                 else S::sti(args.dst[i], size_t(idx), out[i]);
             });

@@ -23,6 +23,7 @@
 // Two barriers per plane: after stage A (densities of the plane visible) and
 // after stage B (M' of the plane visible).
 #pragma once
+#include "bounds.cuh"
 #include "step3d.cuh"
 
 namespace lbk {
@@ -362,6 +363,9 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
     const int4 wk = args.work[blockIdx.x];
     const int x0 = wk.x, y0 = wk.y, z0 = wk.z, z1 = wk.w;
     const int plane = nx * ny;
+#ifdef LB_DEBUG_BOUNDS
+    const size_t nsites = size_t(plane) * nz;   // sites of the lattice
+#endif
     const PairPhys ph{args.fa, args.fb, args.fT, args.fkappa, args.fomega, args.fnu, args.pref, args.rsum};
     const float pk = args.fkappa;
 
@@ -448,6 +452,8 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
         for (int m = 0; m < 1 + NAH; ++m) {
             if (m >= mb && m < me && (m == 0 || a_rs[m] >= 0)) {
                 const unsigned q = unsigned(ld_off) + a_in[m];
+                LB_GUARD(size_t(q) + 1 < nsites, BK_PK_LOAD, q, r0[m] = make_float2(0.f, 0.f);
+                         for (int i = 0; i < 18; ++i) ri[m][i] = Wd{}; continue)
                 r0[m] = reinterpret_cast<const float2*>(args.src[0])[q >> 1];
                 if constexpr (AOS) {
                     const char* b = args.src[1] + (size_t(unsigned(ld_off)) / AOS_SITES) * (2 * AOS_BLOCK_HALVES) + a_h[m];
@@ -486,6 +492,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
             for (int m = 0; m < 1 + NAH; ++m) {
                 if (m == 0 || a_rs[m] >= 0) {
                     const P2 r = pair_rho<S, MIXED>(r0[m], ri[m], ph.rsum);
+                    LB_GUARD(a_rs[m] >= 0 && a_rs[m] + 1 < Lay::RN, BK_PK_SHARED, a_rs[m], continue)
                     *reinterpret_cast<float2*>(rho_w + a_rs[m]) = r.v;
                     if (m == 0) {
                         // thread-private stash of the own pair: raw populations and (rho, j)
@@ -530,6 +537,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
                     finish(acc[m], cur, G, lap);
                     const float g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
                     const float hk = 0.5f * pk * g2;
+                    LB_GUARD(b_mp[m] >= 0 && b_mp[m] < Lay::SN, BK_PK_SHARED, b_mp[m], continue)
                     mpA[b_mp[m]] = make_float4(pk * G[0] * G[0] - hk, pk * G[0] * G[1], pk * G[0] * G[2],
                                                pk * G[1] * G[1] - hk);
                     mpB[b_mp[m]] = make_float2(pk * G[1] * G[2], pk * G[2] * G[2] - hk);
@@ -655,6 +663,14 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
                 auto store = [&](auto I, P2 v) {
                     constexpr int i = decltype(I)::value;
                     constexpr int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+#ifdef LB_DEBUG_BOUNDS
+                    {
+                        const size_t row0 = size_t(unsigned(zr[1 + ez])) + yr[1 + ey];
+                        const size_t xa = ex == 0 ? xc : (ex == 1 ? xc + 1 : xm1);
+                        const size_t xb = ex == 0 ? xc + 1 : (ex == 1 ? xp2 : xc);
+                        LB_GUARD(row0 + xa < nsites && row0 + xb < nsites, BK_PK_STORE, row0 + xa, return)
+                    }
+#endif
                     if constexpr (AOS) {
                         char* b = args.dst[1] + zb[1 + ez] + yb[1 + ey] + (i - 1) * ROWB;
                         if constexpr (ex == 0) {
@@ -680,7 +696,11 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
                     }
                 };
                 const P2 o0 = fma(K.omw, P2{f0}, K.c0);
-                reinterpret_cast<float2*>(args.dst[0])[(unsigned(zr[1]) + yr[1] + xc) >> 1] = o0.v;
+#ifdef LB_DEBUG_BOUNDS
+                const size_t q0 = size_t(unsigned(zr[1])) + yr[1] + xc;
+                if (lbk::in_bounds(q0 + 1 < nsites, BK_PK_STORE, q0))
+#endif
+                    reinterpret_cast<float2*>(args.dst[0])[(unsigned(zr[1]) + yr[1] + xc) >> 1] = o0.v;
                 static_for<1, 19>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr int o = opposite<L>(i);

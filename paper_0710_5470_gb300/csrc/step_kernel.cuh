@@ -28,6 +28,7 @@
 #pragma once
 #include "lattice.cuh"
 #include "storage.cuh"
+#include "bounds.cuh"
 
 namespace lbk {
 
@@ -425,6 +426,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
                 const int rx = (k % (RX / 2)) * 2, ry = k / (RX / 2);
                 const size_t q = size_t(wrap_near(y0 - HY + ry, ny)) * nx + wrap_near(x0 - HX + rx, nx);
                 pair_t<real> f2[Q];
+                LB_GUARD(q + 1 < size_t(nx) * ny, BK_2D_LOAD, q, continue)
                 S::dec0x2(S::ld0x2(args.src, q), f2[0].x, f2[0].y);
                 static_for<1, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
@@ -449,6 +451,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
                 const int rx = k % RX, ry = k / RX;
                 const size_t q = size_t(wrap_near(y0 - HY + ry, ny)) * nx + wrap_near(x0 - HX + rx, nx);
                 real f[Q];
+                LB_GUARD(q < size_t(nx) * ny, BK_2D_LOAD, q, continue)
                 f[0] = S::dec0(S::ld0(args.src, q));
                 static_for<1, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
@@ -553,6 +556,7 @@ __device__ __forceinline__ void step2d_tile(const Tile2DArgs& args, int x0, int 
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             const size_t idx = size_t(yr[1 + L::ey(i)] + xw[1 + L::ex(i)]);
+            LB_GUARD(idx < size_t(nx) * ny, BK_2D_STORE, idx, return)
             if constexpr (i == 0) S::st0(args.dst, idx, out[0]);
             else S::sti(args.dst + S::pop_offset(i, pitch), idx, out[i]);
         });

@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "liblb.so")
+# LB_LIBRARY selects another build of the library (e.g. the index-checked one)
+LIB_PATH = os.environ.get("LB_LIBRARY") or os.path.join(_HERE, "_build", "liblb.so")
 
 D2Q9, D3Q19 = 0, 1
 EQUILIBRIUM, FORCING = 0, 1
@@ -79,6 +80,7 @@ _SIGNATURES = {
     "lb_get_probes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lb_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "lb_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lb_debug_bounds": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)]),
     "lb_params_hash": (C.c_int, [C.POINTER(lb_params), C.POINTER(C.c_ulonglong)]),
     "lb_kernel_info": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
@@ -213,6 +215,13 @@ def params_hash(lattice: int, shape, a: float, b: float, T: float, kappa: float,
     h = C.c_ulonglong()
     _check(load_library().lb_params_hash(C.byref(p), C.byref(h)))
     return h.value
+
+
+def debug_bounds():
+    """lb_debug_bounds: (index checks compiled in, first recorded violation or 0)."""
+    c, v = C.c_int(), C.c_ulonglong()
+    _check(load_library().lb_debug_bounds(C.byref(c), C.byref(v)))
+    return bool(c.value), v.value
 
 
 def version() -> str:
