@@ -40,6 +40,10 @@ KERNEL_SOURCES = ["step3d.cuh", "step3d_pk.cuh", "kern_d3q19_pk.cu", "step_kerne
 # fingerprint of the kernel sources they were measured on and the storage.
 # A changed kernel has a new fingerprint and reports traffic = null.
 NCU_TRAFFIC = {
+    ("8e569adda85f", "f16dev", 128): 145.05e6,   # 103.54 MB read + 41.51 MB written (pair kernel)
+    ("8e569adda85f", "bf16dev", 128): 145.04e6,  # 103.56 MB read + 41.49 MB written (pair kernel)
+    ("8e569adda85f", "f32", 128): 306.61e6,      # 191.43 MB read + 115.18 MB written (tile kernel)
+    ("8e569adda85f", "f64", 128): 638.11e6,      # 357.11 MB read + 281.01 MB written (tile kernel)
     ("0a56c3ba8029", "f16dev", 128): 137.92e6,   # 97.35 MB read + 40.57 MB written
     ("0a56c3ba8029", "f32", 128): 306.32e6,      # 191.48 MB read + 114.84 MB written
     ("0a56c3ba8029", "bf16dev", 128): 135.55e6,  # 97.01 MB read + 38.54 MB written
@@ -48,10 +52,13 @@ NCU_TRAFFIC = {
 
 # Executed floating-point operations per lattice update of the step kernel,
 # from ncu's per-opcode instruction counts of one launch divided by the sites
-# (FFMA, DFMA, FADD2 = 2 flops; FADD, FMUL, DADD, DMUL = 1), keyed like
+# (FFMA, DFMA, FADD2, FMUL2 = 2 flops, FFMA2 = 4; FADD, FMUL, FHADD, DADD,
+# DMUL = 1), keyed like
 # NCU_TRAFFIC.  They include the halo recomputation, so they are the work the
 # FP units do, not an algorithmic minimum.
 NCU_FLOPS = {
+    # pair kernel: FFMA 22.7, FADD 80.1, FMUL 27.2, FADD2 41.0, FFMA2 38.0, FMUL2 26.8, FHADD 38.5 per site
+    ("8e569adda85f", "f16dev", 128): 478.8,
     ("0a56c3ba8029", "f16dev", 128): 484.1,   # FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1 per site
     ("0a56c3ba8029", "f32", 128): 484.1,      # the same counts
     ("0a56c3ba8029", "f64", 128): 525.6,      # DFMA 129.0, DADD 197.4, DMUL 70.2 per site

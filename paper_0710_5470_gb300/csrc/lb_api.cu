@@ -201,7 +201,8 @@ lb_status record(lb_ctx* c, cudaError_t e, const char* where) {
 // resident slots: each tile gets slots / tiles chunks, the remainder one more (no
 // chunk under 4 planes).  Otherwise every tile gets the same number c of chunks:
 // the smallest c whose estimated efficiency (W / ceil(W)) * L / (L + 4) is within
-// 0.02 of the best, W = CTAs per SM, L = chunk length, 4 the halo planes a chunk
+// 0.02 of the best, W = waves of resident CTAs per SM (CTAs per SM / resident
+// CTAs per SM), L = chunk length, 4 the halo planes a chunk
 // loads in addition (measured on GB300: 224^3 c = 3, 256^3 c = 4, 320^3 c = 3 are
 // 13-17% faster than one chunk per tile).  CTAs are listed longest chunk first so
 // that the first wave puts one long CTA on every SM and the second wave pairs it
@@ -218,7 +219,8 @@ std::vector<int4> build_work_list(long long sms, long long occ, int nx, int ny, 
     if (2 * tiles > slots) {
         const long long cmax = std::max(1, nz / 16);
         auto eff = [&](long long cc) {
-            const double W = double(cc * tiles) / double(sms), L = double(nz) / double(cc);
+            // waves of `occ` resident CTAs per SM, the last one partly filled
+            const double W = double(cc * tiles) / double(sms * occ), L = double(nz) / double(cc);
             return W / std::ceil(W) * L / (L + 4.0);
         };
         double best = 0.0;

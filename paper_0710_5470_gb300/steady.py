@@ -28,6 +28,7 @@ the calls and reads the clock.
 
   python -m paper_0710_5470_gb300.steady [--count 16] [--warm]   (one JSON line)
   python -m paper_0710_5470_gb300.steady --sweep [--count 256]   (the whole sweep, batched ways only)
+  python -m paper_0710_5470_gb300.steady --self-test [--sweep]   (no reference values: self-contained test)
   python -m paper_0710_5470_gb300.steady --throughput [--storage f16dev] [--steps 200]   (batched step rate)
 """
 from __future__ import annotations
@@ -323,6 +324,34 @@ def sweep(count=256, seed=0, every=100, max_steps=200000, band=0.05, tol_rho=1e-
     return out
 
 
+def sweep_self(count=256, seed=0, every=100, max_steps=200000, arms=("f16dev", "f32")):
+    """The whole sweep without reference values: one float64 batch to
+    max|u(t) - u(t - every)| < 1e-10 (the plain test), then one batch per
+    reduced format stopped by its self-contained test (SELF_TEST); per way the
+    wall time, lattice updates and retirement counts, and for the reduced
+    formats the accuracy of their steady states against the float64 ones on
+    the instances converged in both (max|u| within 5%: how many)."""
+    from . import inputs
+    inst = W.instances_from_sweep(inputs.sweep_instances(seed=seed, count=count))
+    sites = [d["nx"] * d["ny"] for d in inst]
+    f64 = fast(inst, storage=lb.F64, tol=1e-10, every=every, max_steps=max_steps)
+    out = {"sweep": {"seed": seed, "count": count, "sites": int(sum(sites)), "every": every,
+                     "max_steps": max_steps},
+           "test": {"tol_f64": 1e-10, "self": {a: SELF_TEST[a] for a in arms}},
+           "batch_f64_tol": _sweep_summary(f64, sites)}
+    for a in arms:
+        r = fast(inst, storage=ARMS[a], every=every, max_steps=max_steps, self_test=SELF_TEST[a])
+        summ = _sweep_summary(r, sites)
+        c = [x for x in compare(f64, r) if x]
+        summ["compared"] = len(c)
+        summ["within_5pct"] = sum(x["max_u_rel_err"] <= 0.05 for x in c)
+        for key in ("max_u_rel_err", "rho_max_err", "rho_min_err"):
+            summ[key + "_max"] = max(x[key] for x in c) if c else None
+        summ["speedup_vs_f64_tol"] = f64["seconds"] / r["seconds"]
+        out["batch_" + a + "_self"] = summ
+    return out
+
+
 def throughput(storage=lb.F16DEV, steps=200, count=256, seed=0, scheme=lb.FORCING, autotune_steps=5):
     """Batched step rate on the lattice sizes of the sweep
     (inputs.sweep_instances(seed, count)) at parameters where every instance
@@ -370,6 +399,9 @@ def main():
     lb.load_library()
     if a.throughput:
         print(json.dumps(throughput(ARMS[a.storage], a.steps, a.count or 256, a.seed)), flush=True)
+        return
+    if a.sweep and a.self_test:
+        print(json.dumps(sweep_self(a.count or 256, a.seed, a.every, a.max_steps)), flush=True)
         return
     if a.sweep:
         print(json.dumps(sweep(a.count or 256, a.seed, a.every, a.max_steps, tol_rho=a.tol_rho)), flush=True)
