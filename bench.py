@@ -59,6 +59,8 @@ NCU_TRAFFIC = {
 NCU_FLOPS = {
     # pair kernel: FFMA 22.7, FADD 80.1, FMUL 27.2, FADD2 41.0, FFMA2 38.0, FMUL2 26.8, FHADD 38.5 per site
     ("8e569adda85f", "f16dev", 128): 478.8,
+    ("8e569adda85f", "f32", 128): 484.2,       # tile kernel: FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1
+    ("8e569adda85f", "f64", 128): 525.6,       # tile kernel: DFMA 129.0, DADD 197.4, DMUL 70.2
     ("0a56c3ba8029", "f16dev", 128): 484.1,   # FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1 per site
     ("0a56c3ba8029", "f32", 128): 484.1,      # the same counts
     ("0a56c3ba8029", "f64", 128): 525.6,      # DFMA 129.0, DADD 197.4, DMUL 70.2 per site
@@ -66,7 +68,7 @@ NCU_FLOPS = {
 # FP64-pipe instructions per lattice update of the float64 step (DFMA, DADD,
 # DMUL, DSETP, F2F): each occupies the pipe like one FMA, so their rate against
 # half the FMA flop rate is the pipe's utilisation.
-NCU_FP64_PIPE_OPS = {("0a56c3ba8029", "f64", 128): 401.7}
+NCU_FP64_PIPE_OPS = {("0a56c3ba8029", "f64", 128): 401.7, ("8e569adda85f", "f64", 128): 401.7}
 
 
 def alu_roofline(fp: str, storage: str, n: int, glups: float, fma: dict | None):
