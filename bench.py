@@ -40,14 +40,10 @@ KERNEL_SOURCES = ["step3d.cuh", "step3d_pk.cuh", "kern_d3q19_pk.cu", "step_kerne
 # fingerprint of the kernel sources they were measured on and the storage.
 # A changed kernel has a new fingerprint and reports traffic = null.
 NCU_TRAFFIC = {
-    ("8e569adda85f", "f16dev", 128): 145.05e6,   # 103.54 MB read + 41.51 MB written (pair kernel)
-    ("8e569adda85f", "bf16dev", 128): 145.04e6,  # 103.56 MB read + 41.49 MB written (pair kernel)
-    ("8e569adda85f", "f32", 128): 306.61e6,      # 191.43 MB read + 115.18 MB written (tile kernel)
-    ("8e569adda85f", "f64", 128): 638.11e6,      # 357.11 MB read + 281.01 MB written (tile kernel)
-    ("0a56c3ba8029", "f16dev", 128): 137.92e6,   # 97.35 MB read + 40.57 MB written
-    ("0a56c3ba8029", "f32", 128): 306.32e6,      # 191.48 MB read + 114.84 MB written
-    ("0a56c3ba8029", "bf16dev", 128): 135.55e6,  # 97.01 MB read + 38.54 MB written
-    ("0a56c3ba8029", "f64", 128): 637.08e6,      # 357.15 MB read + 279.94 MB written
+    ("2b86a63b5b5f", "f16dev", 128): 143.34e6,   # 103.33 MB read + 40.01 MB written (pair kernel)
+    ("2b86a63b5b5f", "bf16dev", 128): 143.34e6,  # 103.31 MB read + 40.03 MB written (pair kernel)
+    ("2b86a63b5b5f", "f32", 128): 303.37e6,      # 190.54 MB read + 112.83 MB written (tile kernel)
+    ("2b86a63b5b5f", "f64", 128): 637.07e6,      # 357.14 MB read + 279.93 MB written (tile kernel)
 }
 
 # Executed floating-point operations per lattice update of the step kernel,
@@ -57,18 +53,15 @@ NCU_TRAFFIC = {
 # NCU_TRAFFIC.  They include the halo recomputation, so they are the work the
 # FP units do, not an algorithmic minimum.
 NCU_FLOPS = {
-    # pair kernel: FFMA 22.7, FADD 80.1, FMUL 27.2, FADD2 41.0, FFMA2 38.0, FMUL2 26.8, FHADD 38.5 per site
-    ("8e569adda85f", "f16dev", 128): 478.8,
-    ("8e569adda85f", "f32", 128): 484.2,       # tile kernel: FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1
-    ("8e569adda85f", "f64", 128): 525.6,       # tile kernel: DFMA 129.0, DADD 197.4, DMUL 70.2
-    ("0a56c3ba8029", "f16dev", 128): 484.1,   # FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1 per site
-    ("0a56c3ba8029", "f32", 128): 484.1,      # the same counts
-    ("0a56c3ba8029", "f64", 128): 525.6,      # DFMA 129.0, DADD 197.4, DMUL 70.2 per site
+    # pair kernel: FFMA 10.8, FADD 64.3, FMUL 20.6, FADD2 36.6, FFMA2 43.9, FMUL2 29.9, FHADD 75.2 per site
+    ("2b86a63b5b5f", "f16dev", 128): 490.5,
+    ("2b86a63b5b5f", "f32", 128): 484.2,       # tile kernel: FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1
+    ("2b86a63b5b5f", "f64", 128): 525.6,       # tile kernel: DFMA 129.0, DADD 197.4, DMUL 70.2
 }
 # FP64-pipe instructions per lattice update of the float64 step (DFMA, DADD,
 # DMUL, DSETP, F2F): each occupies the pipe like one FMA, so their rate against
 # half the FMA flop rate is the pipe's utilisation.
-NCU_FP64_PIPE_OPS = {("0a56c3ba8029", "f64", 128): 401.7, ("8e569adda85f", "f64", 128): 401.7}
+NCU_FP64_PIPE_OPS = {("2b86a63b5b5f", "f64", 128): 401.7}
 
 
 def alu_roofline(fp: str, storage: str, n: int, glups: float, fma: dict | None):

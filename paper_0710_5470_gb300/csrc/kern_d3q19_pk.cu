@@ -8,10 +8,10 @@ using namespace lbk;
 
 namespace {
 
-template <class S, int TX, int TY, int MINB, int PF, bool MIXED, bool AOS = false>
+template <class S, int TX, int TY, int MINB, int PF, bool MIXED, bool AOS = false, bool PB = false>
 struct PKLaunch {
     using Lay = LayoutPK<TX, TY, PairIO<S>::RAW16>;
-    static const void* fn() { return reinterpret_cast<const void*>(step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED, AOS>); }
+    static const void* fn() { return reinterpret_cast<const void*>(step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED, AOS, PB>); }
     static cudaError_t step(const StepArgs& a, dim3 grid, cudaStream_t st) {
         static int attr_done = 0;
         if (!attr_done) {
@@ -19,7 +19,7 @@ struct PKLaunch {
             if (e != cudaSuccess) return e;
             attr_done = 1;
         }
-        step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED, AOS><<<grid, Lay::NTH, Lay::BYTES, st>>>(a);
+        step_kernel3d_pk<S, TX, TY, MINB, PF, MIXED, AOS, PB><<<grid, Lay::NTH, Lay::BYTES, st>>>(a);
         return cudaGetLastError();
     }
     static void apply(LbKernelSet& k, const char* name) {
@@ -59,7 +59,7 @@ LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet k) {
             case 10: PKLaunch<StF16, 64, 12, 1, 2, true>::apply(k, "pairs 64x12, prefetch all"); break;
             case 9: PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched"); break;
             case 14:
-                if (aos) PKLaunch<StF16, 32, 8, 3, 2, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
+                if (aos) PKLaunch<StF16, 32, 8, 3, 2, true, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
                 else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
                 break;
             case 16:
@@ -70,13 +70,17 @@ LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet k) {
                 if (aos) PKLaunch<StF16, 32, 8, 3, 1, true, true>::apply(k, "pairs 32x8, interleaved blocks, own pair prefetched");
                 else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
                 break;
+            case 25:
+                if (aos) PKLaunch<StF16, 32, 8, 3, 2, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all, stencils site by site");
+                else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
+                break;
             default:
-                if (aos) PKLaunch<StF16, 32, 8, 3, 2, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
+                if (aos) PKLaunch<StF16, 32, 8, 3, 2, true, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
                 else PKLaunch<StF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
                 break;
         }
     } else if (storage == 3) {
-        if (aos) PKLaunch<StBF16, 32, 8, 3, 2, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
+        if (aos) PKLaunch<StBF16, 32, 8, 3, 2, true, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
         else PKLaunch<StBF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
     } else if (storage == 1 && v > 0) {
         PKLaunch<StF32, 32, 8, 2, 0, false>::apply(k, "pairs 32x8");

@@ -13,12 +13,15 @@
 //     pairs, one paired instruction (FADD2 / FMUL2 / FFMA2) for both sites;
 //   * stage A sums the density of 16-bit deviations with mixed-precision
 //     adds (float32 accumulator, fp16 / bf16 operand), so a halo site costs
-//     one instruction per population besides its load;
+//     one instruction per population besides its load; the own pair's
+//     momentum is summed the same way;
 //   * the owner thread loads its own pair in stage A and keeps the raw
 //     populations in a thread-private shared-memory stash (128-bit accesses)
 //     until its collision two planes later, so the stash needs no barrier;
 //   * the own sites' gradient, Laplacian and density stay in registers from
-//     stage B / stage A to the collision.
+//     stage B / stage A to the collision; stage B forms the own pair's
+//     stencil parts as packed pairs from one aligned 2-vector and two scalars
+//     per row.
 //
 // Two barriers per plane: after stage A (densities of the plane visible) and
 // after stage B (M' of the plane visible).
@@ -188,6 +191,29 @@ __device__ __forceinline__ void pair_momentum(const typename PairIO<S>::W (&w)[1
     });
 }
 
+// The same momentum from the raw 16-bit words by mixed-precision adds: for
+// every axis the populations with e_a = +1 and with e_a = -1 are summed into
+// float32 accumulators (one add per value, no decode) and differenced once.
+template <class S>
+__device__ __forceinline__ void pair_momentum_mixed(const typename PairIO<S>::W (&w)[18], P2 (&j)[3]) {
+    using L = D3Q19;
+    static_assert(PairIO<S>::RAW16, "16-bit storage");
+    float pl[3][2] = {}, mi[3][2] = {};
+    static_for<1, 19>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (e[a] == 0) continue;
+            float* acc = e[a] > 0 ? pl[a] : mi[a];
+            if constexpr (std::is_same<S, StF16>::value) madd_f16x2(acc[0], acc[1], w[i - 1]);
+            else madd_bf16x2(acc[0], acc[1], w[i - 1]);
+        }
+    });
+#pragma unroll
+    for (int a = 0; a < 3; ++a) j[a] = pp(pl[a][0], pl[a][1]) - pp(mi[a][0], mi[a][1]);
+}
+
 // ------------------------------------------------------------ collision of a pair
 // collide() of step_kernel.cuh (forcing scheme, deviation space) for two
 // sites at once, split into the per-site coefficients (PairColl::prep) and the
@@ -204,6 +230,61 @@ struct PairPhys {
 };
 
 __device__ __forceinline__ P2 rcp2(P2 x) { return pp(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+
+// ------------------------------------------------------------ stencils of a pair
+// plane_parts / finish / start of step3d.cuh for the two sites of a pair at
+// once: the 3 x 4 density neighbourhood of the pair is read as one aligned
+// 2-vector and two scalars per row (9 shared loads instead of 18) and the
+// parts are formed with paired float32 instructions.
+struct PlaneParts2 {
+    P2 dx, dy, s;            // Dx, Dy, S of the plane
+    P2 gx, gy, lin, c;       // in-plane parts of d_x, d_y, sum w rho, and rho
+};
+struct StencilAcc2 {
+    P2 gx, gy, gz, lap;
+    P2 dx, dy, s;
+};
+
+// rc: region index of site 0 of the pair (even); RX even
+__device__ __forceinline__ PlaneParts2 plane_parts2(const float* rho, int rc, int RX) {
+    const float2 C = *reinterpret_cast<const float2*>(rho + rc);
+    const float2 U = *reinterpret_cast<const float2*>(rho + rc + RX);
+    const float2 D = *reinterpret_cast<const float2*>(rho + rc - RX);
+    const P2 c{C}, yp{U}, ym{D};
+    const P2 xm = pp(rho[rc - 1], C.x), xp = pp(C.y, rho[rc + 2]);
+    const P2 ppp = pp(U.y, rho[rc + RX + 2]), pm = pp(D.y, rho[rc - RX + 2]);
+    const P2 mp = pp(rho[rc + RX - 1], U.x), mm = pp(rho[rc - RX - 1], D.x);
+    const P2 sixth = pp(1.0f / 6.0f), twelfth = pp(1.0f / 12.0f);
+    PlaneParts2 o;
+    o.dx = xp - xm;
+    o.dy = yp - ym;
+    const P2 f = (xp + xm) + (yp + ym);
+    o.s = fma(sixth, c, twelfth * f);
+    o.gx = fma(sixth, o.dx, twelfth * ((ppp + pm) - (mp + mm)));
+    o.gy = fma(sixth, o.dy, twelfth * ((ppp + mp) - (pm + mm)));
+    o.lin = fma(sixth, f, twelfth * ((ppp + pm) + (mp + mm)));
+    o.c = c;
+    return o;
+}
+
+__device__ __forceinline__ void finish2(const StencilAcc2& a, const PlaneParts2& hi, P2 (&G)[3], P2& lap) {
+    const P2 twelfth = pp(1.0f / 12.0f);
+    G[0] = fma(twelfth, hi.dx, a.gx);
+    G[1] = fma(twelfth, hi.dy, a.gy);
+    G[2] = a.gz + hi.s;
+    lap = fma(pp(2.0f), hi.s, a.lap);
+}
+
+__device__ __forceinline__ void start2(StencilAcc2& a, const PlaneParts2& cur) {
+    const P2 twelfth = pp(1.0f / 12.0f);
+    a.gx = fma(twelfth, a.dx, cur.gx);
+    a.gy = fma(twelfth, a.dy, cur.gy);
+    a.gz = -a.s;
+    a.lap = fma(pp(2.0f), cur.lin + a.s, pp(-4.0f) * cur.c);
+    a.dx = cur.dx;
+    a.dy = cur.dy;
+    a.s = cur.s;
+}
 
 struct PairColl {
     P2 Jw[3];      // omega j + g
@@ -336,8 +417,9 @@ __host__ __device__ __forceinline__ unsigned aos_bytes(unsigned q) {
 // stage A.  MIXED: densities by mixed-precision adds (16-bit storage).
 // AOS: populations 1..18 in the interleaved block layout (nx a multiple of
 // AOS_SITES): one address per site, the 18 rows at fixed offsets from it;
-// args.src[1] / args.dst[1] point at the first block.
-template <class S, int TX, int TY, int MINB, int PF, bool MIXED, bool AOS = false>
+// args.src[1] / args.dst[1] point at the first block.  PB: stage B of the own
+// pair with the paired stencils (plane_parts2) instead of site by site.
+template <class S, int TX, int TY, int MINB, int PF, bool MIXED, bool AOS = false, bool PB = false>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const StepArgs args) {
     using L = D3Q19;
     using IO = PairIO<S>;
@@ -474,6 +556,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
     StencilAcc<float> acc[NB];
 #pragma unroll
     for (int m = 0; m < NB; ++m) acc[m] = StencilAcc<float>{0, 0, 0, 0, 0, 0, 0};
+    StencilAcc2 acc2{pp(0.f), pp(0.f), pp(0.f), pp(0.f), pp(0.f), pp(0.f), pp(0.f)};
     // body force carries of the own pair: -(U0(q-1) + U-(q-2)) and -U-(q-1)
     P2 gacc1[3] = {pp(0.f), pp(0.f), pp(0.f)}, gacc2[3] = {pp(0.f), pp(0.f), pp(0.f)};
     // G, lap of the own pair: of plane q - 1 (Gc, for this plane's collision) and of q (Gn)
@@ -499,7 +582,8 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
                         float2* mo = mom_s + slot * 4 * NTH + tid;
                         mo[0] = r.v;
                         P2 j[3];
-                        pair_momentum<S>(ri[0], j);
+                        if constexpr (MIXED && RAW16) pair_momentum_mixed<S>(ri[0], j);
+                        else pair_momentum<S>(ri[0], j);
                         mo[NTH] = j[0].v;
                         mo[2 * NTH] = j[1].v;
                         mo[3 * NTH] = j[2].v;
@@ -526,10 +610,29 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
         // ---------------- stage B: stencil parts of plane p; G, lap, M' of plane q = p - 1
         const bool assemble = it >= 2;
         float Go[2][4];
+        P2 Gn[3], lapn;
         {
             const float* rho_p = rho_s + (it & 1) * Lay::RN;
+            if constexpr (PB) {
+                const PlaneParts2 cur = plane_parts2(rho_p, b_rc[0], RX);
+                if (assemble) {
+                    finish2(acc2, cur, Gn, lapn);
 #pragma unroll
-            for (int m = 0; m < NB; ++m) {
+                    for (int m = 0; m < 2; ++m) {
+                        const float G[3] = {m ? Gn[0].v.y : Gn[0].v.x, m ? Gn[1].v.y : Gn[1].v.x,
+                                            m ? Gn[2].v.y : Gn[2].v.x};
+                        const float g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+                        const float hk = 0.5f * pk * g2;
+                        LB_GUARD(b_mp[m] >= 0 && b_mp[m] < Lay::SN, BK_PK_SHARED, b_mp[m], continue)
+                        mpA[b_mp[m]] = make_float4(pk * G[0] * G[0] - hk, pk * G[0] * G[1], pk * G[0] * G[2],
+                                                   pk * G[1] * G[1] - hk);
+                        mpB[b_mp[m]] = make_float2(pk * G[1] * G[2], pk * G[2] * G[2] - hk);
+                    }
+                }
+                start2(acc2, cur);
+            }
+#pragma unroll
+            for (int m = PB ? 2 : 0; m < NB; ++m) {
                 if (b_rc[m] < 0) continue;
                 const PlaneParts<float> cur = plane_parts(rho_p, b_rc[m], RX);
                 if (assemble) {
@@ -717,9 +820,15 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) step_kernel3d_pk(const St
             advance(zr[2]);
         }
         if (assemble) {
+            if constexpr (PB) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Gc[c] = pp(Go[0][c], Go[1][c]);
-            lapc = pp(Go[0][3], Go[1][3]);
+                for (int c = 0; c < 3; ++c) Gc[c] = Gn[c];
+                lapc = lapn;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Gc[c] = pp(Go[0][c], Go[1][c]);
+                lapc = pp(Go[0][3], Go[1][3]);
+            }
         }
     }
     if (bad) atomicOr(args.status, 1u);

@@ -286,7 +286,7 @@ def test_paired_halo_loads_are_bit_identical_2d(storage, scheme, shape, monkeypa
 
 
 @pytest.mark.parametrize("storage,tol_f,tol_rho", [(F16DEV, 1e-5, 1e-5), (BF16DEV, 8e-5, 6e-5), (F32, 2e-6, 2e-6)])
-@pytest.mark.parametrize("variant", ["default", "1", "2", "4", "8", "9", "10", "14"])
+@pytest.mark.parametrize("variant", ["default", "1", "2", "4", "8", "9", "10", "14", "15", "16", "25"])
 @pytest.mark.parametrize("shape", [(68, 20, 12), (2, 3, 3), (130, 10, 40), (64, 16, 9), (96, 20, 7), (32, 5, 3)])
 def test_pair_kernel_parity(shape, variant, storage, tol_f, tol_rho, monkeypatch):
     """The D3Q19 forcing-scheme pair kernel (two x sites per thread, packed
@@ -318,3 +318,4 @@ def test_pair_kernel_parity(shape, variant, storage, tol_f, tol_rho, monkeypatch
         rho = want.sum(axis=0)
         assert rel_inf(got, want) < tol_f * steps, (steps, rel_inf(got, want))
         assert rel_inf(rho_g, rho) < tol_rho * steps
+
