@@ -237,6 +237,65 @@ def oracle_sample(n_edge: int, steps: int, scheme: str = "forcing"):
     return lu / dt / 1e6, dt, lu
 
 
+def cpu_model() -> str:
+    """Name of the host CPU (lscpu's model name, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(job):
+    """One process of the all-core oracle run: wait for the others, then time
+    `steps` oracle steps on its own edge^3 drop box."""
+    edge, steps, scheme, bar = job
+    from oracle import lb_oracle as O
+    m = O.Model("D3Q19", A_VDW, B_VDW, WORKLOAD["T"], WORKLOAD["kappa"], WORKLOAD["tau"], scheme=scheme)
+    rl, rg = O.coexistence(A_VDW, B_VDW, WORKLOAD["T"])
+    R = WORKLOAD["R"] * edge / WORKLOAD["n"]
+    f = O.init_equilibrium(O.drop_density((edge,) * 3, [(edge / 2,) * 3], [R], rl, rg, WORKLOAD["width"]), m)
+    bar.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = O.step(f, m)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(edge: int, steps: int, scheme: str = "forcing", procs: int | None = None):
+    """The oracle on every host core at once: `procs` single-threaded processes
+    (spawned), each stepping its own edge^3 box; returns (aggregate MLUPS,
+    seconds of the slowest, processes)."""
+    import multiprocessing as mp
+    procs = procs or len(os.sched_getaffinity(0))
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in keep:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Manager() as man:
+            bar = man.Barrier(procs)
+            with ctx.Pool(procs) as pool:
+                dts = pool.map(_oracle_worker, [(edge, steps, scheme, bar)] * procs)
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    dt = max(dts)
+    return procs * edge ** 3 * steps / dt / 1e6, dt, procs
+
+
 # ---------------------------------------------------------------- arms
 def run_reference(args):
     world, rank, local, dist = dist_setup(args.gpus)
@@ -266,7 +325,8 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"D3Q19 {WORKLOAD['n']}^3 drop R=30, {args.scheme} scheme, T=0.55, kappa=0.01, tau=1",
                        "sample_edge": edge},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -417,8 +477,17 @@ def run_native(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         edge = n
         v, dt, lu = oracle_sample(edge, 5, args.scheme)
-        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        model = cpu_model()
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "cpu": model,
                "sample": f"5 FP64 oracle steps (numpy, one thread) on the full {edge}^3 drop workload ({dt:.1f} s)"}
+        try:
+            va, dta, procs = oracle_all_cores(64, 4, args.scheme)
+            cpu["all_cores"] = {"value": va, "unit": "MLUPS", "cores": procs, "kind": "oracle", "cpu": model,
+                                "sample": f"{procs} single-threaded oracle processes at once, each 4 FP64 steps "
+                                          f"of its own 64^3 drop box (the workload scaled to 64^3; "
+                                          f"slowest {dta:.1f} s)"}
+        except Exception as e:                                  # a host without process support
+            cpu["all_cores"] = {"unavailable": repr(e)}
 
     if rank == 0:
         line = {
