@@ -8,6 +8,7 @@
 // work list on the device.  No kernel waits on another CTA.
 #pragma once
 #include "aux_kernels.cuh"
+#include "step2d_pk.cuh"
 
 namespace lbk {
 
@@ -55,6 +56,23 @@ __global__ void __launch_bounds__(TX* TY) batch_step_kernel(BatchState bs, char*
     const int tx = I.tiles_x;
     step2d_tile<D2Q9, FORCING, S, TX, TY>(a, (t % tx) * TX, (t / tx) * TY,
                                           reinterpret_cast<typename S::real*>(smem_raw));
+}
+
+// The same step with the pair kernel of step2d_pk.cuh ((TX / 2) * TY threads per
+// tile; 32-bit arithmetic): aligned pairs for instances with an even nx.
+template <bool FORCING, class S, int TX, int TY>
+__global__ void __launch_bounds__((TX / 2) * TY) batch_step_kernel_pk(BatchState bs, char* buf, int parity) {
+    if (blockIdx.x >= *bs.count) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned it = bs.items[blockIdx.x];
+    const int k = int(it >> 20), t = int(it & 0xFFFFFu);
+    const BatchInst& I = bs.inst[k];
+    Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
+                 I.kappa, I.omega, I.nu, I.fa, I.fb, I.fT, I.fkappa, I.fomega, I.fnu, I.pref, I.rsum,
+                 bs.status + k};
+    const int tx = I.tiles_x;
+    if (I.pair) step2d_pair_tile<FORCING, S, TX, TY, true>(a, (t % tx) * TX, (t / tx) * TY, smem_raw);
+    else step2d_pair_tile<FORCING, S, TX, TY, false>(a, (t % tx) * TX, (t / tx) * TY, smem_raw);
 }
 
 // max over the tile of |u - uprev| (u = j / rho, Eq. 3), folded into maxdu[k]; uprev <- u.

@@ -21,6 +21,7 @@ enum BoundsKind : unsigned {
     BK_3D_STORE = 5,    // D3Q19 tile kernel push stores
     BK_2D_LOAD = 6,     // D2Q9 tile (single lattice and batch) loads
     BK_2D_STORE = 7,    // D2Q9 tile push stores
+    BK_2D_SHARED = 8,   // D2Q9 pair kernel: M' shared-memory writes
 };
 
 #ifdef LB_DEBUG_BOUNDS

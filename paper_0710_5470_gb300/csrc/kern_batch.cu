@@ -72,10 +72,38 @@ struct BatchLaunch {
     }
 };
 
+// The pair kernel (32-bit arithmetic) on the same tiles: (TX / 2) * TY threads.
+template <bool F, class S, int TX, int TY>
+struct BatchLaunchPK : BatchLaunch<F, S, TX, TY> {
+    using Lay = Layout2PK<F, TX, TY>;
+    static void step(const BatchState& bs, char* buf, int parity, int nblocks, cudaStream_t st) {
+        batch_step_kernel_pk<F, S, TX, TY><<<nblocks, Lay::NTH, Lay::BYTES, st>>>(bs, buf, parity);
+    }
+    static BatchKernels make() {
+        BatchKernels k = BatchLaunch<F, S, TX, TY>::make();
+        k.smem = Lay::BYTES;
+        k.step_fn = reinterpret_cast<const void*>(batch_step_kernel_pk<F, S, TX, TY>);
+        k.step = &step;
+        return k;
+    }
+};
+
 constexpr int NTILES = 3;   // tile variants tried by the autotuner: 32x8, 32x16, 64x8
 
+// Float64 runs the one-site tile kernel; 32-bit arithmetic the pair kernel
+// (LB_D2_VARIANT=0: the tile kernel, for comparisons).
 template <bool F, class S>
 BatchKernels pick_tile(int t) {
+    if constexpr (sizeof(typename S::real) == 4) {
+        const char* env = std::getenv("LB_D2_VARIANT");
+        if (!(env && std::atoi(env) == 0)) {
+            switch (t) {
+                case 0: return BatchLaunchPK<F, S, 32, 8>::make();
+                case 1: return BatchLaunchPK<F, S, 32, 16>::make();
+                default: return BatchLaunchPK<F, S, 64, 8>::make();
+            }
+        }
+    }
     switch (t) {
         case 0: return BatchLaunch<F, S, 32, 8>::make();
         case 1: return BatchLaunch<F, S, 32, 16>::make();

@@ -14,8 +14,10 @@ static LbKernelSet pick(int storage) {
     return LbKernelSet{};
 }
 
+LbKernelSet lbk_pk2d(int scheme, int storage, LbKernelSet k);
+
 LbKernelSet lbk_kernels_d2q9(int scheme, int storage) {
-    return scheme == 1 ? pick<true>(storage) : pick<false>(storage);
+    return lbk_pk2d(scheme, storage, scheme == 1 ? pick<true>(storage) : pick<false>(storage));
 }
 
 // First recorded index violation of this unit's kernels (checked builds; see bounds.cuh).

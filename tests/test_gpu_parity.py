@@ -262,12 +262,15 @@ def test_paired_halo_loads_are_bit_identical(storage, scheme, shape, monkeypatch
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("kernel", ["pairs", "tile"])
 @pytest.mark.parametrize("storage", [F32, F16DEV, BF16DEV])
 @pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
 @pytest.mark.parametrize("shape", [(66, 20), (2, 5), (34, 47)])
-def test_paired_halo_loads_are_bit_identical_2d(storage, scheme, shape, monkeypatch):
-    """The D2Q9 step with an even nx loads two sites per access in its halo
-    stage; it gives exactly the one-site form's result."""
+def test_paired_halo_loads_are_bit_identical_2d(storage, scheme, shape, kernel, monkeypatch):
+    """The D2Q9 step with an even nx moves two sites per access (the pair
+    kernel everywhere, the tile kernel in its halo stage); it gives exactly
+    the result of the same kernel moving one site per access."""
+    monkeypatch.setenv("LB_D2_VARIANT", "1" if kernel == "pairs" else "0")
     lb = library()
     m = oracle_model("D2Q9", scheme)
     f0 = drop_populations(m, shape, 0.3 * min(shape), perturb=1e-3, seed=8)
@@ -319,3 +322,27 @@ def test_pair_kernel_parity(shape, variant, storage, tol_f, tol_rho, monkeypatch
         assert rel_inf(got, want) < tol_f * steps, (steps, rel_inf(got, want))
         assert rel_inf(rho_g, rho) < tol_rho * steps
 
+
+
+@pytest.mark.parametrize("storage,tol_f", [(F32, 2e-6), (F16DEV, 1e-5), (BF16DEV, 8e-5)])
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+@pytest.mark.parametrize("shape", [(45, 37), (46, 37), (64, 16), (3, 9), (2, 2), (130, 7)])
+def test_d2q9_pair_and_tile_kernels(shape, scheme, storage, tol_f, monkeypatch):
+    """The D2Q9 pair kernel (two x sites per thread, packed float32 pairs;
+    odd nx: every site loaded and stored on its own) and the one-site tile
+    kernel, one and five steps from the same rounded state as the oracle:
+    every population within tol_f of max|f| per step."""
+    lb = library()
+    m = oracle_model("D2Q9", scheme)
+    f0 = drop_populations(m, shape, 0.3 * min(shape), perturb=1e-3, seed=9)
+    for variant, form in (("1", "pairs"), ("0", "tile")):
+        monkeypatch.setenv("LB_D2_VARIANT", variant)
+        for steps in (1, 5):
+            with make_ctx(lb, "D2Q9", scheme, shape, storage=storage) as ctx:
+                ctx.set_populations(f0)
+                start = ctx.get_populations()
+                ctx.step(steps)
+                got = ctx.get_populations()
+                assert ctx.kernel_info()["form"].startswith(form)
+            want = O.run(start, m, steps)
+            assert rel_inf(got, want) < tol_f * steps, (variant, steps, rel_inf(got, want))
