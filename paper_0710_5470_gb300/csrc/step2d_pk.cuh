@@ -269,10 +269,11 @@ __device__ __forceinline__ void step2d_pair_tile(const Tile2DArgs& args, int x0,
     const long long pitch = args.pitch;
 
     // raw populations of the pair whose site 0 is at (x, y) of the lattice
+    // (wrap_near: one compare-and-add for offsets up to a lattice width outside)
     auto load = [&](int x, int y, float2& f0, Wd (&w)[8]) {
-        const size_t row = size_t(wrapi(y, ny)) * nx;
+        const size_t row = size_t(wrap_near(y, ny)) * nx;
         if constexpr (AL) {
-            const size_t q = row + wrapi(x, nx);   // even
+            const size_t q = row + wrap_near(x, nx);   // even
             LB_GUARD(q + 1 < nsites, BK_2D_LOAD, q, f0 = make_float2(0.f, 0.f); for (int i = 0; i < 8; ++i) w[i] = Wd{};
                      return)
             f0 = reinterpret_cast<const float2*>(src)[q >> 1];
@@ -281,7 +282,7 @@ __device__ __forceinline__ void step2d_pair_tile(const Tile2DArgs& args, int x0,
                 w[i - 1] = IO::ld(src + S::pop_offset(i, pitch), unsigned(q));
             });
         } else {
-            const size_t qa = row + wrapi(x, nx), qb = row + wrapi(x + 1, nx);
+            const size_t qa = row + wrap_near(x, nx), qb = row + wrap_near(x + 1, nx);
             LB_GUARD(qa < nsites && qb < nsites, BK_2D_LOAD, qa, f0 = make_float2(0.f, 0.f);
                      for (int i = 0; i < 8; ++i) w[i] = Wd{}; return)
             const float* f = reinterpret_cast<const float*>(src);
@@ -389,8 +390,8 @@ __device__ __forceinline__ void step2d_pair_tile(const Tile2DArgs& args, int x0,
     PairColl2D<FORCING> K;
     K.prep(rho, j, G, lap, g, ph);
     const P2 o0 = fma(K.omw, P2{f0o}, K.c0);
-    const int xm1 = wrapi(xo - 1, nx), xp1 = wrapi(xo + 1, nx), xp2 = wrapi(xo + 2, nx);
-    const size_t yr[3] = {size_t(wrapi(yo - 1, ny)) * nx, size_t(yo) * nx, size_t(wrapi(yo + 1, ny)) * nx};
+    const int xm1 = wrap_near(xo - 1, nx), xp1 = wrap_near(xo + 1, nx), xp2 = wrap_near(xo + 2, nx);
+    const size_t yr[3] = {size_t(wrap_near(yo - 1, ny)) * nx, size_t(yo) * nx, size_t(wrap_near(yo + 1, ny)) * nx};
     // destination column of site s moved by ex (site 0 at xo, site 1 at xo + 1)
     const int col[2][3] = {{xm1, xo, xp1}, {xo, xp1, xp2}};
     auto store = [&](auto I, P2 v) {
