@@ -18,7 +18,10 @@ multiplies the O(d^3) stencil errors, zero at tau = 1/2 + 1/(2 sqrt 3).
 Also the 512^2 multi-drop workload (1-8 drops, every (T, kappa) of the
 sweep grid, both schemes, float32 and float64): throughput and spurious velocity.
 
-  python -m paper_0710_5470_gb300.scans tau|fig2|multidrop [--steps N]   (one JSON line)
+Fig. 1: the steady flow around the paper's drop with the simple gradient
+(B = 0) and with the optimum: eight vortices in the gas, and the reduction.
+
+  python -m paper_0710_5470_gb300.scans tau|fig1|fig2|multidrop [--steps N] [--out DIR]   (one JSON line)
 """
 from __future__ import annotations
 
@@ -104,6 +107,83 @@ def fig2_scans(scans=FIG2, steps: int = 10000, forcing_scans=FIG2_FORCING) -> di
     return out
 
 
+def flow_pattern(rho, u, rho_l: float, rho_g: float, nth: int = 720, modes: int = 12) -> dict:
+    """Angular structure of the spurious flow around a centred 2D drop (Fig. 1):
+    on a circle in the gas halfway between the equimolar radius R_e and the
+    box edge, the radial velocity u_r(theta) and the vorticity dx u_y - dy u_x
+    (central differences, periodic), sampled at nth angles by bilinear
+    interpolation; their sign changes around the circle (a ring of N vortices
+    gives N of each) and the amplitudes |sum u_r e^{-i m theta}| / nth of the
+    angular modes m = 0 .. modes of the radial velocity."""
+    import numpy as np
+    rho = np.asarray(rho, dtype=np.float64).reshape(np.shape(rho)[-2:])
+    ux = np.asarray(u[0], dtype=np.float64).reshape(rho.shape)
+    uy = np.asarray(u[1], dtype=np.float64).reshape(rho.shape)
+    ny, nx = rho.shape
+    R_e = math.sqrt(float(np.sum(rho - rho_g)) / (rho_l - rho_g) / math.pi)
+    r = R_e + 0.5 * (0.5 * min(nx, ny) - R_e)
+    wz = 0.5 * (np.roll(uy, -1, axis=1) - np.roll(uy, 1, axis=1)) - 0.5 * (np.roll(ux, -1, axis=0) - np.roll(ux, 1, axis=0))
+
+    def sample(f, x, y):
+        x0, y0 = np.floor(x).astype(int), np.floor(y).astype(int)
+        fx, fy = x - x0, y - y0
+        g = lambda yy, xx: f[yy % ny, xx % nx]
+        return ((1 - fx) * (1 - fy) * g(y0, x0) + fx * (1 - fy) * g(y0, x0 + 1) + (1 - fx) * fy * g(y0 + 1, x0)
+                + fx * fy * g(y0 + 1, x0 + 1))
+
+    th = 2 * math.pi * np.arange(nth) / nth
+    # the drop is centred at (n/2, n/2) of the site grid
+    xs, ys = nx / 2 + r * np.cos(th), ny / 2 + r * np.sin(th)
+    ur = sample(ux, xs, ys) * np.cos(th) + sample(uy, xs, ys) * np.sin(th)
+    om = sample(wz, xs, ys)
+    def changes(a):
+        sg = np.sign(a)
+        for k in range(len(sg)):          # an exact zero keeps the sign before it
+            if sg[k] == 0:
+                sg[k] = sg[k - 1] if k > 0 else 1.0
+        return int(np.sum(sg != np.roll(sg, 1)))
+    amp = [float(abs(np.sum(ur * np.exp(-1j * m * th))) / nth) for m in range(modes + 1)]
+    return {"R_e": R_e, "r_probe": r, "ur_sign_changes": changes(ur), "vorticity_sign_changes": changes(om),
+            "ur_modes": amp, "dominant_mode": int(np.argmax(amp)), "max_u": float(np.sqrt(ux ** 2 + uy ** 2).max())}
+
+
+def fig1(steps: int = 10000, standard: dict | None = None, drop=PAPER_DROP, out_dir: str | None = None) -> dict:
+    """Fig. 1: the steady spurious flow of the paper's drop (equilibrium scheme,
+    float64) with a standard choice - by default the simple central-difference
+    gradient, B = 0 (Sec. IV) - and with the optimum of Sec. III: the flow
+    pattern of each (flow_pattern) and the reduction of max|u|.  With out_dir,
+    the fields go to fig1.npz and the speed |u| of each run to a greyscale
+    PGM image (headless)."""
+    import numpy as np
+    standard = standard if standard is not None else {"B": 0.0}
+    n = drop["n"]
+    rl, rg = lb.coexistence(A_VDW, B_VDW, drop["T"])
+    res, fields = {"drop": dict(drop), "steps": steps, "standard": standard}, {}
+    for name, params in (("standard", standard), ("optimum", {})):
+        with lb.Context(lb.D2Q9, (n, n), A_VDW, B_VDW, drop["T"], drop["kappa"], 1.0, scheme=lb.EQUILIBRIUM,
+                        storage=lb.F64) as ctx:
+            ctx.set_free_params(**params)
+            ctx.init_drops([(n / 2, n / 2)], [drop["R"]], drop["width"])
+            ctx.step(steps)
+            rho, u, _ = ctx.fields(want_v=False)
+        rho2, u2 = rho.reshape(n, n), u.reshape(2, n, n)
+        fields[name] = (rho2, u2)
+        res[name] = flow_pattern(rho2, u2, rl, rg)
+    res["reduction"] = res["standard"]["max_u"] / res["optimum"]["max_u"]
+    if out_dir:
+        import os
+        os.makedirs(out_dir, exist_ok=True)
+        np.savez(os.path.join(out_dir, "fig1.npz"), **{f"{k}_rho": v[0] for k, v in fields.items()},
+                 **{f"{k}_u": v[1] for k, v in fields.items()})
+        for k, (_, u2) in fields.items():
+            sp = np.sqrt((u2 ** 2).sum(axis=0))
+            img = (255 * sp / max(sp.max(), 1e-300)).astype(np.uint8)[::-1]
+            with open(os.path.join(out_dir, f"fig1_{k}_speed.pgm"), "wb") as fh:
+                fh.write(f"P5 {n} {n} 255\n".encode())
+                fh.write(img.tobytes())
+    return res
+
+
 def multi_drop_sweep(seed: int = 0, storages=(lb.F32, lb.F64), steps: int = 20000, n: int = 512, tau: float = 0.8,
                      Ts=(0.50, 0.53, 0.55), kappas=(0.004, 0.01, 0.02)) -> dict:
     """D2Q9 n^2 with 1-8 non-overlapping drops R ~ U[20, 80] (inputs.random_drops(seed)), every
@@ -151,14 +231,17 @@ def tau_sweep(taus=TAUS, steps: int = 10000) -> dict:
 
 def main():
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    p.add_argument("what", choices=["tau", "fig2", "multidrop"])
+    p.add_argument("what", choices=["tau", "fig1", "fig2", "multidrop"])
     p.add_argument("--steps", type=int, default=10000)
+    p.add_argument("--out", default=None, help="fig1: directory for fig1.npz and the PGM speed images")
     a = p.parse_args()
     from . import build
     build.build()
     lb.load_library()
     if a.what == "tau":
         res = tau_sweep(steps=a.steps)
+    elif a.what == "fig1":
+        res = fig1(steps=a.steps, out_dir=a.out)
     elif a.what == "fig2":
         res = fig2_scans(steps=a.steps)
     else:
