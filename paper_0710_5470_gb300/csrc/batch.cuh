@@ -43,95 +43,108 @@ struct BatchState {
     int n;                       // instances
 };
 
+// The launches of a batch are sized to the CTAs the GPU holds at once, not to
+// the work list: every CTA takes the items blockIdx.x, blockIdx.x + gridDim.x,
+// ... below the current count, so a batch whose instances have mostly retired
+// launches no CTAs that only find nothing to do.
 template <bool FORCING, class S, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) batch_step_kernel(BatchState bs, char* buf, int parity) {
-    if (blockIdx.x >= *bs.count) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const unsigned it = bs.items[blockIdx.x];
-    const int k = int(it >> 20), t = int(it & 0xFFFFFu);
-    const BatchInst& I = bs.inst[k];
-    Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
-                 I.kappa, I.omega, I.nu, I.fa, I.fb, I.fT, I.fkappa, I.fomega, I.fnu, I.pref, I.rsum,
-                 bs.status + k};
-    const int tx = I.tiles_x;
-    step2d_tile<D2Q9, FORCING, S, TX, TY>(a, (t % tx) * TX, (t / tx) * TY,
-                                          reinterpret_cast<typename S::real*>(smem_raw));
+    const unsigned count = unsigned(*bs.count);
+    for (unsigned item = blockIdx.x; item < count; item += gridDim.x) {
+        const unsigned it = bs.items[item];
+        const int k = int(it >> 20), t = int(it & 0xFFFFFu);
+        const BatchInst& I = bs.inst[k];
+        Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
+                     I.kappa, I.omega, I.nu, I.fa, I.fb, I.fT, I.fkappa, I.fomega, I.fnu, I.pref, I.rsum,
+                     bs.status + k};
+        const int tx = I.tiles_x;
+        step2d_tile<D2Q9, FORCING, S, TX, TY>(a, (t % tx) * TX, (t / tx) * TY,
+                                              reinterpret_cast<typename S::real*>(smem_raw));
+        __syncthreads();   // shared memory is reused by the next item
+    }
 }
 
 // The same step with the pair kernel of step2d_pk.cuh ((TX / 2) * TY threads per
 // tile; 32-bit arithmetic): aligned pairs for instances with an even nx.
 template <bool FORCING, class S, int TX, int TY>
 __global__ void __launch_bounds__((TX / 2) * TY) batch_step_kernel_pk(BatchState bs, char* buf, int parity) {
-    if (blockIdx.x >= *bs.count) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const unsigned it = bs.items[blockIdx.x];
-    const int k = int(it >> 20), t = int(it & 0xFFFFFu);
-    const BatchInst& I = bs.inst[k];
-    Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
-                 I.kappa, I.omega, I.nu, I.fa, I.fb, I.fT, I.fkappa, I.fomega, I.fnu, I.pref, I.rsum,
-                 bs.status + k};
-    const int tx = I.tiles_x;
-    if (I.pair) step2d_pair_tile<FORCING, S, TX, TY, true>(a, (t % tx) * TX, (t / tx) * TY, smem_raw);
-    else step2d_pair_tile<FORCING, S, TX, TY, false>(a, (t % tx) * TX, (t / tx) * TY, smem_raw);
+    const unsigned count = unsigned(*bs.count);
+    for (unsigned item = blockIdx.x; item < count; item += gridDim.x) {
+        const unsigned it = bs.items[item];
+        const int k = int(it >> 20), t = int(it & 0xFFFFFu);
+        const BatchInst& I = bs.inst[k];
+        Tile2DArgs a{buf + I.off[parity], buf + I.off[1 - parity], I.pitch, I.nx, I.ny, I.pair, I.a, I.b, I.T,
+                     I.kappa, I.omega, I.nu, I.fa, I.fb, I.fT, I.fkappa, I.fomega, I.fnu, I.pref, I.rsum,
+                     bs.status + k};
+        const int tx = I.tiles_x;
+        if (I.pair) step2d_pair_tile<FORCING, S, TX, TY, true>(a, (t % tx) * TX, (t / tx) * TY, smem_raw);
+        else step2d_pair_tile<FORCING, S, TX, TY, false>(a, (t % tx) * TX, (t / tx) * TY, smem_raw);
+        __syncthreads();   // shared memory is reused by the next item
+    }
 }
 
 // max over the tile of |u - uprev| (u = j / rho, Eq. 3), folded into maxdu[k]; uprev <- u.
 template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) batch_check_kernel(BatchState bs, const char* buf, int parity) {
-    if (blockIdx.x >= *bs.count) return;
     __shared__ double red[TX * TY], redu[TX * TY], rmax[TX * TY], rmin[TX * TY];
-    const unsigned it = bs.items[blockIdx.x];
-    const int k = int(it >> 20), t = int(it & 0xFFFFFu);
-    const BatchInst& I = bs.inst[k];
-    const int x = (t % I.tiles_x) * TX + int(threadIdx.x) % TX;
-    const int y = (t / I.tiles_x) * TY + int(threadIdx.x) / TX;
-    double du = 0.0, um = 0.0, rhi = 0.0, rlo = 1e300;
-    if (x < I.nx && y < I.ny) {
-        const size_t q = size_t(y) * I.nx + x;
-        const char* src = buf + I.off[parity];
-        using L = D2Q9;
-        double f[L::Q];
-        f[0] = double(S::dec0(S::ld0(src, q)));
-        static_for<1, L::Q>([&](auto II) {
-            constexpr int i = decltype(II)::value;
-            f[i] = double(S::devi(S::ldi(src + S::pop_offset(i, I.pitch), q)));
-        });
-        double rho = double(I.rsum) + f[0];
-        for (int i = 1; i < L::Q; ++i) rho += f[i];
-        double j[3];
-        momentum<L, double>(f, j);
-        const double ux = j[0] / rho, uy = j[1] / rho;
-        double* up = bs.uprev + 2 * (I.site0 + (long long)q);
-        const double dx = ux - up[0], dy = uy - up[1];
-        du = sqrt(dx * dx + dy * dy);
-        if (!(du <= 1e300)) du = 1e300;   // non-finite -> huge
-        um = sqrt(ux * ux + uy * uy);
-        if (!(um <= 1e300)) um = 1e300;
-        rhi = rho > 0.0 && rho <= 1e300 ? rho : 1e300;   // non-finite or non-positive -> out of any band
-        rlo = rho > 0.0 && rho <= 1e300 ? rho : 0.0;
-        up[0] = ux;
-        up[1] = uy;
-    }
-    red[threadIdx.x] = du;
-    redu[threadIdx.x] = um;
-    rmax[threadIdx.x] = rhi;
-    rmin[threadIdx.x] = rlo;
-    __syncthreads();
-    for (int s = TX * TY / 2; s > 0; s >>= 1) {
-        if (int(threadIdx.x) < s) {
-            red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-            redu[threadIdx.x] = fmax(redu[threadIdx.x], redu[threadIdx.x + s]);
-            rmax[threadIdx.x] = fmax(rmax[threadIdx.x], rmax[threadIdx.x + s]);
-            rmin[threadIdx.x] = fmin(rmin[threadIdx.x], rmin[threadIdx.x + s]);
+    const unsigned count = unsigned(*bs.count);
+    for (unsigned item = blockIdx.x; item < count; item += gridDim.x) {
+        const unsigned it = bs.items[item];
+        const int k = int(it >> 20), t = int(it & 0xFFFFFu);
+        const BatchInst& I = bs.inst[k];
+        const int x = (t % I.tiles_x) * TX + int(threadIdx.x) % TX;
+        const int y = (t / I.tiles_x) * TY + int(threadIdx.x) / TX;
+        double du = 0.0, um = 0.0, rhi = 0.0, rlo = 1e300;
+        if (x < I.nx && y < I.ny) {
+            const size_t q = size_t(y) * I.nx + x;
+            const char* src = buf + I.off[parity];
+            using L = D2Q9;
+            double f[L::Q];
+            f[0] = double(S::dec0(S::ld0(src, q)));
+            static_for<1, L::Q>([&](auto II) {
+                constexpr int i = decltype(II)::value;
+                f[i] = double(S::devi(S::ldi(src + S::pop_offset(i, I.pitch), q)));
+            });
+            double rho = double(I.rsum) + f[0];
+            for (int i = 1; i < L::Q; ++i) rho += f[i];
+            double j[3];
+            momentum<L, double>(f, j);
+            const double ux = j[0] / rho, uy = j[1] / rho;
+            double* up = bs.uprev + 2 * (I.site0 + (long long)q);
+            const double dx = ux - up[0], dy = uy - up[1];
+            du = sqrt(dx * dx + dy * dy);
+            if (!(du <= 1e300)) du = 1e300;   // non-finite -> huge
+            um = sqrt(ux * ux + uy * uy);
+            if (!(um <= 1e300)) um = 1e300;
+            rhi = rho > 0.0 && rho <= 1e300 ? rho : 1e300;   // non-finite or non-positive -> out of any band
+            rlo = rho > 0.0 && rho <= 1e300 ? rho : 0.0;
+            up[0] = ux;
+            up[1] = uy;
         }
+        red[threadIdx.x] = du;
+        redu[threadIdx.x] = um;
+        rmax[threadIdx.x] = rhi;
+        rmin[threadIdx.x] = rlo;
         __syncthreads();
-    }
-    // non-negative doubles order like their bit patterns
-    if (threadIdx.x == 0) {
-        atomicMax(bs.maxdu + k, (unsigned long long)__double_as_longlong(red[0]));
-        atomicMax(bs.maxu + k, (unsigned long long)__double_as_longlong(redu[0]));
-        atomicMax(bs.maxrho + k, (unsigned long long)__double_as_longlong(rmax[0]));
-        atomicMin(bs.minrho + k, (unsigned long long)__double_as_longlong(rmin[0]));
+        for (int s = TX * TY / 2; s > 0; s >>= 1) {
+            if (int(threadIdx.x) < s) {
+                red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+                redu[threadIdx.x] = fmax(redu[threadIdx.x], redu[threadIdx.x + s]);
+                rmax[threadIdx.x] = fmax(rmax[threadIdx.x], rmax[threadIdx.x + s]);
+                rmin[threadIdx.x] = fmin(rmin[threadIdx.x], rmin[threadIdx.x + s]);
+            }
+            __syncthreads();
+        }
+        // non-negative doubles order like their bit patterns
+        if (threadIdx.x == 0) {
+            atomicMax(bs.maxdu + k, (unsigned long long)__double_as_longlong(red[0]));
+            atomicMax(bs.maxu + k, (unsigned long long)__double_as_longlong(redu[0]));
+            atomicMax(bs.maxrho + k, (unsigned long long)__double_as_longlong(rmax[0]));
+            atomicMin(bs.minrho + k, (unsigned long long)__double_as_longlong(rmin[0]));
+        }
+        __syncthreads();   // the reduction arrays are reused by the next item
     }
 }
 

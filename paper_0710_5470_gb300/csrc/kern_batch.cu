@@ -24,8 +24,10 @@ lb_status fail(lb_status s, const std::string& m) {
 // ------------------------------------------------------------ kernel table
 struct BatchKernels {
     int tx = 0, ty = 0;
+    int threads = 0, check_threads = 0;   // per CTA of the step and of the check kernel
     size_t smem = 0;
     const void* step_fn = nullptr;
+    const void* check_fn = nullptr;
     void (*step)(const BatchState&, char*, int, int nblocks, cudaStream_t) = nullptr;
     void (*check)(const BatchState&, const char*, int, int nblocks, cudaStream_t) = nullptr;
     cudaError_t (*init_feq)(const double*, const double*, const PopPtrs&, Grid3, Phys, cudaStream_t) = nullptr;
@@ -61,8 +63,10 @@ struct BatchLaunch {
         BatchKernels k;
         k.tx = TX;
         k.ty = TY;
+        k.threads = k.check_threads = TX * TY;
         k.smem = Lay::BYTES;
         k.step_fn = reinterpret_cast<const void*>(batch_step_kernel<F, S, TX, TY>);
+        k.check_fn = reinterpret_cast<const void*>(batch_check_kernel<S, TX, TY>);
         k.step = &step;
         k.check = &check;
         k.init_feq = &init_feq;
@@ -81,6 +85,7 @@ struct BatchLaunchPK : BatchLaunch<F, S, TX, TY> {
     }
     static BatchKernels make() {
         BatchKernels k = BatchLaunch<F, S, TX, TY>::make();
+        k.threads = Lay::NTH;
         k.smem = Lay::BYTES;
         k.step_fn = reinterpret_cast<const void*>(batch_step_kernel_pk<F, S, TX, TY>);
         k.step = &step;
@@ -140,6 +145,8 @@ struct lb_batch {
     bool tuned = false;
     BatchKernels k;
     int max_items = 0;
+    // launch sizes of the step and check kernels: the CTAs resident at once (at most max_items)
+    int step_grid = 1, check_grid = 1;
     long long gstep = 0;              // host copy of the step counter
     int parity = 0;
     // device
@@ -207,6 +214,20 @@ lb_status set_tile(lb_batch* B, int tile) {
     B->tile = tile;
     B->k = batch_kernels(B->scheme, B->storage, tile);
     cudaFuncSetAttribute(B->k.step_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B->k.smem));
+    {
+        int dev = 0, sms = 1, occ = 1, occ_c = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, B->k.step_fn, B->k.threads, B->k.smem) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, B->k.check_fn, B->k.check_threads, 0) != cudaSuccess ||
+            occ_c < 1)
+            occ_c = 1;
+        cudaGetLastError();
+        B->step_grid = std::max(1, std::min(B->max_items, std::max(sms, 1) * occ));
+        B->check_grid = std::max(1, std::min(B->max_items, std::max(sms, 1) * occ_c));
+    }
     std::vector<unsigned> items;
     for (int k = 0; k < B->n; ++k) {
         BatchInst& I = B->di[k];
@@ -259,7 +280,7 @@ lb_status reset_run_state(lb_batch* B) {
 lb_status launch_steps(lb_batch* B, int nsteps) {
     const BatchState bs = state_of(B);
     for (int s = 0; s < nsteps; ++s) {
-        B->k.step(bs, B->buf, B->parity, B->max_items, B->stream);
+        B->k.step(bs, B->buf, B->parity, B->step_grid, B->stream);
         B->parity ^= 1;
     }
     cudaError_t e = cudaGetLastError();
@@ -508,8 +529,8 @@ lb_status lb_batch_run_to_steady(lb_batch* B, double tol, int every, long long m
         cudaError_t e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_err(e, "begin capture");
         const BatchState bs = state_of(B);
-        for (int s = 0; s < every; ++s) B->k.step(bs, B->buf, s & 1, B->max_items, B->stream);
-        B->k.check(bs, B->buf, 0, B->max_items, B->stream);
+        for (int s = 0; s < every; ++s) B->k.step(bs, B->buf, s & 1, B->step_grid, B->stream);
+        B->k.check(bs, B->buf, 0, B->check_grid, B->stream);
         batch_finalize_kernel<<<1, 1024, 0, B->stream>>>(bs, tol, every, min_steps, B->band, B->tol_rho, B->hold,
                                                          B->self_rtol, B->self_tol_rho, B->self_hold);
         e = cudaStreamEndCapture(B->stream, &g);
