@@ -246,8 +246,8 @@ lb_status lb_shape(const lb_ctx* ctx, long long* n_sites, int* q);
  * callers that stage inputs in device memory themselves.  Layout: population
  * 0 as one array of pitch = N rounded up to a multiple of 128 elements, then
  * populations 1..Q-1, each one array of pitch elements; except for D3Q19
- * forcing-scheme contexts with fp16 / bf16 deviation storage and nx a multiple
- * of 32, whose populations 1..18 are interleaved in blocks of 32 sites (the 18
+ * contexts with fp16 / bf16 deviation storage and nx a multiple of 32 (both
+ * schemes), whose populations 1..18 are interleaved in blocks of 32 sites (the 18
  * rows of 32 values of a block contiguous, 1152 bytes; site q in block q/32). */
 lb_status lb_device_state(lb_ctx* ctx, void** dptr, size_t* bytes);
 

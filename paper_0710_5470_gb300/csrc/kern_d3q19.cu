@@ -14,10 +14,14 @@ static LbKernelSet pick(int storage) {
     return LbKernelSet{};
 }
 
-LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet base);   // kern_d3q19_pk.cu
+LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet base);       // kern_d3q19_pk.cu
+LbKernelSet lbk_pk_equilibrium(int storage, int nx, LbKernelSet base);   // kern_d3q19_pk_eq.cu
 
 LbKernelSet lbk_kernels_d3q19(int scheme, int storage, int nx) {
-    if (scheme != 1) return pick<false>(storage);
+    if (scheme != 1) {
+        LbKernelSet k = pick<false>(storage);
+        return storage == 0 ? k : lbk_pk_equilibrium(storage, nx, k);
+    }
     LbKernelSet k = pick<true>(storage);
     return storage == 0 ? k : lbk_pk_forcing(storage, nx, k);
 }

@@ -440,6 +440,7 @@ unsigned long long lbk_bounds_d3q19();
 unsigned long long lbk_bounds_d3pk();
 unsigned long long lbk_bounds_d2q9();
 unsigned long long lbk_bounds_d2pk();
+unsigned long long lbk_bounds_d3pke();
 unsigned long long lbk_bounds_batch();
 
 extern "C" {
@@ -934,7 +935,8 @@ lb_status lb_get_probes(const lb_ctx* c, int* inside, int* outside) {
 lb_status lb_debug_bounds(int* checked, unsigned long long* violation) {
     if (checked) *checked = lbk::kBoundsChecked ? 1 : 0;
     unsigned long long v = 0;
-    for (unsigned long long w : {lbk_bounds_d3pk(), lbk_bounds_d3q19(), lbk_bounds_d2q9(), lbk_bounds_d2pk(), lbk_bounds_batch()})
+    for (unsigned long long w : {lbk_bounds_d3pk(), lbk_bounds_d3pke(), lbk_bounds_d3q19(), lbk_bounds_d2q9(), lbk_bounds_d2pk(),
+                                 lbk_bounds_batch()})
         if (!v) v = w;
     if (violation) *violation = v;
     return LB_OK;

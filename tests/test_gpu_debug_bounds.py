@@ -1,8 +1,8 @@
 """The index-checked build of the library (-DLB_DEBUG_BOUNDS, bounds.cuh).
 
 Every global population access of the fused step kernels - the D3Q19 pair
-kernel in both population layouts, the D3Q19 tile kernel, the D2Q9 tile
-kernel of single lattices and of batches - runs with its site index tested
+kernels of both schemes in both population layouts, the D3Q19 tile kernel,
+the D2Q9 pair and tile kernels of single lattices and of batches - runs with its site index tested
 against the lattice.  On the tiny and ragged grids of the parity tests (tiles
 cut by the lattice edge, lattices narrower than the halo, periodic wraps on
 every face) no access may fall outside, and the checked kernels must give
@@ -26,6 +26,7 @@ CASES = [
     ("D3Q19", "forcing", (68, 20, 12), 2), ("D3Q19", "forcing", (64, 16, 9), 2), ("D3Q19", "forcing", (2, 3, 3), 2),
     ("D3Q19", "forcing", (38, 13, 11), 3), ("D3Q19", "forcing", (96, 20, 7), 3), ("D3Q19", "forcing", (37, 13, 11), 2),
     ("D3Q19", "forcing", (38, 13, 11), 1), ("D3Q19", "equilibrium", (38, 13, 11), 2),
+    ("D3Q19", "equilibrium", (64, 16, 9), 2), ("D3Q19", "equilibrium", (64, 10, 5), 1),
     ("D3Q19", "equilibrium", (2, 5, 3), 1), ("D3Q19", "forcing", (22, 20, 18), 0),
     ("D2Q9", "forcing", (45, 37), 1), ("D2Q9", "forcing", (46, 37), 2), ("D2Q9", "equilibrium", (2, 5), 3),
     ("D2Q9", "equilibrium", (66, 20), 0),

@@ -241,8 +241,8 @@ def test_paired_halo_loads_are_bit_identical(storage, scheme, shape, monkeypatch
     """With an even nx the tile kernel's halo stage loads two adjacent sites
     per access; it must give exactly the one-site form's result (same
     arithmetic, same order), over ragged tiles and a lattice narrower than one
-    pair of halo columns.  (LB_D3_VARIANT=0 selects the tile kernel for the
-    forcing scheme, whose default with 16-bit storage is the pair kernel,
+    pair of halo columns.  (LB_D3_VARIANT=0 selects the tile kernel for both
+    schemes, whose default with 32-bit arithmetic storage is the pair kernel,
     checked against the oracle in test_pair_kernel_parity.)"""
     monkeypatch.setenv("LB_D3_VARIANT", "0")
     lb = library()
@@ -346,3 +346,29 @@ def test_d2q9_pair_and_tile_kernels(shape, scheme, storage, tol_f, monkeypatch):
                 assert ctx.kernel_info()["form"].startswith(form)
             want = O.run(start, m, steps)
             assert rel_inf(got, want) < tol_f * steps, (variant, steps, rel_inf(got, want))
+
+
+@pytest.mark.parametrize("storage,tol_f,tol_rho", [(F16DEV, 1e-5, 1e-5), (BF16DEV, 8e-5, 6e-5), (F32, 2e-6, 2e-6)])
+@pytest.mark.parametrize("shape", [(68, 20, 12), (2, 3, 3), (130, 10, 40), (64, 16, 9), (96, 20, 7), (32, 5, 3),
+                                   (64, 8, 1)])
+def test_equilibrium_pair_kernel_parity(shape, storage, tol_f, tol_rho, monkeypatch):
+    """The D3Q19 equilibrium-scheme pair kernel (two x sites per thread, packed
+    float32 pairs, the M terms of the optimal weights in the collision; the
+    interleaved 16-bit layout when nx is a multiple of 32), one and five steps
+    from the same rounded state as the oracle."""
+    monkeypatch.delenv("LB_D3_VARIANT", raising=False)
+    lb = library()
+    m = oracle_model("D3Q19", "equilibrium")
+    f0 = drop_populations(m, shape, 0.3 * min(shape), perturb=1e-3, seed=7)
+    for steps in (1, 5):
+        with make_ctx(lb, "D3Q19", "equilibrium", shape, storage=storage) as ctx:
+            ctx.set_populations(f0)
+            start = ctx.get_populations()
+            ctx.step(steps)
+            got = ctx.get_populations()
+            rho_g, _, _ = ctx.fields(want_v=False)
+            assert ctx.kernel_info()["form"].startswith("pairs"), ctx.kernel_info()["form"]
+        want = O.run(start, m, steps)
+        rho = want.sum(axis=0)
+        assert rel_inf(got, want) < tol_f * steps, (steps, rel_inf(got, want))
+        assert rel_inf(rho_g, rho) < tol_rho * steps
