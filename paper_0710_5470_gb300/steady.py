@@ -30,6 +30,7 @@ the calls and reads the clock.
   python -m paper_0710_5470_gb300.steady --sweep [--count 256]   (the whole sweep, batched ways only)
   python -m paper_0710_5470_gb300.steady --self-test [--sweep]   (no reference values: self-contained test)
   python -m paper_0710_5470_gb300.steady --throughput [--storage f16dev] [--steps 200]   (batched step rate)
+  python -m paper_0710_5470_gb300.steady --single 2048 [--scheme forcing] [--storage f16dev]   (one lattice)
 """
 from __future__ import annotations
 
@@ -377,6 +378,27 @@ def throughput(storage=lb.F16DEV, steps=200, count=256, seed=0, scheme=lb.FORCIN
             "glups": sites * steps / dt / 1e9}
 
 
+def single_throughput(n=2048, storage=lb.F16DEV, scheme=lb.FORCING, steps=400, warmup=100):
+    """Step rate of one D2Q9 n x n lattice (a centred drop of radius n/4, T =
+    0.55, kappa = 0.01, tau = 1): `steps` steps of one lb_step call after
+    `warmup`, wall clock closed by a synchronisation; best of three.  Returns
+    the kernel form and the rate in GLUPS."""
+    with lb.Context(lb.D2Q9, (n, n), W.A_VDW, W.B_VDW, 0.55, 0.01, 1.0, scheme=scheme, storage=storage) as ctx:
+        ctx.init_drops([(n / 2, n / 2)], [n / 4], 2.0)
+        ctx.step(warmup)
+        ctx.synchronize()
+        best = None
+        for _ in range(3):
+            t0 = time.perf_counter()
+            ctx.step(steps)
+            ctx.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        form = ctx.kernel_info()["form"]
+    return {"n": n, "scheme": "forcing" if scheme == lb.FORCING else "equilibrium", "steps": steps, "form": form,
+            "seconds": best, "glups": n * n * steps / best / 1e9}
+
+
 def main():
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     p.add_argument("--count", type=int, default=None, help="instances (default 16; 256 with --sweep)")
@@ -391,14 +413,21 @@ def main():
                    help="the whole sweep (default 256 instances), one batch per way (sweep())")
     p.add_argument("--throughput", action="store_true",
                    help="batched step rate on the sweep's sizes at stable parameters (throughput())")
-    p.add_argument("--storage", default="f16dev", choices=list(ARMS), help="storage of --throughput")
-    p.add_argument("--steps", type=int, default=200, help="timed steps of --throughput")
+    p.add_argument("--single", type=int, default=0, metavar="N",
+                   help="step rate of one D2Q9 N x N lattice (single_throughput())")
+    p.add_argument("--scheme", default="forcing", choices=["forcing", "equilibrium"], help="scheme of --single")
+    p.add_argument("--storage", default="f16dev", choices=list(ARMS), help="storage of --throughput / --single")
+    p.add_argument("--steps", type=int, default=200, help="timed steps of --throughput / --single")
     a = p.parse_args()
     from . import build
     build.build()
     lb.load_library()
     if a.throughput:
         print(json.dumps(throughput(ARMS[a.storage], a.steps, a.count or 256, a.seed)), flush=True)
+        return
+    if a.single:
+        sch = lb.FORCING if a.scheme == "forcing" else lb.EQUILIBRIUM
+        print(json.dumps(single_throughput(a.single, ARMS[a.storage], sch, a.steps)), flush=True)
         return
     if a.sweep and a.self_test:
         print(json.dumps(sweep_self(a.count or 256, a.seed, a.every, a.max_steps)), flush=True)
