@@ -92,7 +92,7 @@ def kernel_fingerprint() -> str:
 
 
 def bytes_per_lu(storage: str, q: int = 19) -> int:
-    """Algorithmic HBM bytes per lattice update of the survey's roofline: one
+    """Algorithmic HBM bytes per lattice update of the reported roofline: one
     read and one write of every stored population plus one read and one write
     of the density, B = 2 Q s_f + 2 s_rho (s_rho = 4, or 8 for float64):
     88 B for 16-bit deviations (f_0 float32), 160 B float32, 320 B float64."""

@@ -396,7 +396,7 @@ def evaluate3(train_seed=21, train_count=64, train_side=32, held_seed=99, held=(
 def evaluate_plan(train_target=2000, held_count=128, train_side=64, held_side=256, epochs=200,
                   train_seed0=1, held_seed=999, storage=lb.F16DEV, self_test=(5e-4, 1e-5, 10), every=100,
                   max_steps=100000):
-    """The warm start at the scale of the plan: a network trained on
+    """The warm start at full scale: a network trained on
     ``train_target`` solver-made steady states of drops drawn from the sweep
     ranges (T 0.50-0.56, kappa 0.002-0.03, tau 0.6-1.5, R 0.15-0.35 of the box;
     train_side^2 boxes; unstable draws skipped), evaluated on ``held_count``

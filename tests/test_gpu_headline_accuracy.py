@@ -1,10 +1,10 @@
 """Accuracy of the reduced storage formats at the headline workload, against
-the bounds of the plan: D3Q19 128^3, one centred drop R = 30, forcing scheme,
+the stated mixed-precision bounds: D3Q19 128^3, one centred drop R = 30, forcing scheme,
 T = 0.55, kappa = 0.01, tau = 1, 10^4 steps from the tanh start, each format
 compared with the float64 path (which matches the oracle to 1e-12 per step
 on smaller lattices; the oracle itself would need hours here).
 
-Bounds, from the plan: the spurious velocity max|v| (Eq. 40) within 5%, and
+Bounds: the spurious velocity max|v| (Eq. 40) within 5%, and
 rho within 1e-5 relative.  The density bound is tested on two quantities:
 the bulk densities (the extremes of rho, the liquid and vapour values), which
 every format meets, and rho site by site, which no float32 arithmetic meets
@@ -12,7 +12,7 @@ every format meets, and rho site by site, which no float32 arithmetic meets
 jump (~1.3e-3 here), about 500 times smaller than p0 (~0.64), so float32
 rounding of the equation of state (of T, a, b themselves and of p0) moves
 the interface by ~1e-3 of a site, i.e. ~1e-3 in rho at the interface.  Those
-are kept at the plan's number and marked as expected failures; the test also
+are kept at 1e-5 and marked as expected failures; the test also
 checks that the error is not a translation of the drop (the measured drift
 is below 1e-2 sites) and that it does not come from the 16-bit storage (the
 16-bit formats stay within 2x of float32 storage).
@@ -27,7 +27,7 @@ pytestmark = pytest.mark.gpu
 STEPS = 10000
 FORMATS = ("f32", "f16dev", "bf16dev")
 POINTWISE_REASON = ("float32 arithmetic moves the interface: pointwise rho error ~1e-3 (float32 storage "
-                    "included), above the plan's 1e-5")
+                    "included), above the 1e-5 bound")
 
 
 @pytest.fixture(scope="module")

@@ -68,7 +68,7 @@ _SAME = []
                           "bulk densities and spurious velocity differ), which neither the drift nor the topology "
                           "check detects; training is not bitwise repeatable (float32 atomics), so the count varies")
 def test_3d_warm_start_reaches_the_tanh_steady_state_every_time():
-    """The plan's requirement (the solver has the last word): every held-out
+    """The requirement that the solver has the last word: every held-out
     run from the network's start ends in the tanh start's steady state."""
     if not _SAME:
         pytest.skip("needs test_3d_warm_start_is_closer_to_steady_state in the same session")
