@@ -393,7 +393,7 @@ def evaluate3(train_seed=21, train_count=64, train_side=32, held_seed=99, held=(
     return out
 
 
-def evaluate_plan(train_target=2000, held_count=128, train_side=64, held_side=256, epochs=200,
+def evaluate_full(train_target=2000, held_count=128, train_side=64, held_side=256, epochs=200,
                   train_seed0=1, held_seed=999, storage=lb.F16DEV, self_test=(5e-4, 1e-5, 10), every=100,
                   max_steps=100000):
     """The warm start at full scale: a network trained on
@@ -486,4 +486,4 @@ if __name__ == "__main__":
     from . import build
     build.build()
     lb.load_library()
-    print(json.dumps(evaluate_plan() if "plan" in sys.argv else evaluate3()), flush=True)
+    print(json.dumps(evaluate_full() if "full" in sys.argv else evaluate3()), flush=True)
