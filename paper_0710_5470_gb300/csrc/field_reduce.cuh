@@ -6,8 +6,8 @@
 // Quantities, in this order: mass, momentum x / y / z, max|u|, max|v|,
 // min rho, max rho and, when a previous velocity field is given,
 // max |u - u_prev|.  Every block reduces its sites into per-thread partials,
-// folds them as a fixed binary tree and writes NQ partials; a single thread
-// then folds the blocks in block order, so the sums are deterministic.
+// folds them as a fixed binary tree and writes NQ partials; one more block
+// folds those in a fixed order, so the sums are deterministic.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -99,14 +99,19 @@ __global__ void __launch_bounds__(FR_THREADS)
     fr_block<NQ>(acc, partial + (size_t)blockIdx.x * NQ);
 }
 
-// Folds nblocks partials in block order into out[0..NQ).
+// Folds nblocks partials into out[0..NQ): one block of FR_THREADS threads,
+// thread t folding the blocks t*c ... (t+1)*c - 1 in order (c = nblocks /
+// FR_THREADS rounded up), then the fixed tree of fr_block: the same order on
+// every call, so the result is deterministic.
 template <int NQ>
-__global__ void fr_final_kernel(const double* partial, int nblocks, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(FR_THREADS) fr_final_kernel(const double* partial, int nblocks, double* out) {
+    if (blockIdx.x != 0) return;
     double acc[NQ];
     fr_init<NQ>(acc);
-    for (int b = 0; b < nblocks; ++b) fr_merge<NQ>(acc, partial + (size_t)b * NQ);
-    for (int k = 0; k < NQ; ++k) out[k] = acc[k];
+    const int c = (nblocks + FR_THREADS - 1) / FR_THREADS;
+    const int b0 = int(threadIdx.x) * c, b1 = b0 + c < nblocks ? b0 + c : nblocks;
+    for (int b = b0; b < b1; ++b) fr_merge<NQ>(acc, partial + (size_t)b * NQ);
+    fr_block<NQ>(acc, out);
 }
 
 }  // namespace lbk

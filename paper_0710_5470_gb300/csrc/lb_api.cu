@@ -877,7 +877,7 @@ lb_status lb_stats_get(lb_ctx* c, lb_stats* out) {
     double* res = c->w_part + size_t(c->stat_blocks) * lbk::FR_NQ;
     lbk::fr_partial_kernel<lbk::FR_NQ><<<c->stat_blocks, lbk::FR_THREADS, 0, c->stream>>>(
         c->w_rho, c->w_u, c->w_v, c->uprev_valid ? c->w_uprev : nullptr, c->D, (long long)c->N, 0, part);
-    lbk::fr_final_kernel<lbk::FR_NQ><<<1, 32, 0, c->stream>>>(part, c->stat_blocks, res);
+    lbk::fr_final_kernel<lbk::FR_NQ><<<1, lbk::FR_THREADS, 0, c->stream>>>(part, c->stat_blocks, res);
     double h[lbk::FR_NQ], rp[2];
     const size_t in = (size_t(c->probe_in[2]) * c->p.ny + c->probe_in[1]) * c->p.nx + c->probe_in[0];
     const size_t ou = (size_t(c->probe_out[2]) * c->p.ny + c->probe_out[1]) * c->p.nx + c->probe_out[0];

@@ -75,7 +75,7 @@ lb_status lb_field_stats_noalloc(const double* rho, const double* u, const doubl
     // one block per contiguous chunk of SITES_PER_BLOCK sites, folded in block order
     lbk::fr_partial_kernel<NSTAT><<<nblocks, lbk::FR_THREADS, 0, st>>>(rho, u, v, nullptr, dim, n, SITES_PER_BLOCK,
                                                                       partial);
-    lbk::fr_final_kernel<NSTAT><<<1, 32, 0, st>>>(partial, nblocks, out);
+    lbk::fr_final_kernel<NSTAT><<<1, lbk::FR_THREADS, 0, st>>>(partial, nblocks, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LB_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     return LB_OK;
