@@ -137,6 +137,7 @@ struct lb_batch {
     std::vector<lb_instance> inst;
     std::vector<BatchInst> di;        // host copy of the device table
     std::vector<double> rho_l, rho_g;
+    std::vector<double> pref64;   // per instance: p0(rho_l) in float64 (fref_i = w_i pref, rounded once)
     long long sites = 0, max_sites = 0;
     size_t state_bytes = 0;           // bytes of one state (all instances, one buffer)
     cudaStream_t stream = nullptr;
@@ -196,7 +197,7 @@ PopPtrs pops_of(lb_batch* B, int k, int parity) {
     PopPtrs p{};
     const BatchInst& I = B->di[k];
     char* base = B->buf + I.off[parity];
-    double pref = I.pref;
+    const double pref = B->pref64[k];
     for (int i = 0; i < 9; ++i) {
         const long long o = i == 0 ? 0 : I.pitch * elem0(B->storage) + (i - 1) * I.pitch * elemi(B->storage);
         p.p[i] = base + o;
@@ -308,6 +309,7 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
     B->inst.assign(inst, inst + n);
     B->di.resize(n);
     B->rho_l.resize(n);
+    B->pref64.assign(n, 0.0);
     B->rho_g.resize(n);
     long long off = 0;
     long long max_items = 0;
@@ -348,8 +350,13 @@ lb_status lb_batch_create(int scheme, int storage, double a, double b, int n, co
         I.fnu = float(I.nu);
         const double rl = B->rho_l[k];
         const double pref = (storage == LB_F16DEV || storage == LB_BF16DEV) ? rl * in.T / (1 - b * rl) - a * rl * rl : 0.0;
+        // sum_{i>=1} w_i (5/3 on D2Q9), summed in velocity order like a single
+        // context does, so that the float32 rsum is the same bit for bit
+        double wsum = 0.0;
+        for (int i = 1; i < D2Q9::Q; ++i) wsum += w_vel<D2Q9>(i);
+        B->pref64[k] = pref;
         I.pref = float(pref);
-        I.rsum = float(pref * (5.0 / 3.0));   // sum_{i>=1} w_i = 4/3 + 1/3 on D2Q9
+        I.rsum = float(pref * wsum);
         int most = 0;   // largest tile count over the tile variants (smallest tile: 32x8)
         most = int(((in.nx + 31) / 32) * ((in.ny + 7) / 8));
         max_items += most;

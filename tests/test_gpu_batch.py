@@ -85,19 +85,26 @@ def test_unstable_instance_is_retired_alone():
     assert status[0] == 0 and status[1] == 4
 
 
-@pytest.mark.parametrize("storage", [1, 2])
-def test_reduced_storage_batch_matches_single_context(storage):
+@pytest.mark.parametrize("scheme", ["forcing", "equilibrium"])
+@pytest.mark.parametrize("storage", [1, 2, 3])
+def test_reduced_storage_batch_matches_single_context(storage, scheme):
+    """With 32-bit arithmetic a batch runs the pair kernel on every instance,
+    aligned pairs for an even nx (40, 64) and site-by-site pairs for an odd nx
+    (19), with the single-lattice contexts' 32 x 8 tile: bit for bit the
+    single contexts' results."""
     lb = library()
-    with lb.Batch(INST, A_VDW, B_VDW, scheme=1, storage=storage) as bt:
+    sch = 0 if scheme == "equilibrium" else 1
+    with lb.Batch(INST, A_VDW, B_VDW, scheme=sch, storage=storage) as bt:
         bt.init_drops(2.0)
         bt.step(20)
-        got = bt.populations(0)
-    d = INST[0]
-    with make_ctx(lb, "D2Q9", "forcing", (d["nx"], d["ny"]), storage=storage, T=d["T"], kappa=d["kappa"],
-                  tau=d["tau"]) as ctx:
-        ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
-        ctx.step(20)
-        assert np.array_equal(ctx.get_populations(), got)
+        got = [bt.populations(k) for k in range(len(INST))]
+    for k, d in enumerate(INST):
+        with make_ctx(lb, "D2Q9", scheme, (d["nx"], d["ny"]), storage=storage, T=d["T"], kappa=d["kappa"],
+                      tau=d["tau"]) as ctx:
+            ctx.init_drops([(d["nx"] / 2, d["ny"] / 2)], [d["radius"]])
+            ctx.step(20)
+            assert ctx.kernel_info()["form"].startswith("pairs")
+            assert np.array_equal(ctx.get_populations(), got[k]), k
 
 
 def test_reference_test_stops_reduced_storage_at_float64_accuracy():
