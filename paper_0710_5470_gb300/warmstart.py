@@ -480,10 +480,56 @@ def evaluate_full(train_target=2000, held_count=128, train_side=64, held_side=25
             "runs": rows}
 
 
+def steady_parameter_bound(sets=((48, 16, 11), (96, 16, 12)), tol=1e-9, every=100, max_steps=100000) -> dict:
+    """What a start can gain that knows the steady bulk densities and radius
+    exactly: for held-out drops (the warm start's ranges; side, count, seed
+    per set), the steps to the float64 test from the tanh start of the
+    coexistence densities and initial radius, against the steps from a tanh
+    profile (width 2) with the run's own steady bulk densities (centre and
+    corner site) and equimolar radius, scaled to the start's mass.  A ratio
+    near 1 means the steps are spent settling the interface profile and the
+    flow, not the radius or the bulk densities."""
+    import math
+    from . import inputs
+    out = []
+    for side, count, seed in sets:
+        sw = inputs.sweep_instances(seed=seed, count=count, side=(side, side), T=(0.53, 0.56),
+                                    kappa=(0.005, 0.015), tau=(0.7, 1.2), rfrac=(0.2, 0.35))
+        inst = instances_from_sweep(sw)
+        s_t, st_t, f_t = steps_to_steady(inst, None, tol=tol, every=every, max_steps=max_steps)
+        y, x = np.mgrid[0:side, 0:side]
+        dx = np.minimum(np.abs(x - side / 2), side - np.abs(x - side / 2))
+        dy = np.minimum(np.abs(y - side / 2), side - np.abs(y - side / 2))
+        dist = np.hypot(dx, dy)
+        with lb.Batch(inst, A_VDW, B_VDW, scheme=lb.FORCING, storage=lb.F64) as bt:
+            bt.init_drops(2.0)
+            for k in range(count):
+                rho = f_t[k][0].reshape(side, side)
+                rl, rg = float(rho[side // 2, side // 2]), float(rho[0, 0])
+                R = math.sqrt((float(rho.sum()) - rg * side * side) / (rl - rg) / math.pi)
+                start = rg + (rl - rg) * 0.5 * (1 + np.tanh((R - dist) / 2.0))
+                r0 = bt.fields(k)[0]
+                start = start * (float(r0.sum()) / float(start.sum()))
+                bt.init_fields(k, start.reshape(r0.shape), np.zeros((2,) + r0.shape))
+            bt.autotune(5)
+            s_p, st_p, _ = bt.run_to_steady(tol=tol, every=every, max_steps=max_steps)
+        ok = [k for k in range(count) if st_t[k] == 0 and st_p[k] == 0]
+        out.append({"side": side, "count": count, "converged_both": len(ok),
+                    "steps_tanh": [int(s_t[k]) for k in ok], "steps_steady_parameters": [int(s_p[k]) for k in ok],
+                    "ratio": float(np.sum([s_p[k] for k in ok]) / max(1, np.sum([s_t[k] for k in ok])))})
+    return {"tol": tol, "every": every, "sets": out}
+
+
 if __name__ == "__main__":
     import json
     import sys
     from . import build
     build.build()
     lb.load_library()
-    print(json.dumps(evaluate_full() if "full" in sys.argv else evaluate3()), flush=True)
+    if "full" in sys.argv:
+        res = evaluate_full()
+    elif "bound" in sys.argv:
+        res = steady_parameter_bound()
+    else:
+        res = evaluate3()
+    print(json.dumps(res), flush=True)
