@@ -20,7 +20,9 @@ F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
     ("D3Q19", "forcing", (64, 20, 12)),     # interleaved 16-bit layout (nx a multiple of 32)
     ("D3Q19", "forcing", (38, 13, 11)),     # one array per population
     ("D3Q19", "equilibrium", (38, 13, 11)),
+    ("D3Q19", "equilibrium", (64, 16, 9)),  # the equilibrium pair kernel, interleaved 16-bit layout
     ("D2Q9", "forcing", (46, 37)),
+    ("D2Q9", "equilibrium", (45, 37)),      # odd nx: the pair kernel site by site
 ])
 def test_restart_is_bit_exact(lat, scheme, shape, storage):
     lb = library()
