@@ -40,10 +40,10 @@ KERNEL_SOURCES = ["step3d.cuh", "step3d_pk.cuh", "kern_d3q19_pk.cu", "step_kerne
 # fingerprint of the kernel sources they were measured on and the storage.
 # A changed kernel has a new fingerprint and reports traffic = null.
 NCU_TRAFFIC = {
-    ("2b86a63b5b5f", "f16dev", 128): 143.34e6,   # 103.33 MB read + 40.01 MB written (pair kernel)
-    ("2b86a63b5b5f", "bf16dev", 128): 143.34e6,  # 103.31 MB read + 40.03 MB written (pair kernel)
-    ("2b86a63b5b5f", "f32", 128): 303.37e6,      # 190.54 MB read + 112.83 MB written (tile kernel)
-    ("2b86a63b5b5f", "f64", 128): 637.07e6,      # 357.14 MB read + 279.93 MB written (tile kernel)
+    ("412489fce235", "f16dev", 128): 142.85e6,   # 103.35 MB read + 39.50 MB written (pair kernel)
+    ("412489fce235", "bf16dev", 128): 143.09e6,  # 103.39 MB read + 39.70 MB written (pair kernel)
+    ("412489fce235", "f32", 128): 301.60e6,      # 188.75 MB read + 112.85 MB written (pair kernel, 2 CTAs per SM)
+    ("412489fce235", "f64", 128): 637.11e6,      # 357.07 MB read + 280.05 MB written (tile kernel)
 }
 
 # Executed floating-point operations per lattice update of the step kernel,
@@ -54,14 +54,15 @@ NCU_TRAFFIC = {
 # FP units do, not an algorithmic minimum.
 NCU_FLOPS = {
     # pair kernel: FFMA 10.8, FADD 64.3, FMUL 20.6, FADD2 36.6, FFMA2 43.9, FMUL2 29.9, FHADD 75.2 per site
-    ("2b86a63b5b5f", "f16dev", 128): 490.5,
-    ("2b86a63b5b5f", "f32", 128): 484.2,       # tile kernel: FFMA 114.5, FADD 149.3, FMUL 67.6, FADD2 19.1
-    ("2b86a63b5b5f", "f64", 128): 525.6,       # tile kernel: DFMA 129.0, DADD 197.4, DMUL 70.2
+    ("412489fce235", "f16dev", 128): 490.5,
+    # float32 pair kernel: FFMA 10.3, FADD 61.5, FMUL 17.8, FADD2 64.8, FFMA2 43.5, FMUL2 29.6
+    ("412489fce235", "f32", 128): 462.7,
+    ("412489fce235", "f64", 128): 525.6,       # tile kernel: DFMA 129.0, DADD 197.4, DMUL 70.2
 }
 # FP64-pipe instructions per lattice update of the float64 step (DFMA, DADD,
 # DMUL, DSETP, F2F): each occupies the pipe like one FMA, so their rate against
 # half the FMA flop rate is the pipe's utilisation.
-NCU_FP64_PIPE_OPS = {("2b86a63b5b5f", "f64", 128): 401.7}
+NCU_FP64_PIPE_OPS = {("412489fce235", "f64", 128): 401.7}
 
 
 def alu_roofline(fp: str, storage: str, n: int, glups: float, fma: dict | None):

@@ -38,12 +38,12 @@ struct PKLaunch {
 }  // namespace
 
 // The pair kernel for the forcing scheme with 16-bit deviation storage
-// (storage 2, 3) in place of `step` of `base` (an even nx is required;
-// base.step1, one site per thread, stays the fallback).  float32 storage keeps
-// the one-site-per-thread tile kernel (measured faster for it on GB300: the
-// float32 stash of a pair does not fit three CTAs per SM).  LB_D3_VARIANT
-// selects another tile / prefetch form of the pair kernel for measurements;
-// LB_D3_VARIANT=0 keeps the tile kernel.
+// (storage 2, 3), and with float32 storage at two CTAs per SM (its 82 KB of
+// shared memory do not fit three; measured on GB300 at 128^3 / 256^3 / 512^3:
+// 22.6 / 23.0 / 24.9 GLUPS against 19.9 / 21.2 / 22.5 for the tile kernel), in
+// place of `step` of `base` (an even nx is required; base.step1, one site per
+// thread, stays the fallback).  LB_D3_VARIANT selects another tile / prefetch
+// form of the pair kernel for measurements; LB_D3_VARIANT=0 keeps the tile kernel.
 LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet k) {
     const char* env = std::getenv("LB_D3_VARIANT");
     const int v = env ? std::atoi(env) : -1;
@@ -82,8 +82,10 @@ LbKernelSet lbk_pk_forcing(int storage, int nx, LbKernelSet k) {
     } else if (storage == 3) {
         if (aos) PKLaunch<StBF16, 32, 8, 3, 2, true, true, true>::apply(k, "pairs 32x8, interleaved blocks, prefetch all");
         else PKLaunch<StBF16, 32, 8, 3, 1, true>::apply(k, "pairs 32x8, 3 CTAs per SM, own pair prefetched");
-    } else if (storage == 1 && v > 0) {
-        PKLaunch<StF32, 32, 8, 2, 0, false>::apply(k, "pairs 32x8");
+    } else if (storage == 1) {
+        if (v == 71) PKLaunch<StF32, 32, 8, 2, 1, false, false, true>::apply(k, "pairs 32x8, own pair prefetched");
+        else if (v > 0 && v != 70) PKLaunch<StF32, 32, 8, 2, 0, false>::apply(k, "pairs 32x8");
+        else PKLaunch<StF32, 32, 8, 2, 2, false, false, true>::apply(k, "pairs 32x8, prefetch all");
     }
     return k;
 }
