@@ -122,6 +122,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-steady", action="store_true")
+    p.add_argument("--oracle-table", action="store_true",
+                   help="only time the FP64 oracle on the paper-shaped workloads (one core, all cores) and exit")
     p.add_argument("--scheme", default="forcing", choices=["forcing", "equilibrium"],
                    help="collision scheme (the headline workload is the forcing scheme)")
     return p.parse_args()
@@ -254,6 +256,80 @@ def cpu_model() -> str:
     except OSError:
         pass
     return "unknown"
+
+
+# oracle timing table: workload name -> (lattice, shape (nz, ny, nx), scheme, T, kappa, tau, drops, steps, warm-up)
+ORACLE_TABLE = {
+    "D2Q9 64^2, one drop R=16, equilibrium scheme, T=0.55, kappa=0.01, tau=1": ("D2Q9", (1, 64, 64), "equilibrium",
+                                                                               0.55, 0.01, 1.0, "centre16", 200, 10),
+    "D2Q9 512^2, drops of random_drops(0), forcing scheme, T=0.55, kappa=0.01, tau=0.8": (
+        "D2Q9", (1, 512, 512), "forcing", 0.55, 0.01, 0.8, "random0", 20, 2),
+    "D2Q9 512^2, drops of random_drops(0), equilibrium scheme, T=0.55, kappa=0.01, tau=0.8": (
+        "D2Q9", (1, 512, 512), "equilibrium", 0.55, 0.01, 0.8, "random0", 20, 2),
+    # the 128^3 workload scaled to 64^3 (R = 15): bounded host memory with one copy per core
+    "D3Q19 64^3, one drop R=15, forcing scheme, T=0.55, kappa=0.01, tau=1": ("D3Q19", (64, 64, 64), "forcing",
+                                                                             0.55, 0.01, 1.0, "centre15", 10, 1),
+}
+
+
+def _oracle_table_worker(job):
+    """Time one oracle configuration of ORACLE_TABLE (one process, one thread):
+    warm-up steps, wait for the others, timed steps."""
+    name, bar = job
+    lat, shape, scheme, T, kappa, tau, drops, steps, warm = ORACLE_TABLE[name]
+    from oracle import lb_oracle as O
+    from paper_0710_5470_gb300 import inputs
+    m = O.Model(lat, A_VDW, B_VDW, T, kappa, tau, scheme=scheme)
+    rl, rg = O.coexistence(A_VDW, B_VDW, T)
+    nz, ny, nx = shape
+    if drops == "random0":
+        centres, radii, _ = inputs.random_drops(0, (nx, ny))
+    elif lat == "D2Q9":
+        centres, radii = [(nx / 2, ny / 2)], [float(drops[6:])]
+    else:
+        centres, radii = [(nx / 2, ny / 2, nz / 2)], [float(drops[6:])]
+    rho0 = O.drop_density(shape, centres, radii, rl, rg, 2.0)
+    f = O.init_equilibrium(rho0, m)
+    for _ in range(warm):
+        f = O.step(f, m)
+    if bar is not None:
+        bar.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = O.step(f, m)
+    dt = time.perf_counter() - t0
+    return nx * ny * nz * steps / dt / 1e6
+
+
+def oracle_table() -> dict:
+    """The FP64 oracle's step rate (MLUPS) on the paper-shaped workloads, on one
+    host core and on every host core at once (one single-threaded process per
+    core, each on its own copy of the workload; the larger copies are bounded to
+    a few steps each)."""
+    import multiprocessing as mp
+    procs = len(os.sched_getaffinity(0))
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in keep:
+        os.environ[k] = "1"
+    out = {"cpu": cpu_model(), "cores": procs, "rows": {}}
+    try:
+        ctx = mp.get_context("spawn")
+        for name in ORACLE_TABLE:
+            one = _oracle_table_worker((name, None))
+            with ctx.Manager() as man:
+                bar = man.Barrier(procs)
+                with ctx.Pool(procs) as pool:
+                    rates = pool.map(_oracle_table_worker, [(name, bar)] * procs)
+            lat, shape, scheme, T, kappa, tau, drops, steps, warm = ORACLE_TABLE[name]
+            out["rows"][name] = {"one_core_mlups": one, "all_cores_mlups": float(sum(rates)),
+                                 "cores": procs, "steps": steps, "warmup": warm}
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return out
 
 
 def _oracle_worker(job):
@@ -547,6 +623,9 @@ def run_native(args):
 
 def main():
     args = parse()
+    if args.oracle_table:
+        print(json.dumps(oracle_table()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
