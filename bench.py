@@ -273,10 +273,10 @@ ORACLE_TABLE = {
 
 
 def _oracle_table_worker(job):
-    """Time one oracle configuration of ORACLE_TABLE (one process, one thread):
-    warm-up steps, wait for the others, timed steps."""
-    name, bar = job
-    lat, shape, scheme, T, kappa, tau, drops, steps, warm = ORACLE_TABLE[name]
+    """Time one oracle configuration (a value of ORACLE_TABLE; one process, one
+    thread): warm-up steps, wait for the others, timed steps."""
+    cfg, bar = job
+    lat, shape, scheme, T, kappa, tau, drops, steps, warm = cfg
     from oracle import lb_oracle as O
     from paper_0710_5470_gb300 import inputs
     m = O.Model(lat, A_VDW, B_VDW, T, kappa, tau, scheme=scheme)
@@ -314,13 +314,13 @@ def oracle_table() -> dict:
     out = {"cpu": cpu_model(), "cores": procs, "rows": {}}
     try:
         ctx = mp.get_context("spawn")
-        for name in ORACLE_TABLE:
-            one = _oracle_table_worker((name, None))
+        for name, cfg in ORACLE_TABLE.items():
+            one = _oracle_table_worker((cfg, None))
             with ctx.Manager() as man:
                 bar = man.Barrier(procs)
                 with ctx.Pool(procs) as pool:
-                    rates = pool.map(_oracle_table_worker, [(name, bar)] * procs)
-            lat, shape, scheme, T, kappa, tau, drops, steps, warm = ORACLE_TABLE[name]
+                    rates = pool.map(_oracle_table_worker, [(cfg, bar)] * procs)
+            steps, warm = cfg[7], cfg[8]
             out["rows"][name] = {"one_core_mlups": one, "all_cores_mlups": float(sum(rates)),
                                  "cores": procs, "steps": steps, "warmup": warm}
     finally:

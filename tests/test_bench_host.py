@@ -49,3 +49,18 @@ def test_alu_roofline_arithmetic():
         d["fp64_pipe_ops_per_lu"] * 1.115e9 / (1.25e12 / 2))
     assert bench.alu_roofline(fp, "f16dev", 128, 27.0, None) is None
     assert bench.alu_roofline("0" * 12, "f16dev", 128, 27.0, fma) is None
+
+
+def test_oracle_table_on_tiny_workloads(monkeypatch):
+    """bench.py --oracle-table logic on the host: every row timed on one core
+    and on every core (spawned single-threaded processes), positive rates."""
+    import bench
+    monkeypatch.setattr(bench, "ORACLE_TABLE", {
+        "tiny 2D": ("D2Q9", (1, 12, 10), "equilibrium", 0.55, 0.01, 1.0, "centre3", 2, 1),
+        "tiny 3D": ("D3Q19", (6, 6, 8), "forcing", 0.55, 0.01, 1.0, "centre2", 1, 0),
+    })
+    monkeypatch.setattr(bench.os, "sched_getaffinity", lambda pid: {0, 1})
+    res = bench.oracle_table()
+    assert res["cores"] == 2 and set(res["rows"]) == {"tiny 2D", "tiny 3D"}
+    for row in res["rows"].values():
+        assert row["one_core_mlups"] > 0 and row["all_cores_mlups"] > 0 and row["cores"] == 2
