@@ -435,6 +435,59 @@ def make_ctx(lb, storage: str, n: int, stream, scheme: str = "forcing"):
     return ctx, R
 
 
+BINARY = {"n": 2048, "R": 512.0, "A": -0.04, "B": 0.04, "kappa": 0.08, "Gamma": 1.0, "tau": 1.0, "tau_phi": 1.0}
+
+
+def binary_block(lb, stream, peak, dist, world, warmup, cpu: bool):
+    """D2Q9 binary fluid, one drop of phase +phi* (R = n/4, tanh profile of
+    width w = sqrt(-2 kappa / A)) in -phi*, rho = 1: GLUPS of the fused step in
+    float32 and float64 storage, both schemes, against the HBM roofline at the
+    bytes it moves (18 populations read and written: 144 / 288 B per update)."""
+    import numpy as np
+    b = BINARY
+    n = b["n"]
+    w = np.sqrt(-2 * b["kappa"] / b["A"])
+    y, x = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
+    d = np.hypot(np.minimum(np.abs(x - n / 2), n - np.abs(x - n / 2)), np.minimum(np.abs(y - n / 2), n - np.abs(y - n / 2)))
+    phi0 = -1.0 + 2.0 * 0.5 * (1 + np.tanh((b["R"] - d) / w))
+    out = {"workload": f"D2Q9 {n}^2 periodic, one drop R={b['R']:g} of phi=+1 in phi=-1 (tanh, width "
+                       f"{w:g}), rho=1, A={b['A']}, B={b['B']}, kappa={b['kappa']}, Gamma={b['Gamma']}, "
+                       f"tau=tau_phi=1", "runs": {}}
+    for scheme in ("forcing", "equilibrium"):
+        for sname, st_code, bpl, steps in (("f32", lb.F32, 144, 400), ("f64", lb.F64, 288, 100)):
+            ctx = lb.BinaryContext((n, n), b["A"], b["B"], b["kappa"], b["Gamma"], b["tau"], b["tau_phi"],
+                                   scheme=lb.FORCING if scheme == "forcing" else lb.EQUILIBRIUM, storage=st_code,
+                                   stream=stream.cuda_stream)
+            ctx.init_fields(np.ones((n, n)), phi0)
+            ctx.step(max(warmup, 64))
+            ctx.synchronize()
+            ms = reduce_max(dist, time_steps(ctx, stream, steps, dist))
+            stt = ctx.stats()
+            ctx.close()
+            t = ms / steps / 1e3
+            ach = bpl * n * n / t / 1e9
+            out["runs"][f"{scheme}_{sname}"] = {
+                "value": n * n * steps * world / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
+                "ms_per_step": ms / steps,
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                             "bytes_per_lu": bpl},
+                "max_v": stt["max_v"], "status": stt["status"]}
+    if cpu:
+        from oracle import binary_oracle as BO
+        m = BO.BinaryModel("D2Q9", b["A"], b["B"], b["kappa"], b["Gamma"], b["tau"], b["tau_phi"], scheme="forcing")
+        ns = 512
+        ys, xs = np.meshgrid(np.arange(ns, dtype=np.float64), np.arange(ns, dtype=np.float64), indexing="ij")
+        ds = np.hypot(xs - ns / 2, ys - ns / 2)
+        f, g = BO.init_equilibrium(np.ones((1, ns, ns)), (-1.0 + (1 + np.tanh((ns / 4 - ds) / w)))[None], m)
+        t0 = time.perf_counter()
+        BO.run(f, g, m, 3)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ns * ns * 3 / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                               "sample": f"3 FP64 binary-oracle steps (numpy, one thread), forcing scheme, the "
+                                         f"workload scaled to {ns}^2 ({dt:.1f} s)"}
+    return out
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -547,6 +600,12 @@ def run_native(args):
                                                 "frac": each / peak, "bytes_per_lu": eb},
                                    "max_u": est["max_u"]}
 
+    # the binary-fluid model (the paper's construction carried over to an order
+    # parameter, Sec. I): D2Q9 fused step, both storage formats, forcing scheme
+    binary = None
+    if not args.no_variants:
+        binary = binary_block(lb, stream, peak, dist, world, args.warmup, not args.no_cpu_baseline and rank == 0)
+
     # time to steady state (second half of the metric): plain float64, one
     # instance per launch, to max|u(t) - u(t - 100)| < 1e-10, against one batch
     # in fp16-deviation storage stopped by its own self-contained test (max|u|
@@ -613,6 +672,7 @@ def run_native(args):
             "clocks": clk,
             "variants": variants,
             "equilibrium_scheme": other_scheme or None,
+            "binary_fluid": binary,
             "time_to_steady": tts,
             "check": {"max_v": st["max_v"], "mass": st["mass"], "status": st["status"]},
         }

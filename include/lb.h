@@ -453,6 +453,82 @@ lb_status lb_work_list(int sms, int ctas_per_sm, int nx, int ny, int nz, int til
  * launch runs for milliseconds (float64 ~4000, float32 ~2e5 on a GB300). */
 lb_status lb_fma_peak(int precision, int iters, double* tflops);
 
+/* ---- Binary fluid (D2Q9) --------------------------------------------------
+ *
+ * The paper states (Sec. I) that its analysis applies equally to other
+ * multiphase systems solved by the free-energy method, binary fluids among
+ * them, and prints no equations for them.  This context runs the reading
+ * that carries the liquid-gas construction over to a symmetric binary fluid
+ * with an order parameter phi (the conserved concentration difference):
+ *   free energy   psi = rho/3 ln rho + A/2 phi^2 + B/4 phi^4 + kappa/2 |grad phi|^2
+ *                 (A < 0 < B: bulk phases phi = +-sqrt(-A/B));
+ *   mu            = A phi + B phi^3 - kappa lap(phi);
+ *   p0            = rho/3 + A/2 phi^2 + 3B/4 phi^4;
+ *   f^eq          Eqs. 5, 6 with this p0, w^t kappa phi lap(phi) and
+ *                 w^ab kappa d_a phi d_b phi (optimum weights of Sec. VIII),
+ *                 lambda = 0 (c_s^2 = dp0/drho = 1/3);
+ *   g^eq          sum g = phi, sum g e = phi u, sum g e_a e_b = Gamma mu d_ab
+ *                 + phi u_a u_b, from the same weights (w^p for the mu term);
+ *   relaxation    f with tau (BGK, Eq. 4), g with tau_phi (mobility
+ *                 Gamma (tau_phi - 1/2)), both pushed to r + e_i;
+ *   forcing       (LB_SCHEME_FORCING, Sec. VI) the M terms leave f^eq and act
+ *                 as the body force of Eq. 28 with M_ab = kappa d_a phi d_b phi,
+ *                 F_i of Eq. 27, and g^eq takes the fluid velocity
+ *                 v = u + g/(2 rho) of Eq. 40 in place of u.
+ * Stencils: the gradient and Laplacian of phi by Eqs. 10 and 11 at the
+ * optimum (B = 1/12, D = 1/6), the force stencil with F = 1/12.
+ * Storage: LB_F64 (float64 arithmetic) or LB_F32 (float32 arithmetic).
+ * Populations exchanged with the host: float64 [i][y][x] for f and for g,
+ * i in the paper's D2Q9 order, after streaming.  Conventions otherwise as
+ * above (caller-owned host arrays, status codes, sticky device errors). */
+typedef struct lb_binary lb_binary;
+
+typedef struct {
+    int nx, ny;           /* sites per direction, >= 1 (periodic) */
+    double A, B;          /* free-energy coefficients: A < 0 < B */
+    double kappa;         /* gradient coefficient, >= 0 */
+    double Gamma;         /* mobility coefficient of g^eq, > 0 */
+    double tau;           /* relaxation time of f, > 1/2 */
+    double tau_phi;       /* relaxation time of g, > 1/2 */
+    int scheme;           /* lb_scheme */
+    int storage;          /* LB_F64 or LB_F32 */
+} lb_binary_params;
+
+typedef struct {
+    double mass;          /* sum rho */
+    double phi_total;     /* sum phi */
+    double momentum[2];   /* sum rho u */
+    double max_u;         /* max |u| (Eq. 3) */
+    double max_v;         /* max |v| (Eq. 40 in the forcing scheme; = max_u otherwise) */
+    double min_phi, max_phi;
+    long long step;       /* steps taken since the last initialisation */
+    int status;           /* 0, or LB_EUNSTABLE once a density became non-finite or non-positive */
+} lb_binary_stats;
+
+/* Creates a context: validates the parameters (LB_EINVAL), allocates two
+ * population sets (f and g, double-buffered) on the device and returns it in
+ * *out.  stream: the cudaStream_t to queue work on (NULL = the legacy default
+ * stream); graphs of 64 steps are captured on a private stream and launched
+ * on it. */
+lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** out);
+lb_status lb_binary_destroy(lb_binary* ctx);
+/* f = f^eq, g = g^eq of host fields rho [N], phi [N] and u [2][N] (NULL: u = 0),
+ * stencils of phi taken on the device (the oracle's initial state); resets the
+ * step counter.  rho must be positive and finite (LB_EINVAL otherwise). */
+lb_status lb_binary_init_fields(lb_binary* ctx, const double* rho, const double* phi, const double* u);
+/* Replaces / reads the populations: host f [9][N] and g [9][N], float64 (rounded
+ * to float32 for LB_F32 storage).  set resets the step counter. */
+lb_status lb_binary_set_populations(lb_binary* ctx, const double* f, const double* g);
+lb_status lb_binary_get_populations(lb_binary* ctx, double* f, double* g);
+/* nsteps fused steps (one kernel launch each; CUDA-graph replay on long runs). */
+lb_status lb_binary_step(lb_binary* ctx, int nsteps);
+lb_status lb_binary_synchronize(lb_binary* ctx);
+/* Host float64 fields of the current state; any pointer may be NULL.
+ * rho [N], phi [N], u [2][N] (Eq. 3), v [2][N] (Eq. 40; = u in the equilibrium
+ * scheme), mu [N]. */
+lb_status lb_binary_fields(lb_binary* ctx, double* rho, double* phi, double* u, double* v, double* mu);
+lb_status lb_binary_stats_get(lb_binary* ctx, lb_binary_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,758 @@
+// Binary-fluid free-energy lattice Boltzmann on D2Q9: the liquid-gas
+// construction of Pooley & Furtado (Secs. II-VI) carried over to a symmetric
+// binary fluid with an order parameter phi, as the paper says it applies
+// (Sec. I).  The model (free energy, mu, p0, f^eq, g^eq, forcing) is stated
+// in include/lb.h beside lb_binary_params.
+//
+// One fused kernel per time step.  A CTA owns a 32 x 8 tile, one site per
+// thread:
+//   stage A  the tile's f_i and g_i (18 loads per site, kept in registers)
+//            and phi = sum_i g_i on the tile plus a halo (1 site for the
+//            equilibrium scheme, 2 for the forcing scheme: Eq. 28 takes
+//            differences of M' at the neighbours), halo sites reading g only;
+//   stage B  (forcing) M'_xx - M'_yy and M'_xy on the tile plus one ring;
+//            the gradient (Eq. 10) and Laplacian (Eq. 11) of phi at each site;
+//   stage C  rho, u (Eq. 3), mu, p0, f^eq (Eqs. 5, 6), body force (Eq. 28)
+//            and F_i (Eq. 27), v (Eq. 40), g^eq, both BGK relaxations and the
+//            push of f*_i and g*_i to r + e_i in the other buffer.
+// HBM traffic: one read and one write of the 18 populations per site
+// (288 B per lattice update in float64, 144 B in float32); the halo sites'
+// g are re-read by neighbouring CTAs from L2.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lb.h"
+#include "lattice.cuh"
+
+// Sets the thread-local message returned by lb_last_error (defined in lb_api.cu).
+void lb_internal_set_error(const char* msg);
+
+namespace lbb {
+
+using lbk::D2Q9;
+using lbk::static_for;
+
+constexpr int Q = 9;
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int GRAPH_STEPS = 64;   // steps per captured graph (even: a replay ends in its start buffer)
+
+// Periodic wrap of an offset coordinate: one compare-and-add for v in
+// [-n, 2n), the integer modulo otherwise (lattices narrower than a tile).
+__host__ __device__ __forceinline__ int wrapc(int v, int n) {
+    if (v < 0) v += n;
+    else if (v >= n) v -= n;
+    if (unsigned(v) >= unsigned(n)) {
+        v %= n;
+        if (v < 0) v += n;
+    }
+    return v;
+}
+
+template <class real>
+struct StepArgs {
+    const real* src;     // populations after streaming: f_0..f_8 then g_0..g_8, each `pitch` elements
+    real* dst;
+    long long pitch;
+    int nx, ny;
+    real A, B, kappa, Gamma, omega, omega_phi;   // omega = 1/tau, omega_phi = 1/tau_phi
+    unsigned* status;
+};
+
+// Weights of the optimum (Sec. VIII): w_i = w^p_i = w^t_i, and w^ab_i.
+template <int I>
+__device__ __forceinline__ constexpr double W() { return lbk::w_vel<D2Q9>(I); }
+
+// Gradient (Eq. 10, A = 1/3, B = 1/12) and Laplacian (Eq. 11, C = 2/3,
+// D = 1/6) of a field on a row-major shared-memory region of row length RX
+// at index c; the same sums give the force stencil (Eq. 28 with F = 1/12).
+template <int RX, class real>
+__device__ __forceinline__ void stencil(const real* p, int c, real& gx, real& gy) {
+    const real a = real(1.0 / 3.0), b = real(1.0 / 12.0);
+    gx = a * (p[c + 1] - p[c - 1]) + b * ((p[c + 1 + RX] - p[c - 1 + RX]) + (p[c + 1 - RX] - p[c - 1 - RX]));
+    gy = a * (p[c + RX] - p[c - RX]) + b * ((p[c + RX + 1] - p[c - RX + 1]) + (p[c + RX - 1] - p[c - RX - 1]));
+}
+template <int RX, class real>
+__device__ __forceinline__ real laplacian(const real* p, int c) {
+    const real C = real(2.0 / 3.0), D = real(1.0 / 6.0);
+    return C * ((p[c + 1] + p[c - 1]) + (p[c + RX] + p[c - RX])) +
+           D * ((p[c + RX + 1] + p[c + RX - 1]) + (p[c - RX + 1] + p[c - RX - 1])) - real(10.0 / 3.0) * p[c];
+}
+
+// The velocity part of Eq. 5 with lambda = 0 for population I of a density
+// `dens` moving with (ux, uy): (w_I)(e.dens u + 3/2 [dens (e.u)^2 - dens |u|^2 / 3]).
+template <int I, class real>
+__device__ __forceinline__ real velocity_part(real dens, real ux, real uy) {
+    constexpr int ex = D2Q9::ex(I), ey = D2Q9::ey(I);
+    const real eu = real(ex) * ux + real(ey) * uy;
+    const real usq = ux * ux + uy * uy;
+    return real(W<I>()) * (dens * eu + real(1.5) * (dens * eu * eu - dens * usq * real(1.0 / 3.0)));
+}
+
+// f^eq_i, i = 1..8, of the binary model (Eq. 5 with p0 = rho/3 + A/2 phi^2 +
+// 3B/4 phi^4, w^t kappa phi lap(phi) and, in the equilibrium scheme,
+// sum_{a<=b} w^ab kappa d_a phi d_b phi); f^eq_0 = rho - sum (Eq. 6).
+template <bool MTERMS, class real>
+__device__ __forceinline__ void f_equilibrium(real rho, real ux, real uy, real phi, real gx, real gy, real lap,
+                                              real A, real B, real kappa, real (&fe)[Q]) {
+    const real phi2 = phi * phi;
+    const real p0 = rho * real(1.0 / 3.0) + real(0.5) * A * phi2 + real(0.75) * B * phi2 * phi2;
+    const real iso = p0 - kappa * phi * lap;
+    const real mxx = kappa * gx * gx, myy = kappa * gy * gy, mxy = kappa * gx * gy;
+    real sum = 0;
+    static_for<1, Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        real pr = real(W<i>()) * iso;
+        if constexpr (MTERMS) {
+            pr += real(lbk::w_m<D2Q9>(i, 0, 0)) * mxx + real(lbk::w_m<D2Q9>(i, 1, 1)) * myy +
+                  real(lbk::w_m<D2Q9>(i, 0, 1)) * mxy;
+        }
+        fe[i] = velocity_part<i>(rho, ux, uy) + pr;
+        sum += fe[i];
+    });
+    fe[0] = rho - sum;
+}
+
+// g^eq_i = velocity part of phi moving with (vx, vy) + w_i Gamma mu (i >= 1),
+// g^eq_0 = phi - sum: sum g = phi, sum g e = phi v, sum g e e = Gamma mu I + phi v v.
+template <class real>
+__device__ __forceinline__ void g_equilibrium(real phi, real vx, real vy, real mu, real Gamma, real (&ge)[Q]) {
+    const real gm = Gamma * mu;
+    real sum = 0;
+    static_for<1, Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        ge[i] = velocity_part<i>(phi, vx, vy) + real(W<i>()) * gm;
+        sum += ge[i];
+    });
+    ge[0] = phi - sum;
+}
+
+// Force populations of Eq. 27, F_i = w_i (e.g + 3/2 [2 (e.u)(e.g) - 2 u.g / 3]),
+// F_0 = -sum (reading R8: sum_i F_i = 0).
+template <class real>
+__device__ __forceinline__ void force_populations(real ux, real uy, real gx, real gy, real (&F)[Q]) {
+    const real ug = ux * gx + uy * gy;
+    real sum = 0;
+    static_for<1, Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
+        const real eg = real(ex) * gx + real(ey) * gy;
+        const real eu = real(ex) * ux + real(ey) * uy;
+        F[i] = real(W<i>()) * (eg + real(1.5) * (real(2) * eu * eg - real(2.0 / 3.0) * ug));
+        sum += F[i];
+    });
+    F[0] = -sum;
+}
+
+template <bool FORCING, class real>
+__global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a) {
+    constexpr int H = FORCING ? 2 : 1;
+    constexpr int RX = TX + 2 * H, RY = TY + 2 * H, RN = RX * RY;
+    constexpr int SX = TX + 2, SY = TY + 2, SN = SX * SY;
+    __shared__ real phs[RN];
+    __shared__ real mdiff[FORCING ? SN : 1], mxy_s[FORCING ? SN : 1];
+
+    const int nx = a.nx, ny = a.ny;
+    const long long pitch = a.pitch;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own = x < nx && y < ny;
+
+    // ---- stage A: own populations; phi on the tile and the halo
+    real f[Q], g[Q];
+    {
+        const int sx = own ? x : wrapc(x, nx), sy = own ? y : wrapc(y, ny);
+        const long long s = (long long)sy * nx + sx;
+        real phi = 0;
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = a.src[i * pitch + s];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            g[i] = a.src[(Q + i) * pitch + s];
+            phi += g[i];
+        }
+        phs[(ty + H) * RX + tx + H] = phi;
+    }
+    for (int h = threadIdx.x; h < RN - NT; h += NT) {
+        int rx, ry;
+        if (h < 2 * H * RX) {          // rows above and below the tile
+            const int r = h / RX;
+            rx = h % RX;
+            ry = r < H ? r : r + TY;
+        } else {                       // H columns left and right of every tile row
+            const int k = h - 2 * H * RX;
+            ry = H + k / (2 * H);
+            const int c = k % (2 * H);
+            rx = c < H ? c : c + TX;
+        }
+        const long long s = (long long)wrapc(y0 - H + ry, ny) * nx + wrapc(x0 - H + rx, nx);
+        real phi = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) phi += a.src[(Q + i) * pitch + s];
+        phs[ry * RX + rx] = phi;
+    }
+    __syncthreads();
+
+    // ---- stage B: M' on the tile + one ring (forcing); own gradient and Laplacian
+    if constexpr (FORCING) {
+        for (int k = threadIdx.x; k < SN; k += NT) {
+            const int c = (k / SX - 1 + H) * RX + (k % SX - 1 + H);
+            real gx, gy;
+            stencil<RX>(phs, c, gx, gy);
+            mdiff[k] = a.kappa * (gx * gx - gy * gy);
+            mxy_s[k] = a.kappa * (gx * gy);
+        }
+    }
+    const int c = (ty + H) * RX + tx + H;
+    real gx, gy;
+    stencil<RX>(phs, c, gx, gy);
+    const real lap = laplacian<RX>(phs, c);
+    const real phi = phs[c];
+    if constexpr (FORCING) __syncthreads();
+
+    // ---- stage C: collision and push of the own site
+    bool bad = false;
+    if (own) {
+        real rho = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            rho += f[i];
+            jx += real(D2Q9::ex(i)) * f[i];
+            jy += real(D2Q9::ey(i)) * f[i];
+        }
+        bad = !(rho > real(0)) || !isfinite(rho);
+        const real ux = jx / rho, uy = jy / rho;
+        const real mu = a.A * phi + a.B * phi * phi * phi - a.kappa * lap;
+        real fe[Q], ge[Q], F[Q];
+        f_equilibrium<!FORCING>(rho, ux, uy, phi, gx, gy, lap, a.A, a.B, a.kappa, fe);
+        real vx = ux, vy = uy;
+        if constexpr (FORCING) {
+            // Eq. 28: g_x = -1/2 d_x (M'_xx - M'_yy) - d_y M'_xy, g_y = 1/2 d_y (M'_xx - M'_yy) - d_x M'_xy
+            const int k = (ty + 1) * SX + tx + 1;
+            real dDx, dDy, dXx, dXy;
+            stencil<SX>(mdiff, k, dDx, dDy);
+            stencil<SX>(mxy_s, k, dXx, dXy);
+            const real bfx = real(-0.5) * dDx - dXy, bfy = real(0.5) * dDy - dXx;
+            force_populations(ux, uy, bfx, bfy, F);
+            vx = ux + bfx / (real(2) * rho);   // Eq. 40
+            vy = uy + bfy / (real(2) * rho);
+        }
+        g_equilibrium(phi, vx, vy, mu, a.Gamma, ge);
+        const int xw[3] = {wrapc(x - 1, nx), x, wrapc(x + 1, nx)};
+        const int yw[3] = {wrapc(y - 1, ny), y, wrapc(y + 1, ny)};
+        static_for<0, Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
+            real fs = f[i] + a.omega * (fe[i] - f[i]);
+            if constexpr (FORCING) fs += F[i];
+            const real gs = g[i] + a.omega_phi * (ge[i] - g[i]);
+            const long long d = (long long)yw[1 + ey] * nx + xw[1 + ex];
+            a.dst[i * pitch + d] = fs;
+            a.dst[(Q + i) * pitch + d] = gs;
+        });
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x % 32) == 0) atomicOr(a.status, 1u);
+}
+
+// f = f^eq, g = g^eq of float64 fields (rho, phi, u), stencils of phi read
+// from the periodic field; one thread per site.
+template <bool FORCING, class real>
+__global__ void binary_init_kernel(const double* rho, const double* phi, const double* ux, const double* uy,
+                                   real* dst, long long pitch, int nx, int ny, double A, double B, double kappa,
+                                   double Gamma) {
+    const long long n = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int x = int(s % nx), y = int(s / nx);
+        double p[9];   // 3 x 3 neighbourhood, row-major, centre p[4]
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                p[(dy + 1) * 3 + dx + 1] = phi[(long long)wrapc(y + dy, ny) * nx + wrapc(x + dx, nx)];
+        double gx, gy;
+        stencil<3>(p, 4, gx, gy);
+        const double lap = laplacian<3>(p, 4);
+        const double mu = A * p[4] + B * p[4] * p[4] * p[4] - kappa * lap;
+        const double u0 = ux ? ux[s] : 0.0, u1 = uy ? uy[s] : 0.0;
+        double fe[Q], ge[Q];
+        f_equilibrium<!FORCING>(rho[s], u0, u1, p[4], gx, gy, lap, A, B, kappa, fe);
+        g_equilibrium(p[4], u0, u1, mu, Gamma, ge);
+        for (int i = 0; i < Q; ++i) {
+            dst[i * pitch + s] = real(fe[i]);
+            dst[(Q + i) * pitch + s] = real(ge[i]);
+        }
+    }
+}
+
+// Observables in float64: rho, phi, u (Eq. 3) and mu; in the forcing scheme
+// also M'_xx - M'_yy and M'_xy for binary_velocity_kernel.
+template <class real>
+__global__ void binary_moments_kernel(const real* src, long long pitch, int nx, int ny, double* rho, double* phi,
+                                      double* ux, double* uy) {
+    const long long n = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        double r = 0, p = 0, jx = 0, jy = 0;
+        for (int i = 0; i < Q; ++i) {
+            const double fi = double(src[i * pitch + s]);
+            r += fi;
+            jx += D2Q9::ex(i) * fi;
+            jy += D2Q9::ey(i) * fi;
+            p += double(src[(Q + i) * pitch + s]);
+        }
+        rho[s] = r;
+        phi[s] = p;
+        ux[s] = jx / r;
+        uy[s] = jy / r;
+    }
+}
+
+__global__ void binary_mu_kernel(const double* phi, int nx, int ny, double A, double B, double kappa, double* mu,
+                                 double* mdiff, double* mxy) {
+    const long long n = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int x = int(s % nx), y = int(s / nx);
+        double p[9];
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                p[(dy + 1) * 3 + dx + 1] = phi[(long long)wrapc(y + dy, ny) * nx + wrapc(x + dx, nx)];
+        double gx, gy;
+        stencil<3>(p, 4, gx, gy);
+        mu[s] = A * p[4] + B * p[4] * p[4] * p[4] - kappa * laplacian<3>(p, 4);
+        if (mdiff) {
+            mdiff[s] = kappa * (gx * gx - gy * gy);
+            mxy[s] = kappa * (gx * gy);
+        }
+    }
+}
+
+// v = u + g / (2 rho) (Eq. 40) with g of Eq. 28 from the M' fields.
+__global__ void binary_velocity_kernel(const double* rho, const double* ux, const double* uy, const double* mdiff,
+                                       const double* mxy, int nx, int ny, double* vx, double* vy) {
+    const long long n = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int x = int(s % nx), y = int(s / nx);
+        double d[9], m[9];
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const long long t = (long long)wrapc(y + dy, ny) * nx + wrapc(x + dx, nx);
+                d[(dy + 1) * 3 + dx + 1] = mdiff[t];
+                m[(dy + 1) * 3 + dx + 1] = mxy[t];
+            }
+        double dDx, dDy, dXx, dXy;
+        stencil<3>(d, 4, dDx, dDy);
+        stencil<3>(m, 4, dXx, dXy);
+        vx[s] = ux[s] + (-0.5 * dDx - dXy) / (2.0 * rho[s]);
+        vy[s] = uy[s] + (0.5 * dDy - dXx) / (2.0 * rho[s]);
+    }
+}
+
+template <class real>
+__global__ void binary_convert_kernel(const real* src, double* out, long long pitch, long long n, int to_double,
+                                      const double* in, real* dst) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * Q * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long k = t / n, s = t % n;
+        if (to_double) out[t] = double(src[k * pitch + s]);
+        else dst[k * pitch + s] = real(in[t]);
+    }
+}
+
+inline unsigned blocks_for(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 8192) b = 8192;
+    return unsigned(b < 1 ? 1 : b);
+}
+
+}  // namespace lbb
+
+using namespace lbb;
+
+struct lb_binary {
+    lb_binary_params p{};
+    cudaStream_t stream = nullptr;       // the caller's stream (NULL: the legacy default stream)
+    cudaStream_t cap_stream = nullptr;   // private stream the step graphs are captured on
+    long long N = 0, pitch = 0;
+    size_t esize = 8;
+    void* pop = nullptr;          // 2 sets x 18 populations x pitch elements
+    int cur = 0;                  // set holding the current populations
+    bool initialised = false;
+    long long step = 0;
+    unsigned* d_status = nullptr;
+    double* work = nullptr;       // 9 float64 fields of N (observables)
+    double* d_in = nullptr;       // staging of host float64 inputs (2 Q N)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_failed = false;
+    lb_status sticky = LB_OK;
+};
+
+namespace {
+
+lb_status bfail(lb_status s, const std::string& msg) {
+    lb_internal_set_error(msg.c_str());
+    return s;
+}
+
+lb_status brecord(lb_binary* c, cudaError_t e, const char* where) {
+    cudaGetLastError();
+    c->sticky = LB_ECUDA;
+    return bfail(LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+lb_status bcheck(lb_binary* c) {
+    if (!c) return bfail(LB_EINVAL, "null context");
+    if (c->sticky != LB_OK) return bfail(c->sticky, "binary context is in an error state");
+    return LB_OK;
+}
+
+char* set_ptr(lb_binary* c, int set) {
+    return static_cast<char*>(c->pop) + size_t(set) * 2 * Q * c->pitch * c->esize;
+}
+
+template <class real>
+cudaError_t launch_step(lb_binary* c, int from, cudaStream_t st) {
+    StepArgs<real> a;
+    a.src = reinterpret_cast<const real*>(set_ptr(c, from));
+    a.dst = reinterpret_cast<real*>(set_ptr(c, 1 - from));
+    a.pitch = c->pitch;
+    a.nx = c->p.nx;
+    a.ny = c->p.ny;
+    a.A = real(c->p.A);
+    a.B = real(c->p.B);
+    a.kappa = real(c->p.kappa);
+    a.Gamma = real(c->p.Gamma);
+    a.omega = real(1.0 / c->p.tau);
+    a.omega_phi = real(1.0 / c->p.tau_phi);
+    a.status = c->d_status;
+    const dim3 grid((c->p.nx + TX - 1) / TX, (c->p.ny + TY - 1) / TY);
+    if (c->p.scheme == LB_SCHEME_FORCING) binary_step_kernel<true, real><<<grid, NT, 0, st>>>(a);
+    else binary_step_kernel<false, real><<<grid, NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t step_once(lb_binary* c, int from, cudaStream_t st) {
+    return c->p.storage == LB_F64 ? launch_step<double>(c, from, st) : launch_step<float>(c, from, st);
+}
+
+lb_status sync_status(lb_binary* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return brecord(c, e, "cudaStreamSynchronize");
+    unsigned st = 0;
+    e = cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return brecord(c, e, "status read");
+    if (st) {
+        c->sticky = LB_EUNSTABLE;
+        return bfail(LB_EUNSTABLE, "a density became non-finite or non-positive");
+    }
+    return LB_OK;
+}
+
+lb_status ensure_work(lb_binary* c) {
+    if (c->work) return LB_OK;
+    cudaError_t e = cudaMalloc(&c->work, size_t(9) * c->N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->work = nullptr;
+        return bfail(LB_ENOMEM, "field workspace");
+    }
+    return LB_OK;
+}
+
+lb_status ensure_in(lb_binary* c) {
+    if (c->d_in) return LB_OK;
+    cudaError_t e = cudaMalloc(&c->d_in, size_t(2) * Q * c->N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->d_in = nullptr;
+        return bfail(LB_ENOMEM, "input staging");
+    }
+    return LB_OK;
+}
+
+void drop_graphs(lb_binary* c) {
+    for (auto& g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+lb_status reset_after_set(lb_binary* c) {
+    c->cur = 0;
+    c->step = 0;
+    c->initialised = true;
+    cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return brecord(c, e, "status reset");
+    return sync_status(c);
+}
+
+// Observables of the current state into the workspace:
+// rho, phi, ux, uy, vx, vy, mu, mdiff, mxy (each N doubles).
+lb_status compute_fields(lb_binary* c) {
+    lb_status s = ensure_work(c);
+    if (s != LB_OK) return s;
+    const long long N = c->N;
+    double* w = c->work;
+    double *rho = w, *phi = w + N, *ux = w + 2 * N, *uy = w + 3 * N, *vx = w + 4 * N, *vy = w + 5 * N,
+           *mu = w + 6 * N, *md = w + 7 * N, *mx = w + 8 * N;
+    const unsigned nb = blocks_for(N);
+    const int nx = c->p.nx, ny = c->p.ny;
+    if (c->p.storage == LB_F64)
+        binary_moments_kernel<double><<<nb, 256, 0, c->stream>>>(
+            reinterpret_cast<const double*>(set_ptr(c, c->cur)), c->pitch, nx, ny, rho, phi, ux, uy);
+    else
+        binary_moments_kernel<float><<<nb, 256, 0, c->stream>>>(
+            reinterpret_cast<const float*>(set_ptr(c, c->cur)), c->pitch, nx, ny, rho, phi, ux, uy);
+    const bool forcing = c->p.scheme == LB_SCHEME_FORCING;
+    binary_mu_kernel<<<nb, 256, 0, c->stream>>>(phi, nx, ny, c->p.A, c->p.B, c->p.kappa, mu, forcing ? md : nullptr,
+                                                 forcing ? mx : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return brecord(c, e, "binary moments");
+    if (forcing) {
+        binary_velocity_kernel<<<nb, 256, 0, c->stream>>>(rho, ux, uy, md, mx, nx, ny, vx, vy);
+        e = cudaGetLastError();
+    } else {
+        e = cudaMemcpyAsync(vx, ux, size_t(2) * N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e != cudaSuccess) return brecord(c, e, "binary velocity");
+    return LB_OK;
+}
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** out) {
+    if (!p || !out) return bfail(LB_EINVAL, "null argument");
+    *out = nullptr;
+    if (p->nx < 1 || p->ny < 1) return bfail(LB_EINVAL, "nx and ny must be >= 1");
+    if ((long long)p->nx * p->ny > 0x7fffffffLL) return bfail(LB_EINVAL, "more than 2^31 - 1 sites");
+    if (!is_fin(p->A) || !is_fin(p->B) || !is_fin(p->kappa) || !is_fin(p->Gamma) || !is_fin(p->tau) ||
+        !is_fin(p->tau_phi))
+        return bfail(LB_EINVAL, "non-finite parameter");
+    if (p->B < 0 || p->kappa < 0) return bfail(LB_EINVAL, "B and kappa must be >= 0");
+    if (!(p->Gamma > 0)) return bfail(LB_EINVAL, "Gamma must be > 0");
+    if (!(p->tau > 0.5) || !(p->tau_phi > 0.5)) return bfail(LB_EINVAL, "tau and tau_phi must be > 1/2");
+    if (p->scheme != LB_SCHEME_EQUILIBRIUM && p->scheme != LB_SCHEME_FORCING) return bfail(LB_EINVAL, "scheme");
+    if (p->storage != LB_F64 && p->storage != LB_F32) return bfail(LB_EINVAL, "storage must be LB_F64 or LB_F32");
+    lb_binary* c = new (std::nothrow) lb_binary;
+    if (!c) return bfail(LB_ENOMEM, "context");
+    c->p = *p;
+    c->N = (long long)p->nx * p->ny;
+    c->esize = p->storage == LB_F64 ? 8 : 4;
+    c->pitch = (c->N + 63) / 64 * 64;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMalloc(&c->pop, size_t(2) * 2 * Q * c->pitch * c->esize);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lb_binary_destroy(c);
+        return bfail(e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_binary_destroy(lb_binary* c) {
+    if (!c) return LB_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    drop_graphs(c);
+    cudaFree(c->pop);
+    cudaFree(c->d_status);
+    cudaFree(c->work);
+    cudaFree(c->d_in);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return LB_OK;
+}
+
+lb_status lb_binary_init_fields(lb_binary* c, const double* rho, const double* phi, const double* u) {
+    lb_status s = bcheck(c);
+    if (s != LB_OK) return s;
+    if (!rho || !phi) return bfail(LB_EINVAL, "rho and phi are required");
+    for (long long i = 0; i < c->N; ++i)
+        if (!(rho[i] > 0) || !is_fin(rho[i]) || !is_fin(phi[i])) return bfail(LB_EINVAL, "rho must be positive and finite, phi finite");
+    if ((s = ensure_in(c)) != LB_OK) return s;
+    const long long N = c->N;
+    double* d = c->d_in;
+    const size_t nb = size_t(N) * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(d, rho, nb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + N, phi, nb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(d + 2 * N, u, 2 * nb, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return brecord(c, e, "field upload");
+    const double* ux = u ? d + 2 * N : nullptr;
+    const double* uy = u ? d + 3 * N : nullptr;
+    const unsigned nbk = blocks_for(N);
+    const bool forcing = c->p.scheme == LB_SCHEME_FORCING;
+    const lb_binary_params& p = c->p;
+    if (p.storage == LB_F64) {
+        double* dst = reinterpret_cast<double*>(set_ptr(c, 0));
+        if (forcing) binary_init_kernel<true, double><<<nbk, 256, 0, c->stream>>>(d, d + N, ux, uy, dst, c->pitch, p.nx, p.ny, p.A, p.B, p.kappa, p.Gamma);
+        else binary_init_kernel<false, double><<<nbk, 256, 0, c->stream>>>(d, d + N, ux, uy, dst, c->pitch, p.nx, p.ny, p.A, p.B, p.kappa, p.Gamma);
+    } else {
+        float* dst = reinterpret_cast<float*>(set_ptr(c, 0));
+        if (forcing) binary_init_kernel<true, float><<<nbk, 256, 0, c->stream>>>(d, d + N, ux, uy, dst, c->pitch, p.nx, p.ny, p.A, p.B, p.kappa, p.Gamma);
+        else binary_init_kernel<false, float><<<nbk, 256, 0, c->stream>>>(d, d + N, ux, uy, dst, c->pitch, p.nx, p.ny, p.A, p.B, p.kappa, p.Gamma);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return brecord(c, e, "binary init");
+    return reset_after_set(c);
+}
+
+lb_status lb_binary_set_populations(lb_binary* c, const double* f, const double* g) {
+    lb_status s = bcheck(c);
+    if (s != LB_OK) return s;
+    if (!f || !g) return bfail(LB_EINVAL, "null populations");
+    if ((s = ensure_in(c)) != LB_OK) return s;
+    const size_t half = size_t(Q) * c->N;
+    cudaError_t e = cudaMemcpyAsync(c->d_in, f, half * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_in + half, g, half * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return brecord(c, e, "population upload");
+    const unsigned nb = blocks_for(2 * half);
+    if (c->p.storage == LB_F64)
+        binary_convert_kernel<double><<<nb, 256, 0, c->stream>>>(nullptr, nullptr, c->pitch, c->N, 0, c->d_in,
+                                                                  reinterpret_cast<double*>(set_ptr(c, 0)));
+    else
+        binary_convert_kernel<float><<<nb, 256, 0, c->stream>>>(nullptr, nullptr, c->pitch, c->N, 0, c->d_in,
+                                                                 reinterpret_cast<float*>(set_ptr(c, 0)));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return brecord(c, e, "set populations");
+    return reset_after_set(c);
+}
+
+lb_status lb_binary_get_populations(lb_binary* c, double* f, double* g) {
+    lb_status s = bcheck(c);
+    if (s != LB_OK) return s;
+    if (!f || !g) return bfail(LB_EINVAL, "null output");
+    if (!c->initialised) return bfail(LB_ESTATE, "state not initialised");
+    if ((s = ensure_in(c)) != LB_OK) return s;
+    const size_t half = size_t(Q) * c->N;
+    const unsigned nb = blocks_for(2 * half);
+    if (c->p.storage == LB_F64)
+        binary_convert_kernel<double><<<nb, 256, 0, c->stream>>>(
+            reinterpret_cast<const double*>(set_ptr(c, c->cur)), c->d_in, c->pitch, c->N, 1, nullptr, nullptr);
+    else
+        binary_convert_kernel<float><<<nb, 256, 0, c->stream>>>(
+            reinterpret_cast<const float*>(set_ptr(c, c->cur)), c->d_in, c->pitch, c->N, 1, nullptr, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, c->d_in, half * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g, c->d_in + half, half * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return brecord(c, e, "get populations");
+    return sync_status(c);
+}
+
+lb_status lb_binary_step(lb_binary* c, int nsteps) {
+    lb_status s = bcheck(c);
+    if (s != LB_OK) return s;
+    if (nsteps < 0) return bfail(LB_EINVAL, "nsteps must be >= 0");
+    if (!c->initialised) return bfail(LB_ESTATE, "step before init");
+    int k = 0;
+    // long runs: replay a graph of GRAPH_STEPS launches per start buffer, captured
+    // on a private stream (the legacy default stream cannot be captured) and
+    // launched on the context's stream
+    if (!c->graph_failed && nsteps >= GRAPH_STEPS) {
+        if (!c->graph[c->cur]) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaSuccess;
+            if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+            const bool capturing = e == cudaSuccess;
+            for (int j = 0; e == cudaSuccess && j < GRAPH_STEPS; ++j) e = step_once(c, (c->cur + j) & 1, c->cap_stream);
+            if (capturing) {
+                cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+                if (e == cudaSuccess) e = e2;
+            }
+            cudaGraphExec_t exec = nullptr;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e == cudaSuccess) c->graph[c->cur] = exec;
+            else {
+                cudaGetLastError();
+                c->graph_failed = true;
+            }
+        }
+        for (cudaGraphExec_t g = c->graph[c->cur]; g && k + GRAPH_STEPS <= nsteps; k += GRAPH_STEPS) {
+            cudaError_t e = cudaGraphLaunch(g, c->stream);
+            if (e != cudaSuccess) return brecord(c, e, "binary step graph");
+            c->step += GRAPH_STEPS;
+        }
+    }
+    for (; k < nsteps; ++k) {
+        cudaError_t e = step_once(c, c->cur, c->stream);
+        if (e != cudaSuccess) return brecord(c, e, "binary step");
+        c->cur = 1 - c->cur;
+        ++c->step;
+    }
+    return LB_OK;
+}
+
+lb_status lb_binary_synchronize(lb_binary* c) {
+    lb_status s = bcheck(c);
+    if (s != LB_OK) return s;
+    return sync_status(c);
+}
+
+lb_status lb_binary_fields(lb_binary* c, double* rho, double* phi, double* u, double* v, double* mu) {
+    lb_status s = bcheck(c);
+    if (s != LB_OK) return s;
+    if (!c->initialised) return bfail(LB_ESTATE, "state not initialised");
+    if ((s = compute_fields(c)) != LB_OK) return s;
+    const long long N = c->N;
+    const size_t nb = size_t(N) * sizeof(double);
+    const double* w = c->work;
+    cudaError_t e = cudaSuccess;
+    if (rho) e = cudaMemcpyAsync(rho, w, nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && phi) e = cudaMemcpyAsync(phi, w + N, nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, w + 2 * N, 2 * nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, w + 4 * N, 2 * nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && mu) e = cudaMemcpyAsync(mu, w + 6 * N, nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return brecord(c, e, "field download");
+    return sync_status(c);
+}
+
+lb_status lb_binary_stats_get(lb_binary* c, lb_binary_stats* out) {
+    lb_status s = bcheck(c);
+    if (s != LB_OK) return s;
+    if (!out) return bfail(LB_EINVAL, "null output");
+    if (!c->initialised) return bfail(LB_ESTATE, "state not initialised");
+    const long long N = c->N;
+    std::vector<double> h;
+    try {
+        h.resize(size_t(6) * N);
+    } catch (...) {
+        return bfail(LB_ENOMEM, "host buffer");
+    }
+    s = lb_binary_fields(c, h.data(), h.data() + N, h.data() + 2 * N, h.data() + 4 * N, nullptr);
+    if (s != LB_OK && s != LB_EUNSTABLE) return s;
+    lb_binary_stats r{};
+    r.min_phi = h[N];
+    r.max_phi = h[N];
+    for (long long i = 0; i < N; ++i) {
+        const double rh = h[i], ph = h[N + i], ux = h[2 * N + i], uy = h[3 * N + i];
+        const double vx = h[4 * N + i], vy = h[5 * N + i];
+        r.mass += rh;
+        r.phi_total += ph;
+        r.momentum[0] += rh * ux;
+        r.momentum[1] += rh * uy;
+        r.max_u = std::fmax(r.max_u, std::sqrt(ux * ux + uy * uy));
+        r.max_v = std::fmax(r.max_v, std::sqrt(vx * vx + vy * vy));
+        r.min_phi = std::fmin(r.min_phi, ph);
+        r.max_phi = std::fmax(r.max_phi, ph);
+    }
+    r.step = c->step;
+    r.status = s == LB_EUNSTABLE ? LB_EUNSTABLE : 0;
+    *out = r;
+    return s;
+}
+
+}  // extern "C"

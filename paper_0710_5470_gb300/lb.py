@@ -55,6 +55,18 @@ class lb_instance(C.Structure):
                 ("radius", C.c_double)]
 
 
+class lb_binary_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("A", C.c_double), ("B", C.c_double), ("kappa", C.c_double),
+                ("Gamma", C.c_double), ("tau", C.c_double), ("tau_phi", C.c_double), ("scheme", C.c_int),
+                ("storage", C.c_int)]
+
+
+class lb_binary_stats(C.Structure):
+    _fields_ = [("mass", C.c_double), ("phi_total", C.c_double), ("momentum", C.c_double * 2),
+                ("max_u", C.c_double), ("max_v", C.c_double), ("min_phi", C.c_double), ("max_phi", C.c_double),
+                ("step", C.c_longlong), ("status", C.c_int)]
+
+
 _lib = None
 
 _DPTR = C.POINTER(C.c_double)
@@ -134,6 +146,15 @@ _SIGNATURES = {
     "lb_work_list": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                C.POINTER(C.c_int)]),
     "lb_get_populations_box": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _DPTR]),
+    "lb_binary_create": (C.c_int, [C.POINTER(lb_binary_params), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lb_binary_destroy": (C.c_int, [C.c_void_p]),
+    "lb_binary_init_fields": (C.c_int, [C.c_void_p, _DPTR, _DPTR, _DPTR]),
+    "lb_binary_set_populations": (C.c_int, [C.c_void_p, _DPTR, _DPTR]),
+    "lb_binary_get_populations": (C.c_int, [C.c_void_p, _DPTR, _DPTR]),
+    "lb_binary_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lb_binary_synchronize": (C.c_int, [C.c_void_p]),
+    "lb_binary_fields": (C.c_int, [C.c_void_p, _DPTR, _DPTR, _DPTR, _DPTR, _DPTR]),
+    "lb_binary_stats_get": (C.c_int, [C.c_void_p, C.POINTER(lb_binary_stats)]),
 }
 
 
@@ -639,3 +660,80 @@ def ws_decode(rho_tanh: np.ndarray, rho_l: float, rho_g: float, y: np.ndarray):
     u = np.empty((2, ny, nx), dtype=np.float64)
     _check(load_library().lb_ws_decode(nx, ny, _dptr(r), rho_l, rho_g, _fptr(y), _dptr(rho), _dptr(u)))
     return rho, u
+
+
+class BinaryContext:
+    """One D2Q9 binary-fluid lattice (lb_binary_create ... lb_binary_destroy).
+
+    shape is (nx, ny); fields are (ny, nx) arrays, populations (9, ny, nx)."""
+
+    def __init__(self, shape, A: float, B: float, kappa: float, Gamma: float, tau: float, tau_phi: float,
+                 scheme: int = EQUILIBRIUM, storage: int = F64, stream=None):
+        lib = load_library()
+        nx, ny = (int(v) for v in shape)
+        self.params = lb_binary_params(nx, ny, A, B, kappa, Gamma, tau, tau_phi, scheme, storage)
+        self.shape = (ny, nx)
+        self.n = nx * ny
+        h = C.c_void_p()
+        st = C.c_void_p(int(stream)) if stream else None
+        _check(lib.lb_binary_create(C.byref(self.params), st, C.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lb_binary_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init_fields(self, rho: np.ndarray, phi: np.ndarray, u: np.ndarray | None = None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        assert rho.size == self.n and phi.size == self.n and (uu is None or uu.size == 2 * self.n)
+        _check(self._lib.lb_binary_init_fields(self._h, _dptr(rho), _dptr(phi), _dptr(uu)))
+
+    def set_populations(self, f: np.ndarray, g: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.size == 9 * self.n and g.size == 9 * self.n
+        _check(self._lib.lb_binary_set_populations(self._h, _dptr(f), _dptr(g)))
+
+    def get_populations(self):
+        f = np.empty((9,) + self.shape, dtype=np.float64)
+        g = np.empty((9,) + self.shape, dtype=np.float64)
+        _check(self._lib.lb_binary_get_populations(self._h, _dptr(f), _dptr(g)))
+        return f, g
+
+    def step(self, n: int = 1):
+        _check(self._lib.lb_binary_step(self._h, int(n)))
+
+    def synchronize(self):
+        _check(self._lib.lb_binary_synchronize(self._h))
+
+    def fields(self):
+        """rho, phi, u (2, ny, nx), v (2, ny, nx), mu."""
+        rho = np.empty(self.shape)
+        phi = np.empty(self.shape)
+        u = np.empty((2,) + self.shape)
+        v = np.empty((2,) + self.shape)
+        mu = np.empty(self.shape)
+        _check(self._lib.lb_binary_fields(self._h, _dptr(rho), _dptr(phi), _dptr(u), _dptr(v), _dptr(mu)))
+        return rho, phi, u, v, mu
+
+    def stats(self) -> dict:
+        s = lb_binary_stats()
+        _check(self._lib.lb_binary_stats_get(self._h, C.byref(s)))
+        return {"mass": s.mass, "phi_total": s.phi_total, "momentum": list(s.momentum), "max_u": s.max_u,
+                "max_v": s.max_v, "min_phi": s.min_phi, "max_phi": s.max_phi, "step": s.step, "status": s.status}

@@ -1,0 +1,172 @@
+"""Binary-fluid D2Q9 kernels (csrc/binary2d.cu) against the binary oracle.
+
+float64: every population, rho, phi, u, v and mu to 1e-12 after 100 steps on
+ragged, odd and tiny lattices, both schemes; the initial state to 1e-14; one
+step at 1024^2.  float32: the same comparison at float32 rounding.  The graph
+replay path equals single launches bit for bit; mass, order parameter and
+momentum stay conserved; Laplace's law holds on the device.
+"""
+import numpy as np
+import pytest
+
+from oracle import binary_oracle as BO
+from paper_0710_5470_gb300 import inputs
+from tests.helpers import library, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+A_BIN, B_BIN, K_BIN = -0.04, 0.04, 0.08     # phi* = 1, interface width w = 2
+SCHEMES = ["equilibrium", "forcing"]
+
+
+def _model(scheme, tau=0.8, tau_phi=0.9, Gamma=0.7):
+    return BO.BinaryModel("D2Q9", A_BIN, B_BIN, K_BIN, Gamma, tau, tau_phi, scheme=scheme)
+
+
+def _ctx(lb, m, shape_xy, storage=0):
+    return lb.BinaryContext(shape_xy, m.A, m.B, m.kappa, m.Gamma, m.tau, m.tau_phi,
+                            scheme=lb.FORCING if m.scheme == "forcing" else lb.EQUILIBRIUM, storage=storage)
+
+
+def _fields(m, nx, ny, R=None, seed=1):
+    """A drop of phase +phi* in -phi*, rho = 1 + 1e-3 noise, u = 1e-3 noise (seeded)."""
+    shape = (1, ny, nx)
+    R = R if R is not None else 0.3 * min(nx, ny)
+    phi0 = BO.drop_phi(shape, [(nx / 2, ny / 2)], [R], 1.0, -1.0, BO.interface_width(m.A, m.kappa))
+    rho0 = 1.0 + 1e-3 * inputs.noise(seed, shape)
+    u0 = [1e-3 * inputs.noise(seed + 1, shape), 1e-3 * inputs.noise(seed + 2, shape)]
+    return rho0, phi0, u0
+
+
+SHAPES = [(48, 20), (37, 11), (5, 3), (64, 16)]
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_f64_parity(scheme, shape):
+    m = _model(scheme)
+    nx, ny = shape
+    rho0, phi0, u0 = _fields(m, nx, ny)
+    f, g = BO.init_equilibrium(rho0, phi0, m, u0)
+    with _ctx(library(), m, shape) as c:
+        c.set_populations(f[:, 0], g[:, 0])
+        c.step(100)
+        fg, gg = c.get_populations()
+        rho, phi, u, v, mu = c.fields()
+        st = c.stats()
+    fo, go = BO.run(f, g, m, 100)
+    assert rel_inf(fg, fo[:, 0]) < 1e-12
+    assert rel_inf(gg, go[:, 0]) < 1e-12
+    orho, ophi, ou, ov, omu = BO.observables(fo, go, m)
+    assert np.abs(rho - orho[0]).max() < 1e-12 and np.abs(phi - ophi[0]).max() < 1e-12
+    for a in range(2):
+        assert np.abs(u[a] - ou[a][0]).max() < 1e-14
+        assert np.abs(v[a] - ov[a][0]).max() < 1e-14
+    assert np.abs(mu - omu[0]).max() < 1e-13
+    d = BO.diagnostics(fo, go, m)
+    assert abs(st["mass"] - d["mass"]) < 1e-10 and abs(st["phi_total"] - d["phi_total"]) < 1e-10
+    assert abs(st["max_v"] - d["max_v"]) < 1e-14 and st["step"] == 100 and st["status"] == 0
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_init_fields_matches_oracle(scheme):
+    m = _model(scheme)
+    nx, ny = 40, 24
+    rho0, phi0, u0 = _fields(m, nx, ny)
+    f, g = BO.init_equilibrium(rho0, phi0, m, u0)
+    with _ctx(library(), m, (nx, ny)) as c:
+        c.init_fields(rho0[0], phi0[0], np.stack([u0[0][0], u0[1][0]]))
+        fg, gg = c.get_populations()
+    assert rel_inf(fg, f[:, 0]) < 1e-14 and rel_inf(gg, g[:, 0]) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_f32_parity(scheme):
+    """float32 storage and arithmetic: 20 steps within 2e-6 of max |f| (float32
+    rounding of ~100 operations per population and step, accumulated)."""
+    m = _model(scheme)
+    nx, ny = 48, 20
+    rho0, phi0, u0 = _fields(m, nx, ny)
+    f, g = BO.init_equilibrium(rho0, phi0, m, u0)
+    with _ctx(library(), m, (nx, ny), storage=1) as c:
+        c.set_populations(f[:, 0], g[:, 0])
+        c.step(20)
+        fg, gg = c.get_populations()
+    fo, go = BO.run(f, g, m, 20)
+    ef, eg = rel_inf(fg, fo[:, 0]), rel_inf(gg, go[:, 0])
+    print(f"binary f32 {scheme}: f {ef:.2e} g {eg:.2e}")
+    assert ef < 2e-6 and eg < 2e-6
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_graph_replay_equals_single_launches(storage):
+    m = _model("forcing")
+    nx, ny = 64, 24
+    rho0, phi0, u0 = _fields(m, nx, ny)
+    lb = library()
+    out = []
+    for chunks in ([130], [1] * 130):
+        with _ctx(lb, m, (nx, ny), storage=storage) as c:
+            c.init_fields(rho0[0], phi0[0])
+            for k in chunks:
+                c.step(k)
+            out.append(c.get_populations())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_conservation_on_device(scheme):
+    m = _model(scheme)
+    nx, ny = 64, 64
+    rho0, phi0, u0 = _fields(m, nx, ny)
+    with _ctx(library(), m, (nx, ny)) as c:
+        c.init_fields(rho0[0], phi0[0], np.stack([u0[0][0], u0[1][0]]))
+        s0 = c.stats()
+        c.step(3000)
+        s1 = c.stats()
+    assert abs(s1["mass"] / s0["mass"] - 1) < 1e-12
+    assert abs(s1["phi_total"] - s0["phi_total"]) < 1e-9
+    for a in range(2):
+        assert abs(s1["momentum"][a] - s0["momentum"][a]) < 1e-11
+    assert s1["status"] == 0 and s1["step"] == 3000
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_laplace_law_on_device(storage):
+    """dP R / sigma = 1 (sigma = 4 kappa phi*^2 / (3 w)) within 5% for a drop of
+    radius 20 after 20000 steps, both schemes; the forcing scheme's max|v| is
+    below half the equilibrium scheme's."""
+    lb = library()
+    n, R = 96, 20.0
+    res = {}
+    for scheme in SCHEMES:
+        m = _model(scheme, tau=1.0, tau_phi=1.0, Gamma=1.0)
+        shape = (1, n, n)
+        phi0 = BO.drop_phi(shape, [(n / 2, n / 2)], [R], 1.0, -1.0, BO.interface_width(A_BIN, K_BIN))
+        with _ctx(lb, m, (n, n), storage=storage) as c:
+            c.init_fields(np.ones((n, n)), phi0[0])
+            c.step(20000)
+            rho, phi, u, v, mu = c.fields()
+        pin, pout = phi[n // 2, n // 2], phi[0, 0]
+        R_e = np.sqrt((phi.sum() - pout * n * n) / (np.pi * (pin - pout)))
+        dP = BO.p0(rho[n // 2, n // 2], pin, A_BIN, B_BIN) - BO.p0(rho[0, 0], pout, A_BIN, B_BIN)
+        res[scheme] = (dP * R_e / BO.surface_tension(A_BIN, B_BIN, K_BIN), float(np.hypot(v[0], v[1]).max()))
+    print("binary Laplace", storage, res)
+    for scheme in SCHEMES:
+        assert abs(res[scheme][0] - 1) < 0.05, (scheme, res)
+    assert res["forcing"][1] < 0.5 * res["equilibrium"][1], res
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_one_step_at_1024(scheme):
+    """The bench lattice (1024^2, one drop of radius 256): one float64 step, every population."""
+    m = _model(scheme, tau=1.0, tau_phi=1.0, Gamma=1.0)
+    n = 1024
+    rho0, phi0, u0 = _fields(m, n, n, R=256.0, seed=11)
+    f, g = BO.init_equilibrium(rho0, phi0, m, u0)
+    with _ctx(library(), m, (n, n)) as c:
+        c.set_populations(f[:, 0], g[:, 0])
+        c.step(1)
+        fg, gg = c.get_populations()
+    fo, go = BO.step(f, g, m)
+    assert rel_inf(fg, fo[:, 0]) < 1e-14 and rel_inf(gg, go[:, 0]) < 1e-14

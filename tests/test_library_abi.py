@@ -105,3 +105,21 @@ def test_params_hash_is_stable_and_sensitive():
         seen.add(h)
     with pytest.raises(lb.LBError):
         lb.params_hash(**dict(base, tau=0.4))
+
+
+def test_binary_parameters_rejected_before_device_work():
+    """lb_binary_create validates its parameters on the host (LB_EINVAL) before any CUDA call."""
+    lb = library()
+    ok = dict(A=-0.04, B=0.04, kappa=0.08, Gamma=1.0, tau=1.0, tau_phi=1.0)
+    bad = [dict(tau=0.5), dict(tau_phi=0.4), dict(Gamma=0.0), dict(kappa=-1.0), dict(B=-0.1),
+           dict(A=float("nan"))]
+    for b in bad:
+        kw = dict(ok)
+        kw.update(b)
+        with pytest.raises(lb.LBError) as e:
+            lb.BinaryContext((16, 8), **kw)
+        assert e.value.status == 1, b
+    for shape, extra in (((0, 8), {}), ((8, 8), dict(scheme=2)), ((8, 8), dict(storage=2))):
+        with pytest.raises(lb.LBError) as e:
+            lb.BinaryContext(shape, **ok, **extra)
+        assert e.value.status == 1
