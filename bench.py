@@ -444,12 +444,11 @@ def binary_block(lb, stream, peak, dist, world, warmup, cpu: bool):
     float32 and float64 storage, both schemes, against the HBM roofline at the
     bytes it moves (18 populations read and written: 144 / 288 B per update)."""
     import numpy as np
+    from paper_0710_5470_gb300 import binary as bin_runs
     b = BINARY
     n = b["n"]
-    w = np.sqrt(-2 * b["kappa"] / b["A"])
-    y, x = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
-    d = np.hypot(np.minimum(np.abs(x - n / 2), n - np.abs(x - n / 2)), np.minimum(np.abs(y - n / 2), n - np.abs(y - n / 2)))
-    phi0 = -1.0 + 2.0 * 0.5 * (1 + np.tanh((b["R"] - d) / w))
+    w = bin_runs.interface_width(b["A"], b["kappa"])
+    phi0 = bin_runs.drop_phi(n, b["R"], b["A"], b["kappa"], b["B"])
     out = {"workload": f"D2Q9 {n}^2 periodic, one drop R={b['R']:g} of phi=+1 in phi=-1 (tanh, width "
                        f"{w:g}), rho=1, A={b['A']}, B={b['B']}, kappa={b['kappa']}, Gamma={b['Gamma']}, "
                        f"tau=tau_phi=1", "runs": {}}

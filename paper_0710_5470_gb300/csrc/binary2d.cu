@@ -58,7 +58,7 @@ template <class real>
 struct StepArgs {
     const real* src;     // populations after streaming: f_0..f_8 then g_0..g_8, each `pitch` elements
     real* dst;
-    long long pitch;
+    unsigned pitch;      // 18 pitch < 2^32: element offsets within a set are 32-bit
     int nx, ny;
     real A, B, kappa, Gamma, omega, omega_phi;   // omega = 1/tau, omega_phi = 1/tau_phi
     unsigned* status;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
     __shared__ real mdiff[FORCING ? SN : 1], mxy_s[FORCING ? SN : 1];
 
     const int nx = a.nx, ny = a.ny;
-    const long long pitch = a.pitch;
+    const unsigned pitch = a.pitch;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int x = x0 + tx, y = y0 + ty;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
     real f[Q], g[Q];
     {
         const int sx = own ? x : wrapc(x, nx), sy = own ? y : wrapc(y, ny);
-        const long long s = (long long)sy * nx + sx;
+        const unsigned s = unsigned(sy) * unsigned(nx) + unsigned(sx);
         real phi = 0;
         if (own) {
 #pragma unroll
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
             const int c = k % (2 * H);
             rx = c < H ? c : c + TX;
         }
-        const long long s = (long long)wrapc(y0 - H + ry, ny) * nx + wrapc(x0 - H + rx, nx);
+        const unsigned s = unsigned(wrapc(y0 - H + ry, ny)) * unsigned(nx) + unsigned(wrapc(x0 - H + rx, nx));
         real phi = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) phi += a.src[(Q + i) * pitch + s];
@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
             jy += real(D2Q9::ey(i)) * f[i];
         }
         bad = !(rho > real(0)) || !isfinite(rho);
-        const real ux = jx / rho, uy = jy / rho;
+        const real ir = real(1) / rho;
+        const real ux = jx * ir, uy = jy * ir;
         const real mu = a.A * phi + a.B * phi * phi * phi - a.kappa * lap;
         real fe[Q], ge[Q], F[Q];
         f_equilibrium<!FORCING>(rho, ux, uy, phi, gx, gy, lap, a.A, a.B, a.kappa, fe);
@@ -242,8 +243,8 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
             stencil<SX>(mxy_s, k, dXx, dXy);
             const real bfx = real(-0.5) * dDx - dXy, bfy = real(0.5) * dDy - dXx;
             force_populations(ux, uy, bfx, bfy, F);
-            vx = ux + bfx / (real(2) * rho);   // Eq. 40
-            vy = uy + bfy / (real(2) * rho);
+            vx = ux + bfx * (real(0.5) * ir);   // Eq. 40
+            vy = uy + bfy * (real(0.5) * ir);
         }
         g_equilibrium(phi, vx, vy, mu, a.Gamma, ge);
         const int xw[3] = {wrapc(x - 1, nx), x, wrapc(x + 1, nx)};
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
             real fs = f[i] + a.omega * (fe[i] - f[i]);
             if constexpr (FORCING) fs += F[i];
             const real gs = g[i] + a.omega_phi * (ge[i] - g[i]);
-            const long long d = (long long)yw[1 + ey] * nx + xw[1 + ex];
+            const unsigned d = unsigned(yw[1 + ey]) * unsigned(nx) + unsigned(xw[1 + ex]);
             a.dst[i * pitch + d] = fs;
             a.dst[(Q + i) * pitch + d] = gs;
         });
@@ -419,7 +420,7 @@ cudaError_t launch_step(lb_binary* c, int from, cudaStream_t st) {
     StepArgs<real> a;
     a.src = reinterpret_cast<const real*>(set_ptr(c, from));
     a.dst = reinterpret_cast<real*>(set_ptr(c, 1 - from));
-    a.pitch = c->pitch;
+    a.pitch = unsigned(c->pitch);
     a.nx = c->p.nx;
     a.ny = c->p.ny;
     a.A = real(c->p.A);
@@ -548,6 +549,11 @@ lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** 
     c->N = (long long)p->nx * p->ny;
     c->esize = p->storage == LB_F64 ? 8 : 4;
     c->pitch = (c->N + 63) / 64 * 64;
+    if (2 * Q * c->pitch >= (1LL << 32)) {
+        delete c;
+        return bfail(LB_EINVAL, "lattice too large: element offsets of a population set must fit 32 bits "
+                                "(at most 238,609,280 sites)");
+    }
     c->stream = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMalloc(&c->pop, size_t(2) * 2 * Q * c->pitch * c->esize);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
