@@ -29,6 +29,8 @@
 
 #include "../../include/lb.h"
 #include "lattice.cuh"
+#include "aux_kernels.cuh"
+#include "step3d_pk.cuh"   // lbk::P2: packed float32 pairs
 
 // Sets the thread-local message returned by lb_last_error (defined in lb_api.cu).
 void lb_internal_set_error(const char* msg);
@@ -36,6 +38,8 @@ void lb_internal_set_error(const char* msg);
 namespace lbb {
 
 using lbk::D2Q9;
+using lbk::P2;
+using lbk::pp;
 using lbk::static_for;
 
 constexpr int Q = 9;
@@ -84,14 +88,33 @@ __device__ __forceinline__ real laplacian(const real* p, int c) {
            D * ((p[c + RX + 1] + p[c + RX - 1]) + (p[c - RX + 1] + p[c - RX - 1])) - real(10.0 / 3.0) * p[c];
 }
 
+// The arithmetic below is written once for a scalar (float, double) and for
+// a packed pair of float32 sites (lbk::P2: FADD2 / FMUL2 / FFMA2, one
+// instruction for two sites); cst<real> makes a constant of either.
+template <class real>
+__device__ __forceinline__ real cst(double d) { return real(d); }
+template <>
+__device__ __forceinline__ P2 cst<P2>(double d) { return pp(float(d)); }
+
+// e_i . (ux, uy) for a velocity with components in {-1, 0, 1}: adds only.
+template <int EX, int EY, class real>
+__device__ __forceinline__ real edot(real ux, real uy) {
+    if constexpr (EX == 0 && EY == 0) return cst<real>(0.0);
+    else if constexpr (EX == 0) return EY > 0 ? uy : -uy;
+    else if constexpr (EY == 0) return EX > 0 ? ux : -ux;
+    else {
+        const real a = EX > 0 ? ux : -ux;
+        return EY > 0 ? a + uy : a - uy;
+    }
+}
+
 // The velocity part of Eq. 5 with lambda = 0 for population I of a density
-// `dens` moving with (ux, uy): (w_I)(e.dens u + 3/2 [dens (e.u)^2 - dens |u|^2 / 3]).
+// `dens` moving with (ux, uy): w_I (dens e.u + 3/2 [dens (e.u)^2 - dens |u|^2 / 3]).
 template <int I, class real>
-__device__ __forceinline__ real velocity_part(real dens, real ux, real uy) {
-    constexpr int ex = D2Q9::ex(I), ey = D2Q9::ey(I);
-    const real eu = real(ex) * ux + real(ey) * uy;
-    const real usq = ux * ux + uy * uy;
-    return real(W<I>()) * (dens * eu + real(1.5) * (dens * eu * eu - dens * usq * real(1.0 / 3.0)));
+__device__ __forceinline__ real velocity_part(real dens, real ux, real uy, real usq3) {
+    const real eu = edot<D2Q9::ex(I), D2Q9::ey(I)>(ux, uy);
+    const real de = dens * eu;
+    return cst<real>(W<I>()) * (de + cst<real>(1.5) * (de * eu - dens * usq3));
 }
 
 // f^eq_i, i = 1..8, of the binary model (Eq. 5 with p0 = rho/3 + A/2 phi^2 +
@@ -101,18 +124,19 @@ template <bool MTERMS, class real>
 __device__ __forceinline__ void f_equilibrium(real rho, real ux, real uy, real phi, real gx, real gy, real lap,
                                               real A, real B, real kappa, real (&fe)[Q]) {
     const real phi2 = phi * phi;
-    const real p0 = rho * real(1.0 / 3.0) + real(0.5) * A * phi2 + real(0.75) * B * phi2 * phi2;
+    const real p0 = rho * cst<real>(1.0 / 3.0) + cst<real>(0.5) * A * phi2 + cst<real>(0.75) * B * phi2 * phi2;
     const real iso = p0 - kappa * phi * lap;
     const real mxx = kappa * gx * gx, myy = kappa * gy * gy, mxy = kappa * gx * gy;
-    real sum = 0;
+    const real usq3 = (ux * ux + uy * uy) * cst<real>(1.0 / 3.0);
+    real sum = cst<real>(0.0);
     static_for<1, Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
-        real pr = real(W<i>()) * iso;
+        real pr = cst<real>(W<i>()) * iso;
         if constexpr (MTERMS) {
-            pr += real(lbk::w_m<D2Q9>(i, 0, 0)) * mxx + real(lbk::w_m<D2Q9>(i, 1, 1)) * myy +
-                  real(lbk::w_m<D2Q9>(i, 0, 1)) * mxy;
+            pr += cst<real>(lbk::w_m<D2Q9>(i, 0, 0)) * mxx + cst<real>(lbk::w_m<D2Q9>(i, 1, 1)) * myy;
+            if constexpr (lbk::w_m<D2Q9>(i, 0, 1) != 0.0) pr += cst<real>(lbk::w_m<D2Q9>(i, 0, 1)) * mxy;
         }
-        fe[i] = velocity_part<i>(rho, ux, uy) + pr;
+        fe[i] = velocity_part<i>(rho, ux, uy, usq3) + pr;
         sum += fe[i];
     });
     fe[0] = rho - sum;
@@ -123,10 +147,11 @@ __device__ __forceinline__ void f_equilibrium(real rho, real ux, real uy, real p
 template <class real>
 __device__ __forceinline__ void g_equilibrium(real phi, real vx, real vy, real mu, real Gamma, real (&ge)[Q]) {
     const real gm = Gamma * mu;
-    real sum = 0;
+    const real usq3 = (vx * vx + vy * vy) * cst<real>(1.0 / 3.0);
+    real sum = cst<real>(0.0);
     static_for<1, Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
-        ge[i] = velocity_part<i>(phi, vx, vy) + real(W<i>()) * gm;
+        ge[i] = velocity_part<i>(phi, vx, vy, usq3) + cst<real>(W<i>()) * gm;
         sum += ge[i];
     });
     ge[0] = phi - sum;
@@ -136,14 +161,14 @@ __device__ __forceinline__ void g_equilibrium(real phi, real vx, real vy, real m
 // F_0 = -sum (reading R8: sum_i F_i = 0).
 template <class real>
 __device__ __forceinline__ void force_populations(real ux, real uy, real gx, real gy, real (&F)[Q]) {
-    const real ug = ux * gx + uy * gy;
-    real sum = 0;
+    const real ug23 = (ux * gx + uy * gy) * cst<real>(2.0 / 3.0);
+    real sum = cst<real>(0.0);
     static_for<1, Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
         constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
-        const real eg = real(ex) * gx + real(ey) * gy;
-        const real eu = real(ex) * ux + real(ey) * uy;
-        F[i] = real(W<i>()) * (eg + real(1.5) * (real(2) * eu * eg - real(2.0 / 3.0) * ug));
+        const real eg = edot<ex, ey>(gx, gy);
+        const real eu = edot<ex, ey>(ux, uy);
+        F[i] = cst<real>(W<i>()) * (eg + cst<real>(1.5) * (cst<real>(2.0) * eu * eg - ug23));
         sum += F[i];
     });
     F[0] = -sum;
@@ -258,6 +283,211 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
             const unsigned d = unsigned(yw[1 + ey]) * unsigned(nx) + unsigned(xw[1 + ex]);
             a.dst[i * pitch + d] = fs;
             a.dst[(Q + i) * pitch + d] = gs;
+        });
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x % 32) == 0) atomicOr(a.status, 1u);
+}
+
+// The same step with two adjacent x sites per thread (x even; nx even) for
+// float32 storage: each population of the pair is one aligned 8-byte access,
+// and every arithmetic step of stage C runs as packed float32 pair
+// instructions.  CTA: a 32 x 8 tile, 128 threads; the phi halo is 2 sites in
+// x (one pair) and 1 (equilibrium) or 2 (forcing) rows in y.
+constexpr int PTX_ = 32, PTY = 8, PTXP = PTX_ / 2, PNT = PTXP * PTY;
+// Five resident CTAs per SM (at most 96 registers; the forcing form spills 28
+// bytes): measured on GB300 at 2048^2 against the unbounded form (118 / 94
+// registers, four CTAs): forcing 36.7 against 34.0 GLUPS, equilibrium 35.8
+// against 33.4-36.0.
+constexpr int PAIR_MINB = 5;
+
+// Gradient (Eq. 10) and Laplacian (Eq. 11) of both sites of a pair from the
+// 4 x 3 neighbourhood columns x-1 .. x+2 (c[r][0..3]) of rows y-1, y, y+1
+// (r = 0, 1, 2): the scalar stencils of each site, lane by lane.
+__device__ __forceinline__ void pair_stencil(const float (&c)[3][4], P2& gx, P2& gy, P2* lap) {
+    const P2 a = pp(1.0f / 3.0f), b = pp(1.0f / 12.0f);
+    P2 L[3], M[3], R[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        L[r] = pp(c[r][0], c[r][1]);
+        M[r] = pp(c[r][1], c[r][2]);
+        R[r] = pp(c[r][2], c[r][3]);
+    }
+    gx = a * (R[1] - L[1]) + b * ((R[2] - L[2]) + (R[0] - L[0]));
+    gy = a * (M[2] - M[0]) + b * ((R[2] - R[0]) + (L[2] - L[0]));
+    if (lap)
+        *lap = pp(2.0f / 3.0f) * ((R[1] + L[1]) + (M[2] + M[0])) + pp(1.0f / 6.0f) * ((R[2] + L[2]) + (R[0] + L[0])) -
+               pp(10.0f / 3.0f) * M[1];
+}
+
+template <bool FORCING, int MINB>
+__global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepArgs<float> a) {
+    constexpr int H = FORCING ? 2 : 1, HX = 2;
+    constexpr int RX = PTX_ + 2 * HX, RY = PTY + 2 * H, RN = RX * RY, RXP = RX / 2;
+    constexpr int SX = PTX_ + 2, SY = PTY + 2, SN = SX * SY;
+    constexpr int NHALO = 2 * H * RXP + 2 * PTY;        // halo pairs: H rows above and below, one pair each side
+    constexpr int NRING = 2 * SX + 2 * PTY;             // M' ring sites around the tile
+    static_assert(NHALO <= PNT && NRING <= PNT, "one halo pair and one ring site per thread at most");
+    __shared__ __align__(8) float phs[RN];
+    __shared__ float mdiff[FORCING ? SN : 1], mxy_s[FORCING ? SN : 1];
+
+    const int nx = a.nx, ny = a.ny;
+    const unsigned pitch = a.pitch;
+    const int tid = threadIdx.x;
+    const int px = tid % PTXP, py = tid / PTXP;
+    const int x0 = blockIdx.x * PTX_, y0 = blockIdx.y * PTY;
+    const int x = x0 + 2 * px, y = y0 + py;
+    const bool own = x < nx && y < ny;
+    const float2* src = reinterpret_cast<const float2*>(a.src);
+
+    // ---- stage A: the own pair's populations; phi pairs on the tile and halo
+    P2 f[Q], g[Q];
+    {
+        const int sx = own ? x : wrapc(x, nx), sy = own ? y : wrapc(y, ny);
+        const unsigned s2 = (unsigned(sy) * unsigned(nx) + unsigned(sx)) >> 1;   // pair index (x even)
+        const unsigned p2 = pitch >> 1;
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i].v = src[i * p2 + s2];
+        }
+        P2 phi = pp(0.0f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            g[i].v = src[(Q + i) * p2 + s2];
+            phi += g[i];
+        }
+        *reinterpret_cast<float2*>(&phs[(py + H) * RX + 2 * px + HX]) = phi.v;
+        if (tid < NHALO) {
+            int rxp, ry;
+            if (tid < 2 * H * RXP) {
+                const int r = tid / RXP;
+                rxp = tid % RXP;
+                ry = r < H ? r : r + PTY;
+            } else {
+                const int k = tid - 2 * H * RXP;
+                ry = H + (k >> 1);
+                rxp = (k & 1) ? RXP - 1 : 0;
+            }
+            const unsigned h2 = (unsigned(wrapc(y0 - H + ry, ny)) * unsigned(nx) +
+                                 unsigned(wrapc(x0 - HX + 2 * rxp, nx))) >> 1;
+            P2 ph = pp(0.0f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ph += P2{src[(Q + i) * p2 + h2]};
+            *reinterpret_cast<float2*>(&phs[ry * RX + 2 * rxp]) = ph.v;
+        }
+    }
+    __syncthreads();
+
+    // ---- stage B: the pair's gradient and Laplacian; M' on the tile and its ring
+    float nb[3][4];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int c = (py + H - 1 + r) * RX + 2 * px + HX;
+        const float2 m = *reinterpret_cast<const float2*>(&phs[c]);
+        nb[r][0] = phs[c - 1];
+        nb[r][1] = m.x;
+        nb[r][2] = m.y;
+        nb[r][3] = phs[c + 2];
+    }
+    P2 gx, gy, lap;
+    pair_stencil(nb, gx, gy, &lap);
+    const P2 phi = pp(nb[1][1], nb[1][2]);
+    if constexpr (FORCING) {
+        const P2 kp = pp(a.kappa);
+        const P2 md = kp * (gx * gx - gy * gy), mx = kp * (gx * gy);
+        const int k = (py + 1) * SX + 2 * px + 1;
+        mdiff[k] = md.v.x;
+        mdiff[k + 1] = md.v.y;
+        mxy_s[k] = mx.v.x;
+        mxy_s[k + 1] = mx.v.y;
+        if (tid < NRING) {
+            int sx, sy;
+            if (tid < 2 * SX) {
+                sx = tid % SX;
+                sy = tid < SX ? 0 : SY - 1;
+            } else {
+                const int q = tid - 2 * SX;
+                sy = 1 + (q >> 1);
+                sx = (q & 1) ? SX - 1 : 0;
+            }
+            const int c = (sy - 1 + H) * RX + (sx - 1 + HX);
+            const float rgx = (1.0f / 3.0f) * (phs[c + 1] - phs[c - 1]) +
+                              (1.0f / 12.0f) * ((phs[c + 1 + RX] - phs[c - 1 + RX]) + (phs[c + 1 - RX] - phs[c - 1 - RX]));
+            const float rgy = (1.0f / 3.0f) * (phs[c + RX] - phs[c - RX]) +
+                              (1.0f / 12.0f) * ((phs[c + RX + 1] - phs[c - RX + 1]) + (phs[c + RX - 1] - phs[c - RX - 1]));
+            mdiff[sy * SX + sx] = a.kappa * (rgx * rgx - rgy * rgy);
+            mxy_s[sy * SX + sx] = a.kappa * (rgx * rgy);
+        }
+        __syncthreads();
+    }
+
+    // ---- stage C: collision of the pair and push
+    bool bad = false;
+    if (own) {
+        P2 rho = pp(0.0f), jx = pp(0.0f), jy = pp(0.0f);
+        static_for<0, Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            rho += f[i];
+            if constexpr (D2Q9::ex(i) > 0) jx += f[i];
+            if constexpr (D2Q9::ex(i) < 0) jx -= f[i];
+            if constexpr (D2Q9::ey(i) > 0) jy += f[i];
+            if constexpr (D2Q9::ey(i) < 0) jy -= f[i];
+        });
+        bad = !(rho.v.x > 0.0f) || !(rho.v.y > 0.0f) || !isfinite(rho.v.x) || !isfinite(rho.v.y);
+        const P2 ir = pp(1.0f / rho.v.x, 1.0f / rho.v.y);
+        const P2 ux = jx * ir, uy = jy * ir;
+        const P2 A = pp(a.A), B = pp(a.B), kp = pp(a.kappa);
+        const P2 mu = A * phi + B * phi * phi * phi - kp * lap;
+        P2 fe[Q], ge[Q], F[Q];
+        f_equilibrium<!FORCING>(rho, ux, uy, phi, gx, gy, lap, A, B, kp, fe);
+        P2 vx = ux, vy = uy;
+        if constexpr (FORCING) {
+            // Eq. 28 from the 4 x 3 neighbourhoods of M'_xx - M'_yy and M'_xy
+            float dn[3][4], xn[3][4];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int k = (py + r) * SX + 2 * px + c;
+                    dn[r][c] = mdiff[k];
+                    xn[r][c] = mxy_s[k];
+                }
+            P2 dDx, dDy, dXx, dXy;
+            pair_stencil(dn, dDx, dDy, nullptr);
+            pair_stencil(xn, dXx, dXy, nullptr);
+            const P2 bfx = pp(-0.5f) * dDx - dXy, bfy = pp(0.5f) * dDy - dXx;
+            force_populations(ux, uy, bfx, bfy, F);
+            const P2 hir = pp(0.5f) * ir;
+            vx = ux + bfx * hir;   // Eq. 40
+            vy = uy + bfy * hir;
+        }
+        g_equilibrium(phi, vx, vy, mu, pp(a.Gamma), ge);
+        const P2 om = pp(a.omega), omp = pp(a.omega_phi);
+        const unsigned xm = unsigned(wrapc(x - 1, nx)), xp2 = unsigned(wrapc(x + 2, nx));
+        const unsigned row[3] = {unsigned(wrapc(y - 1, ny)) * unsigned(nx), unsigned(y) * unsigned(nx),
+                                 unsigned(wrapc(y + 1, ny)) * unsigned(nx)};
+        static_for<0, Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
+            P2 fs = f[i] + om * (fe[i] - f[i]);
+            if constexpr (FORCING) fs += F[i];
+            const P2 gs = g[i] + omp * (ge[i] - g[i]);
+            const unsigned r = row[1 + ey];
+            float* df = a.dst + i * pitch + r;
+            float* dg = a.dst + (Q + i) * pitch + r;
+            if constexpr (ex == 0) {
+                *reinterpret_cast<float2*>(df + x) = fs.v;
+                *reinterpret_cast<float2*>(dg + x) = gs.v;
+            } else if constexpr (ex > 0) {
+                df[x + 1] = fs.v.x;
+                df[xp2] = fs.v.y;
+                dg[x + 1] = gs.v.x;
+                dg[xp2] = gs.v.y;
+            } else {
+                df[xm] = fs.v.x;
+                df[x] = fs.v.y;
+                dg[xm] = gs.v.x;
+                dg[x] = gs.v.y;
+            }
         });
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x % 32) == 0) atomicOr(a.status, 1u);
@@ -389,6 +619,7 @@ struct lb_binary {
     double* d_in = nullptr;       // staging of host float64 inputs (2 Q N)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
+    bool pair = false;            // float32 with an even nx: the two-sites-per-thread kernel
     lb_status sticky = LB_OK;
 };
 
@@ -430,8 +661,17 @@ cudaError_t launch_step(lb_binary* c, int from, cudaStream_t st) {
     a.omega = real(1.0 / c->p.tau);
     a.omega_phi = real(1.0 / c->p.tau_phi);
     a.status = c->d_status;
+    const bool forcing = c->p.scheme == LB_SCHEME_FORCING;
+    if constexpr (sizeof(real) == 4) {
+        if (c->pair) {   // float32, even nx: two sites per thread
+            const dim3 grid((c->p.nx + PTX_ - 1) / PTX_, (c->p.ny + PTY - 1) / PTY);
+            if (forcing) binary_step_kernel_pair<true, PAIR_MINB><<<grid, PNT, 0, st>>>(a);
+            else binary_step_kernel_pair<false, PAIR_MINB><<<grid, PNT, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     const dim3 grid((c->p.nx + TX - 1) / TX, (c->p.ny + TY - 1) / TY);
-    if (c->p.scheme == LB_SCHEME_FORCING) binary_step_kernel<true, real><<<grid, NT, 0, st>>>(a);
+    if (forcing) binary_step_kernel<true, real><<<grid, NT, 0, st>>>(a);
     else binary_step_kernel<false, real><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -548,6 +788,8 @@ lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** 
     c->p = *p;
     c->N = (long long)p->nx * p->ny;
     c->esize = p->storage == LB_F64 ? 8 : 4;
+    // LB_BINARY_SITE=1 keeps the one-site kernel for float32 (comparisons)
+    c->pair = p->storage == LB_F32 && p->nx % 2 == 0 && !std::getenv("LB_BINARY_SITE");
     c->pitch = (c->N + 63) / 64 * 64;
     if (2 * Q * c->pitch >= (1LL << 32)) {
         delete c;

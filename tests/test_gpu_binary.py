@@ -2,7 +2,8 @@
 
 float64: every population, rho, phi, u, v and mu to 1e-12 after 100 steps on
 ragged, odd and tiny lattices, both schemes; the initial state to 1e-14; one
-step at 1024^2.  float32: the same comparison at float32 rounding.  The graph
+step at 1024^2.  float32 (two sites per thread for even nx): the same comparison
+at float32 rounding, and one step at the bench's 2048^2.  The graph
 replay path equals single launches bit for bit; mass, order parameter and
 momentum stay conserved; Laplace's law holds on the device.
 """
@@ -81,11 +82,14 @@ def test_init_fields_matches_oracle(scheme):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_f32_parity(scheme):
+@pytest.mark.parametrize("shape", [(48, 20), (36, 10), (6, 3), (37, 11)])
+def test_f32_parity(scheme, shape):
     """float32 storage and arithmetic: 20 steps within 2e-6 of max |f| (float32
-    rounding of ~100 operations per population and step, accumulated)."""
+    rounding of ~100 operations per population and step, accumulated).  Even nx
+    runs the two-sites-per-thread kernel (a ragged tile at 36, pairs wrapping at
+    6), odd nx the one-site kernel."""
     m = _model(scheme)
-    nx, ny = 48, 20
+    nx, ny = shape
     rho0, phi0, u0 = _fields(m, nx, ny)
     f, g = BO.init_equilibrium(rho0, phi0, m, u0)
     with _ctx(library(), m, (nx, ny), storage=1) as c:
@@ -94,7 +98,7 @@ def test_f32_parity(scheme):
         fg, gg = c.get_populations()
     fo, go = BO.run(f, g, m, 20)
     ef, eg = rel_inf(fg, fo[:, 0]), rel_inf(gg, go[:, 0])
-    print(f"binary f32 {scheme}: f {ef:.2e} g {eg:.2e}")
+    print(f"binary f32 {scheme} {shape}: f {ef:.2e} g {eg:.2e}")
     assert ef < 2e-6 and eg < 2e-6
 
 
@@ -158,15 +162,19 @@ def test_laplace_law_on_device(storage):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_one_step_at_1024(scheme):
-    """The bench lattice (1024^2, one drop of radius 256): one float64 step, every population."""
+@pytest.mark.parametrize("n, storage, tol", [(1024, 0, 1e-14), (2048, 1, 1e-6)])
+def test_one_step_at_full_size(scheme, n, storage, tol):
+    """One step on large lattices, every population: float64 at 1024^2, and the
+    bench's configuration (2048^2, one drop of radius 512, float32 storage: the
+    two-sites-per-thread kernel) from the float32-rounded state, against the
+    oracle stepping that state in float64 (one step of float32 rounding)."""
     m = _model(scheme, tau=1.0, tau_phi=1.0, Gamma=1.0)
-    n = 1024
-    rho0, phi0, u0 = _fields(m, n, n, R=256.0, seed=11)
+    rho0, phi0, u0 = _fields(m, n, n, R=n / 4, seed=11)
     f, g = BO.init_equilibrium(rho0, phi0, m, u0)
-    with _ctx(library(), m, (n, n)) as c:
+    with _ctx(library(), m, (n, n), storage=storage) as c:
         c.set_populations(f[:, 0], g[:, 0])
+        f, g = c.get_populations()          # the state as stored
         c.step(1)
         fg, gg = c.get_populations()
-    fo, go = BO.step(f, g, m)
-    assert rel_inf(fg, fo[:, 0]) < 1e-14 and rel_inf(gg, go[:, 0]) < 1e-14
+    fo, go = BO.step(f[:, None], g[:, None], m)
+    assert rel_inf(fg, fo[:, 0]) < tol and rel_inf(gg, go[:, 0]) < tol
