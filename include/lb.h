@@ -115,7 +115,21 @@ lb_status lb_coexistence(double a, double b, double T, double* rho_l, double* rh
  * 32-bit integers). */
 lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out);
 
-/* Release every device allocation of the context.  NULL-safe. */
+/* Bytes of the two population buffers a context with parameters *p holds
+ * (host only; LB_EINVAL for invalid parameters or a NULL bytes). */
+lb_status lb_population_bytes(const lb_params* p, size_t* bytes);
+
+/* lb_create with the two population buffers in caller-owned device memory
+ * (for instance a framework's allocator): `populations` must be a device
+ * pointer on the current device, 256-byte aligned, with at least
+ * lb_population_bytes(p) bytes; it is used as is (no copy), must outlive the
+ * context and is not freed by lb_destroy.  Both are checked on the host
+ * before any device work (LB_EINVAL).  Everything else as lb_create. */
+lb_status lb_create_with_buffers(const lb_params* p, void* cuda_stream, void* populations, size_t bytes,
+                                 lb_ctx** out);
+
+/* Release every device allocation of the context (not a buffer given to
+ * lb_create_with_buffers).  NULL-safe. */
 lb_status lb_destroy(lb_ctx* ctx);
 
 /* Coexistence densities the context uses (liquid, gas). */

@@ -2,6 +2,7 @@
 // the Maxwell construction, device buffers, and kernel launches.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -106,6 +107,7 @@ struct lb_ctx {
     size_t pitch = 0;        // elements per population array (padded)
     size_t buf_bytes = 0;    // bytes of one population buffer
     char* fbuf = nullptr;    // two buffers back to back
+    bool own_fbuf = true;    // false: the caller's memory (lb_create_with_buffers), not freed here
     int cur = 0;
     bool aos = false;        // populations 1..Q-1 in the interleaved block layout (PopPtrs aos)
     double rho_l = 0, rho_g = 0;
@@ -454,7 +456,59 @@ lb_status lb_coexistence(double a, double b, double T, double* rho_l, double* rh
     return maxwell(a, b, T, rho_l, rho_g);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Bytes of the two population buffers of a context with parameters *p
+// (validated): 2 x pitch x (size of f_0 + (Q - 1) x size of f_i).
+size_t population_bytes(const lb_params* p) {
+    const size_t Q = p->lattice == LB_D2Q9 ? 9 : 19;
+    const size_t N = size_t(p->nx) * p->ny * p->nz;
+    const size_t pitch = (N + 127) / 128 * 128;
+    const size_t elem0 = p->storage == LB_F64 ? 8 : 4;
+    const size_t elemi = p->storage == LB_F64 ? 8 : (p->storage == LB_F32 ? 4 : 2);
+    return 2 * pitch * (elem0 + (Q - 1) * elemi);
+}
+
+lb_status create_impl(const lb_params* p, void* cuda_stream, void* pop_buf, size_t pop_bytes, lb_ctx** out);
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_population_bytes(const lb_params* p, size_t* bytes) {
+    if (!bytes) return fail(LB_EINVAL, "null output");
+    lb_status s = validate(p);
+    if (s != LB_OK) return s;
+    *bytes = population_bytes(p);
+    return LB_OK;
+}
+
 lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
+    return create_impl(p, cuda_stream, nullptr, 0, out);
+}
+
+lb_status lb_create_with_buffers(const lb_params* p, void* cuda_stream, void* populations, size_t bytes,
+                                 lb_ctx** out) {
+    if (out) *out = nullptr;
+    if (!populations) return fail(LB_EINVAL, "null population buffer");
+    if (reinterpret_cast<uintptr_t>(populations) % 256 != 0)
+        return fail(LB_EINVAL, "population buffer must be 256-byte aligned");
+    lb_status s = validate(p);
+    if (s != LB_OK) return s;
+    if (bytes < population_bytes(p))
+        return fail(LB_EINVAL, "population buffer too small: " + std::to_string(bytes) + " < " +
+                                   std::to_string(population_bytes(p)) + " bytes (lb_population_bytes)");
+    return create_impl(p, cuda_stream, populations, bytes, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+lb_status create_impl(const lb_params* p, void* cuda_stream, void* pop_buf, size_t pop_bytes, lb_ctx** out) {
+    (void)pop_bytes;
     if (!out) return fail(LB_EINVAL, "null output");
     *out = nullptr;
     lb_status s = validate(p);
@@ -502,10 +556,20 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     // the interleaved layout holds whole blocks of sites (pitch is a multiple of 128)
     c->aos = c->ks.aos && c->p.storage >= LB_F16DEV && c->pitch % lbk::AOS_SITES == 0;
 
-    cudaError_t e = cudaMalloc(&c->fbuf, 2 * c->buf_bytes);
-    if (e != cudaSuccess) { delete c; return fail(LB_ENOMEM, std::string("population buffers: ") + cudaGetErrorString(e)); }
+    cudaError_t e = cudaSuccess;
+    if (pop_buf) {
+        c->fbuf = static_cast<char*>(pop_buf);
+        c->own_fbuf = false;
+    } else {
+        e = cudaMalloc(&c->fbuf, 2 * c->buf_bytes);
+        if (e != cudaSuccess) { delete c; return fail(LB_ENOMEM, std::string("population buffers: ") + cudaGetErrorString(e)); }
+    }
     e = cudaMalloc(&c->d_status, sizeof(unsigned));
-    if (e != cudaSuccess) { cudaFree(c->fbuf); delete c; return fail(LB_ENOMEM, "status word"); }
+    if (e != cudaSuccess) {
+        if (c->own_fbuf) cudaFree(c->fbuf);
+        delete c;
+        return fail(LB_ENOMEM, "status word");
+    }
     cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
 
     // launch geometry of the fused step: one CTA per TX x TY column tile and z chunk;
@@ -539,10 +603,14 @@ lb_status lb_create(const lb_params* p, void* cuda_stream, lb_ctx** out) {
     return LB_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
 lb_status lb_destroy(lb_ctx* c) {
     if (!c) return LB_OK;
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-    cudaFree(c->fbuf);
+    if (c->own_fbuf) cudaFree(c->fbuf);
     cudaFree(c->d_status);
     cudaFree(c->w_rho);
     cudaFree(c->w_u);

@@ -431,8 +431,14 @@ __device__ __forceinline__ void step2d_pair_tile(const Tile2DArgs& args, int x0,
 }
 
 // One step of a single D2Q9 lattice: one CTA of (TX / 2) * TY threads per tile.
+// Resident CTAs of 128 threads per SM: 10 for 16-bit storage (48 registers;
+// measured on GB300 at 2048^2 against the unbounded 56 registers: fp16
+// deviations forcing 73.6 against 71.6 GLUPS, equilibrium 94.1 against 89.9),
+// 8 for float32 (64 registers, what the unbounded form takes; 10 cost it 12%,
+// a bound of 1 let it grow to 89 registers and cost 11%).
 template <bool FORCING, class S, int TX, int TY>
-__global__ void __launch_bounds__((TX / 2) * TY) step_kernel2d_pk(const Tile2DArgs args) {
+__global__ void __launch_bounds__((TX / 2) * TY, (PairIO<S>::RAW16 ? 1280 : 1024) / ((TX / 2) * TY))
+    step_kernel2d_pk(const Tile2DArgs args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (args.pair) step2d_pair_tile<FORCING, S, TX, TY, true>(args, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
     else step2d_pair_tile<FORCING, S, TX, TY, false>(args, blockIdx.x * TX, blockIdx.y * TY, smem_raw);

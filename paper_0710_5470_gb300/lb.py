@@ -75,6 +75,9 @@ _SIGNATURES = {
     "lb_last_error": (C.c_char_p, []),
     "lb_coexistence": (C.c_int, [C.c_double, C.c_double, C.c_double, _DPTR, _DPTR]),
     "lb_create": (C.c_int, [C.POINTER(lb_params), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lb_population_bytes": (C.c_int, [C.POINTER(lb_params), C.POINTER(C.c_size_t)]),
+    "lb_create_with_buffers": (C.c_int, [C.POINTER(lb_params), C.c_void_p, C.c_void_p, C.c_size_t,
+                                         C.POINTER(C.c_void_p)]),
     "lb_destroy": (C.c_int, [C.c_void_p]),
     "lb_get_coexistence": (C.c_int, [C.c_void_p, _DPTR, _DPTR]),
     "lb_init_drops": (C.c_int, [C.c_void_p, C.c_int, _DPTR, _DPTR, C.c_double]),
@@ -238,6 +241,16 @@ def params_hash(lattice: int, shape, a: float, b: float, T: float, kappa: float,
     return h.value
 
 
+def population_bytes(lattice: int, shape, a: float, b: float, T: float, kappa: float, tau: float,
+                     scheme: int = EQUILIBRIUM, storage: int = F64, rho_ref: float = 0.0) -> int:
+    """lb_population_bytes (host only): bytes of a context's two population buffers."""
+    nx, ny, nz = (tuple(shape) + (1,))[:3] if len(shape) == 2 else tuple(shape)
+    p = lb_params(lattice, nx, ny, nz, a, b, T, kappa, tau, scheme, storage, rho_ref)
+    n = C.c_size_t()
+    _check(load_library().lb_population_bytes(C.byref(p), C.byref(n)))
+    return n.value
+
+
 def debug_bounds():
     """lb_debug_bounds: (index checks compiled in, first recorded violation or 0)."""
     c, v = C.c_int(), C.c_ulonglong()
@@ -253,7 +266,11 @@ class Context:
     """One lattice (lb_create ... lb_destroy)."""
 
     def __init__(self, lattice: int, shape, a: float, b: float, T: float, kappa: float, tau: float,
-                 scheme: int = EQUILIBRIUM, storage: int = F64, rho_ref: float = 0.0, stream=None):
+                 scheme: int = EQUILIBRIUM, storage: int = F64, rho_ref: float = 0.0, stream=None,
+                 buffer=None):
+        """buffer: optional caller-owned device memory for the population buffers
+        (lb_create_with_buffers), an object with data_ptr() and nbytes (a CUDA
+        tensor) or a (device pointer, bytes) pair; kept referenced by the context."""
         lib = load_library()
         nx, ny, nz = (tuple(shape) + (1,))[:3] if len(shape) == 2 else tuple(shape)
         self.params = lb_params(lattice, nx, ny, nz, a, b, T, kappa, tau, scheme, storage, rho_ref)
@@ -263,7 +280,13 @@ class Context:
         self.n = nx * ny * nz
         h = C.c_void_p()
         st = C.c_void_p(int(stream)) if stream else None
-        _check(lib.lb_create(C.byref(self.params), st, C.byref(h)))
+        self._buffer = buffer
+        if buffer is None:
+            _check(lib.lb_create(C.byref(self.params), st, C.byref(h)))
+        else:
+            ptr, nbytes = (buffer.data_ptr(), buffer.nbytes) if hasattr(buffer, "data_ptr") else buffer
+            _check(lib.lb_create_with_buffers(C.byref(self.params), st, C.c_void_p(int(ptr)), int(nbytes),
+                                              C.byref(h)))
         self._h = h
         self._lib = lib
 

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from tests.helpers import A_VDW, B_VDW, library
@@ -122,4 +124,28 @@ def test_binary_parameters_rejected_before_device_work():
     for shape, extra in (((0, 8), {}), ((8, 8), dict(scheme=2)), ((8, 8), dict(storage=2))):
         with pytest.raises(lb.LBError) as e:
             lb.BinaryContext(shape, **ok, **extra)
+        assert e.value.status == 1
+
+
+def test_population_bytes_host_only():
+    """lb_population_bytes: 2 buffers x pitch (sites rounded up to 128) x bytes per site."""
+    lb = library()
+    per_site = {lb.F64: (8, 8), lb.F32: (4, 4), lb.F16DEV: (4, 2), lb.BF16DEV: (4, 2)}
+    for lat, shape, q in ((lb.D2Q9, (37, 11), 9), (lb.D3Q19, (32, 8, 5), 19)):
+        n = int(np.prod(shape))
+        pitch = (n + 127) // 128 * 128
+        for st, (b0, bi) in per_site.items():
+            got = lb.population_bytes(lat, shape, A_VDW, B_VDW, 0.55, 0.01, 0.8, storage=st)
+            assert got == 2 * pitch * (b0 + (q - 1) * bi), (lat, st)
+    with pytest.raises(lb.LBError):
+        lb.population_bytes(lb.D2Q9, (8, 8), A_VDW, B_VDW, 0.55, 0.01, 0.5)
+
+
+def test_caller_buffer_checked_before_device_work():
+    """lb_create_with_buffers refuses a NULL, unaligned or too small buffer on the host."""
+    lb = library()
+    need = lb.population_bytes(lb.D2Q9, (16, 8), A_VDW, B_VDW, 0.55, 0.01, 0.8)
+    for ptr, nbytes in ((0, need), (256 * 1000 + 8, need), (256 * 1000, need - 1)):
+        with pytest.raises(lb.LBError) as e:
+            lb.Context(0, (16, 8), A_VDW, B_VDW, 0.55, 0.01, 0.8, buffer=(ptr, nbytes))
         assert e.value.status == 1
