@@ -42,13 +42,18 @@ order parameter phi in place of the density wherever a gradient enters:
 * B8  Stencils: the gradient and Laplacian of phi are Eq. 10 / Eq. 11
       (Eq. 29 in 3D) at the paper's optimum coefficients.
 
+Both lattices: D2Q9 with the weights of Sec. VIII, D3Q19 with those of Eq. 31
+(readings R4, R5), the forcing scheme in 3D by reading R7.
+
 Parity status: pinned by ``tests/test_binary_oracle.py`` (reduction to the
 textbook D2Q9 equilibrium, the moments of f^eq and g^eq against the closed
 forms B3 / B5, exact conservation of mass, order parameter and momentum, the
 stationary flat interface phi* tanh(x / w), w = sqrt(-2 kappa / A), Laplace's
 law with sigma = 4 kappa phi*^2 / (3 w), phi -> -phi symmetry, the forcing
 scheme's smaller spurious velocity, the diffusion of phi with mobility
-Gamma (tau_phi - 1/2) and the shear-wave decay with nu = (tau - 1/2)/3).
+Gamma (tau_phi - 1/2) and the shear-wave decay with nu = (tau - 1/2)/3; in 3D
+the moments, conservation, phi -> -phi symmetry, the uniform fixed point and
+the shear wave).
 """
 from __future__ import annotations
 

@@ -249,3 +249,87 @@ def test_shear_wave_decays_with_viscosity(tau):
     u = BO.observables(f, g, m)[2]
     nu = (tau - 0.5) / 3
     assert abs(_mode_amplitude(u[0][0, :, 0], k) / 1e-4 / np.exp(-nu * k * k * t) - 1) < 0.01
+
+
+# ---------------------------------------------------------------- D3Q19 (Sec. VII weights)
+
+def _smooth_fields_3d(n=(12, 10, 8), seed=5):
+    nx, ny, nz = n
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = inputs.noise(seed, (8,))
+    kx, ky, kz = 2 * np.pi / nx, 2 * np.pi / ny, 2 * np.pi / nz
+    rho = 1.0 + 0.05 * np.sin(kx * x + r[0]) * np.cos(kz * z + r[1])
+    phi = 0.8 * np.sin(kx * x + r[2]) + 0.1 * np.cos(ky * y + r[3]) + 0.05 * np.sin(kz * z + r[4])
+    u = [0.03 * np.cos(ky * y + r[5]), 0.02 * np.sin(kz * z + r[6]), 0.01 * np.cos(kx * x + r[7])]
+    return rho, phi, u
+
+
+def _model3(scheme="equilibrium", **kw):
+    p = dict(A=A_BIN, B=B_BIN, kappa=K_BIN, Gamma=0.7, tau=0.8, tau_phi=0.9)
+    p.update(kw)
+    return BO.BinaryModel("D3Q19", p["A"], p["B"], p["kappa"], p["Gamma"], p["tau"], p["tau_phi"], scheme=scheme)
+
+
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_f_and_g_moments_d3q19(scheme):
+    """The D3Q19 weights (Eq. 31 with readings R4, R5) give the moments of B3 / B5 in 3D."""
+    m = _model3(scheme)
+    rho, phi, u = _smooth_fields_3d()
+    grad = O.gradient(phi, m.stencils)
+    lap = O.laplacian(phi, m.stencils)
+    feq = BO.equilibrium_f(rho, phi, u, grad, lap, m, include_m_terms=scheme == "equilibrium")
+    mu = m.A * phi + m.B * phi ** 3 - m.kappa * lap
+    geq = BO.equilibrium_g(phi, u, BO.chemical_potential(phi, lap, m.A, m.B, m.kappa), m)
+    e = m.e.astype(np.float64)
+    g2 = sum(ga ** 2 for ga in grad)
+    assert np.abs(feq.sum(axis=0) - rho).max() < 1e-15 and np.abs(geq.sum(axis=0) - phi).max() < 1e-15
+    for a in range(3):
+        assert np.abs(np.einsum("i,i...->...", e[:, a], feq) - rho * u[a]).max() < 1e-15
+        assert np.abs(np.einsum("i,i...->...", e[:, a], geq) - phi * u[a]).max() < 1e-15
+        for b in range(3):
+            P = (BO.p0(rho, phi, m.A, m.B) - m.kappa * phi * lap - 0.5 * m.kappa * g2) * (a == b) \
+                + m.kappa * grad[a] * grad[b]
+            if scheme == "forcing":
+                P = P - m.kappa * (grad[a] * grad[b] - 0.5 * g2 * (a == b))
+            mf = np.einsum("i,i,i...->...", e[:, a], e[:, b], feq)
+            mg = np.einsum("i,i,i...->...", e[:, a], e[:, b], geq)
+            assert np.abs(mf - (P + rho * u[a] * u[b])).max() < 1e-14, (a, b)
+            assert np.abs(mg - (m.Gamma * mu * (a == b) + phi * u[a] * u[b])).max() < 1e-15, (a, b)
+
+
+@pytest.mark.parametrize("scheme", ["equilibrium", "forcing"])
+def test_conservation_and_symmetry_d3q19(scheme):
+    """3D: mass, sum phi and momentum conserved; phi -> -phi symmetric; uniform bulk fixed."""
+    m = _model3(scheme)
+    shape = (10, 12, 14)
+    w = BO.interface_width(m.A, m.kappa)
+    phi0 = BO.drop_phi(shape, [(7.0, 6.0, 5.0)], [4.0], 1.0, -1.0, w)
+    rho0 = 1.0 + 1e-3 * inputs.noise(9, shape)
+    out = []
+    for sign in (1.0, -1.0):
+        f, g = BO.init_equilibrium(rho0, sign * phi0, m)
+        d0 = BO.diagnostics(f, g, m)
+        f, g = BO.run(f, g, m, 25)
+        d1 = BO.diagnostics(f, g, m)
+        assert abs(d1["mass"] - d0["mass"]) < 1e-10 and abs(d1["phi_total"] - d0["phi_total"]) < 1e-10
+        for a in range(3):
+            assert abs(d1["momentum"][a] - d0["momentum"][a]) < 1e-11
+        out.append((f, g))
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-13 and np.abs(out[0][1] + out[1][1]).max() < 1e-13
+    fb, gb = BO.init_equilibrium(np.full((3, 4, 5), 1.2), np.full((3, 4, 5), 1.0), m)
+    f1, g1 = BO.run(fb, gb, m, 3)
+    assert np.abs(f1 - fb).max() < 1e-15 and np.abs(g1 - gb).max() < 1e-15
+
+
+def test_shear_wave_d3q19():
+    """A shear wave u_x = U sin(k z) in a bulk phase decays as exp(-nu k^2 t), nu = (tau - 1/2)/3."""
+    n, t, tau = 32, 150, 1.1
+    k = 2 * np.pi / n
+    m = _model3(tau=tau)
+    z = np.arange(n)[:, None, None] * np.ones((1, 2, 2))
+    ux = 1e-4 * np.sin(k * z)
+    f, g = BO.init_equilibrium(np.ones_like(ux), np.ones_like(ux), m, u0=[ux, 0 * ux, 0 * ux])
+    f, g = BO.run(f, g, m, t)
+    u = BO.observables(f, g, m)[2]
+    nu = (tau - 0.5) / 3
+    assert abs(_mode_amplitude(u[0][:, 0, 0], k) / 1e-4 / np.exp(-nu * k * k * t) - 1) < 0.01
