@@ -471,6 +471,31 @@ def binary_block(lb, stream, peak, dist, world, warmup, cpu: bool):
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                              "bytes_per_lu": bpl},
                 "max_v": stt["max_v"], "status": stt["status"]}
+    # D3Q19: 128^3, one drop R = 32; two launches per step (the phi pass and the
+    # fused step), algorithmic bytes the 38 populations read and written
+    n3 = 128
+    phi3 = bin_runs.drop_phi(n3, 32.0, b["A"], b["kappa"], b["B"], dim=3)
+    out["workload_3d"] = (f"D3Q19 {n3}^3 periodic, one drop R=32 of phi=+1 in phi=-1 (tanh, width {w:g}), "
+                          f"rho=1, the same parameters")
+    for scheme in ("forcing", "equilibrium"):
+        for sname, st_code, bpl, steps in (("f32", lb.F32, 304, 200), ("f64", lb.F64, 608, 40)):
+            ctx = lb.BinaryContext((n3, n3, n3), b["A"], b["B"], b["kappa"], b["Gamma"], b["tau"], b["tau_phi"],
+                                   scheme=lb.FORCING if scheme == "forcing" else lb.EQUILIBRIUM, storage=st_code,
+                                   stream=stream.cuda_stream)
+            ctx.init_fields(np.ones((n3, n3, n3)), phi3)
+            ctx.step(max(warmup, 64) if sname == "f32" else 8)
+            ctx.synchronize()
+            ms = reduce_max(dist, time_steps(ctx, stream, steps, dist))
+            stt = ctx.stats()
+            ctx.close()
+            t = ms / steps / 1e3
+            ach = bpl * n3 ** 3 / t / 1e9
+            out["runs"][f"d3q19_{scheme}_{sname}"] = {
+                "value": n3 ** 3 * steps * world / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
+                "ms_per_step": ms / steps,
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                             "bytes_per_lu": bpl, "note": "the phi pass adds 80 B (float32) per update"},
+                "max_v": stt["max_v"], "status": stt["status"]}
     if cpu:
         from oracle import binary_oracle as BO
         m = BO.BinaryModel("D2Q9", b["A"], b["B"], b["kappa"], b["Gamma"], b["tau"], b["tau_phi"], scheme="forcing")

@@ -467,7 +467,7 @@ lb_status lb_work_list(int sms, int ctas_per_sm, int nx, int ny, int nz, int til
  * launch runs for milliseconds (float64 ~4000, float32 ~2e5 on a GB300). */
 lb_status lb_fma_peak(int precision, int iters, double* tflops);
 
-/* ---- Binary fluid (D2Q9) --------------------------------------------------
+/* ---- Binary fluid (D2Q9, D3Q19) -------------------------------------------
  *
  * The paper states (Sec. I) that its analysis applies equally to other
  * multiphase systems solved by the free-energy method, binary fluids among
@@ -490,15 +490,17 @@ lb_status lb_fma_peak(int precision, int iters, double* tflops);
  *                 F_i of Eq. 27, and g^eq takes the fluid velocity
  *                 v = u + g/(2 rho) of Eq. 40 in place of u.
  * Stencils: the gradient and Laplacian of phi by Eqs. 10 and 11 at the
- * optimum (B = 1/12, D = 1/6), the force stencil with F = 1/12.
+ * optimum (B = 1/12, D = 1/6), the force stencil with F = 1/12; in 3D
+ * Eq. 29 with A = 1/6, B = 1/12, C = 1/3, D = 1/6 and the weights of Eq. 31.
  * Storage: LB_F64 (float64 arithmetic) or LB_F32 (float32 arithmetic).
- * Populations exchanged with the host: float64 [i][y][x] for f and for g,
- * i in the paper's D2Q9 order, after streaming.  Conventions otherwise as
+ * Populations exchanged with the host: float64 [i][z][y][x] for f and for g,
+ * i in the paper's order (Sec. II, Sec. VII), after streaming.  Conventions otherwise as
  * above (caller-owned host arrays, status codes, sticky device errors). */
 typedef struct lb_binary lb_binary;
 
 typedef struct {
-    int nx, ny;           /* sites per direction, >= 1 (periodic) */
+    int lattice;          /* lb_lattice: LB_D2Q9 or LB_D3Q19 (Sec. VII weights, reading R7 for forcing) */
+    int nx, ny, nz;       /* sites per direction, >= 1 (periodic); nz = 1 for D2Q9 */
     double A, B;          /* free-energy coefficients: A < 0 < B */
     double kappa;         /* gradient coefficient, >= 0 */
     double Gamma;         /* mobility coefficient of g^eq, > 0 */
@@ -511,7 +513,7 @@ typedef struct {
 typedef struct {
     double mass;          /* sum rho */
     double phi_total;     /* sum phi */
-    double momentum[2];   /* sum rho u */
+    double momentum[3];   /* sum rho u (the z component 0 for D2Q9) */
     double max_u;         /* max |u| (Eq. 3) */
     double max_v;         /* max |v| (Eq. 40 in the forcing scheme; = max_u otherwise) */
     double min_phi, max_phi;
@@ -526,19 +528,20 @@ typedef struct {
  * on it. */
 lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** out);
 lb_status lb_binary_destroy(lb_binary* ctx);
-/* f = f^eq, g = g^eq of host fields rho [N], phi [N] and u [2][N] (NULL: u = 0),
+/* f = f^eq, g = g^eq of host fields rho [N], phi [N] and u [D][N] (NULL: u = 0),
  * stencils of phi taken on the device (the oracle's initial state); resets the
  * step counter.  rho must be positive and finite (LB_EINVAL otherwise). */
 lb_status lb_binary_init_fields(lb_binary* ctx, const double* rho, const double* phi, const double* u);
-/* Replaces / reads the populations: host f [9][N] and g [9][N], float64 (rounded
+/* Replaces / reads the populations: host f [Q][N] and g [Q][N], float64 (rounded
  * to float32 for LB_F32 storage).  set resets the step counter. */
 lb_status lb_binary_set_populations(lb_binary* ctx, const double* f, const double* g);
 lb_status lb_binary_get_populations(lb_binary* ctx, double* f, double* g);
-/* nsteps fused steps (one kernel launch each; CUDA-graph replay on long runs). */
+/* nsteps steps (D2Q9: one fused kernel launch each; D3Q19: a phi pass and the
+ * fused step; CUDA-graph replay on long runs). */
 lb_status lb_binary_step(lb_binary* ctx, int nsteps);
 lb_status lb_binary_synchronize(lb_binary* ctx);
 /* Host float64 fields of the current state; any pointer may be NULL.
- * rho [N], phi [N], u [2][N] (Eq. 3), v [2][N] (Eq. 40; = u in the equilibrium
+ * rho [N], phi [N], u [D][N] (Eq. 3), v [D][N] (Eq. 40; = u in the equilibrium
  * scheme), mu [N]. */
 lb_status lb_binary_fields(lb_binary* ctx, double* rho, double* phi, double* u, double* v, double* mu);
 lb_status lb_binary_stats_get(lb_binary* ctx, lb_binary_stats* out);

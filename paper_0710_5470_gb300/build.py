@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "liblb.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(BUILD_DEBUG, "liblb_debug.so")
 SOURCES = ["kern_d2q9.cu", "kern_d2q9_pk.cu", "kern_d3q19.cu", "kern_d3q19_pk.cu", "kern_d3q19_pk_eq.cu", "kern_batch.cu", "lb_api.cu", "cnn.cu", "cnn3d.cu", "noalloc.cu",
-           "param2d.cu", "peak.cu", "binary2d.cu"]
+           "param2d.cu", "peak.cu", "binary2d.cu", "binary3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,4 +1,5 @@
-// Binary-fluid free-energy lattice Boltzmann on D2Q9: the liquid-gas
+// Binary-fluid free-energy lattice Boltzmann: the D2Q9 kernels and the C ABI
+// of both lattices (the D3Q19 kernels are in binary3d.cu).  The liquid-gas
 // construction of Pooley & Furtado (Secs. II-VI) carried over to a symmetric
 // binary fluid with an order parameter phi, as the paper says it applies
 // (Sec. I).  The model (free energy, mu, p0, f^eq, g^eq, forcing) is stated
@@ -28,49 +29,17 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lb.h"
-#include "lattice.cuh"
-#include "aux_kernels.cuh"
-#include "step3d_pk.cuh"   // lbk::P2: packed float32 pairs
+#include "binary_common.cuh"
+#include "binary_launch.h"
 
 // Sets the thread-local message returned by lb_last_error (defined in lb_api.cu).
 void lb_internal_set_error(const char* msg);
 
 namespace lbb {
 
-using lbk::D2Q9;
-using lbk::P2;
-using lbk::pp;
-using lbk::static_for;
-
 constexpr int Q = 9;
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int GRAPH_STEPS = 64;   // steps per captured graph (even: a replay ends in its start buffer)
-
-// Periodic wrap of an offset coordinate: one compare-and-add for v in
-// [-n, 2n), the integer modulo otherwise (lattices narrower than a tile).
-__host__ __device__ __forceinline__ int wrapc(int v, int n) {
-    if (v < 0) v += n;
-    else if (v >= n) v -= n;
-    if (unsigned(v) >= unsigned(n)) {
-        v %= n;
-        if (v < 0) v += n;
-    }
-    return v;
-}
-
-template <class real>
-struct StepArgs {
-    const real* src;     // populations after streaming: f_0..f_8 then g_0..g_8, each `pitch` elements
-    real* dst;
-    unsigned pitch;      // 18 pitch < 2^32: element offsets within a set are 32-bit
-    int nx, ny;
-    real A, B, kappa, Gamma, omega, omega_phi;   // omega = 1/tau, omega_phi = 1/tau_phi
-    unsigned* status;
-};
-
-// Weights of the optimum (Sec. VIII): w_i = w^p_i = w^t_i, and w^ab_i.
-template <int I>
-__device__ __forceinline__ constexpr double W() { return lbk::w_vel<D2Q9>(I); }
 
 // Gradient (Eq. 10, A = 1/3, B = 1/12) and Laplacian (Eq. 11, C = 2/3,
 // D = 1/6) of a field on a row-major shared-memory region of row length RX
@@ -86,92 +55,6 @@ __device__ __forceinline__ real laplacian(const real* p, int c) {
     const real C = real(2.0 / 3.0), D = real(1.0 / 6.0);
     return C * ((p[c + 1] + p[c - 1]) + (p[c + RX] + p[c - RX])) +
            D * ((p[c + RX + 1] + p[c + RX - 1]) + (p[c - RX + 1] + p[c - RX - 1])) - real(10.0 / 3.0) * p[c];
-}
-
-// The arithmetic below is written once for a scalar (float, double) and for
-// a packed pair of float32 sites (lbk::P2: FADD2 / FMUL2 / FFMA2, one
-// instruction for two sites); cst<real> makes a constant of either.
-template <class real>
-__device__ __forceinline__ real cst(double d) { return real(d); }
-template <>
-__device__ __forceinline__ P2 cst<P2>(double d) { return pp(float(d)); }
-
-// e_i . (ux, uy) for a velocity with components in {-1, 0, 1}: adds only.
-template <int EX, int EY, class real>
-__device__ __forceinline__ real edot(real ux, real uy) {
-    if constexpr (EX == 0 && EY == 0) return cst<real>(0.0);
-    else if constexpr (EX == 0) return EY > 0 ? uy : -uy;
-    else if constexpr (EY == 0) return EX > 0 ? ux : -ux;
-    else {
-        const real a = EX > 0 ? ux : -ux;
-        return EY > 0 ? a + uy : a - uy;
-    }
-}
-
-// The velocity part of Eq. 5 with lambda = 0 for population I of a density
-// `dens` moving with (ux, uy): w_I (dens e.u + 3/2 [dens (e.u)^2 - dens |u|^2 / 3]).
-template <int I, class real>
-__device__ __forceinline__ real velocity_part(real dens, real ux, real uy, real usq3) {
-    const real eu = edot<D2Q9::ex(I), D2Q9::ey(I)>(ux, uy);
-    const real de = dens * eu;
-    return cst<real>(W<I>()) * (de + cst<real>(1.5) * (de * eu - dens * usq3));
-}
-
-// f^eq_i, i = 1..8, of the binary model (Eq. 5 with p0 = rho/3 + A/2 phi^2 +
-// 3B/4 phi^4, w^t kappa phi lap(phi) and, in the equilibrium scheme,
-// sum_{a<=b} w^ab kappa d_a phi d_b phi); f^eq_0 = rho - sum (Eq. 6).
-template <bool MTERMS, class real>
-__device__ __forceinline__ void f_equilibrium(real rho, real ux, real uy, real phi, real gx, real gy, real lap,
-                                              real A, real B, real kappa, real (&fe)[Q]) {
-    const real phi2 = phi * phi;
-    const real p0 = rho * cst<real>(1.0 / 3.0) + cst<real>(0.5) * A * phi2 + cst<real>(0.75) * B * phi2 * phi2;
-    const real iso = p0 - kappa * phi * lap;
-    const real mxx = kappa * gx * gx, myy = kappa * gy * gy, mxy = kappa * gx * gy;
-    const real usq3 = (ux * ux + uy * uy) * cst<real>(1.0 / 3.0);
-    real sum = cst<real>(0.0);
-    static_for<1, Q>([&](auto K) {
-        constexpr int i = decltype(K)::value;
-        real pr = cst<real>(W<i>()) * iso;
-        if constexpr (MTERMS) {
-            pr += cst<real>(lbk::w_m<D2Q9>(i, 0, 0)) * mxx + cst<real>(lbk::w_m<D2Q9>(i, 1, 1)) * myy;
-            if constexpr (lbk::w_m<D2Q9>(i, 0, 1) != 0.0) pr += cst<real>(lbk::w_m<D2Q9>(i, 0, 1)) * mxy;
-        }
-        fe[i] = velocity_part<i>(rho, ux, uy, usq3) + pr;
-        sum += fe[i];
-    });
-    fe[0] = rho - sum;
-}
-
-// g^eq_i = velocity part of phi moving with (vx, vy) + w_i Gamma mu (i >= 1),
-// g^eq_0 = phi - sum: sum g = phi, sum g e = phi v, sum g e e = Gamma mu I + phi v v.
-template <class real>
-__device__ __forceinline__ void g_equilibrium(real phi, real vx, real vy, real mu, real Gamma, real (&ge)[Q]) {
-    const real gm = Gamma * mu;
-    const real usq3 = (vx * vx + vy * vy) * cst<real>(1.0 / 3.0);
-    real sum = cst<real>(0.0);
-    static_for<1, Q>([&](auto K) {
-        constexpr int i = decltype(K)::value;
-        ge[i] = velocity_part<i>(phi, vx, vy, usq3) + cst<real>(W<i>()) * gm;
-        sum += ge[i];
-    });
-    ge[0] = phi - sum;
-}
-
-// Force populations of Eq. 27, F_i = w_i (e.g + 3/2 [2 (e.u)(e.g) - 2 u.g / 3]),
-// F_0 = -sum (reading R8: sum_i F_i = 0).
-template <class real>
-__device__ __forceinline__ void force_populations(real ux, real uy, real gx, real gy, real (&F)[Q]) {
-    const real ug23 = (ux * gx + uy * gy) * cst<real>(2.0 / 3.0);
-    real sum = cst<real>(0.0);
-    static_for<1, Q>([&](auto K) {
-        constexpr int i = decltype(K)::value;
-        constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
-        const real eg = edot<ex, ey>(gx, gy);
-        const real eu = edot<ex, ey>(ux, uy);
-        F[i] = cst<real>(W<i>()) * (eg + cst<real>(1.5) * (cst<real>(2.0) * eu * eg - ug23));
-        sum += F[i];
-    });
-    F[0] = -sum;
 }
 
 template <bool FORCING, class real>
@@ -258,7 +141,8 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
         const real ux = jx * ir, uy = jy * ir;
         const real mu = a.A * phi + a.B * phi * phi * phi - a.kappa * lap;
         real fe[Q], ge[Q], F[Q];
-        f_equilibrium<!FORCING>(rho, ux, uy, phi, gx, gy, lap, a.A, a.B, a.kappa, fe);
+        const real u[2] = {ux, uy}, gr[2] = {gx, gy};
+        f_equilibrium<D2Q9, !FORCING>(rho, u, phi, gr, lap, a.A, a.B, a.kappa, fe);
         real vx = ux, vy = uy;
         if constexpr (FORCING) {
             // Eq. 28: g_x = -1/2 d_x (M'_xx - M'_yy) - d_y M'_xy, g_y = 1/2 d_y (M'_xx - M'_yy) - d_x M'_xy
@@ -267,11 +151,13 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
             stencil<SX>(mdiff, k, dDx, dDy);
             stencil<SX>(mxy_s, k, dXx, dXy);
             const real bfx = real(-0.5) * dDx - dXy, bfy = real(0.5) * dDy - dXx;
-            force_populations(ux, uy, bfx, bfy, F);
+            const real bf[2] = {bfx, bfy};
+            force_populations<D2Q9>(u, bf, F);
             vx = ux + bfx * (real(0.5) * ir);   // Eq. 40
             vy = uy + bfy * (real(0.5) * ir);
         }
-        g_equilibrium(phi, vx, vy, mu, a.Gamma, ge);
+        const real v[2] = {vx, vy};
+        g_equilibrium<D2Q9>(phi, v, mu, a.Gamma, ge);
         const int xw[3] = {wrapc(x - 1, nx), x, wrapc(x + 1, nx)};
         const int yw[3] = {wrapc(y - 1, ny), y, wrapc(y + 1, ny)};
         static_for<0, Q>([&](auto K) {
@@ -438,7 +324,8 @@ __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepA
         const P2 A = pp(a.A), B = pp(a.B), kp = pp(a.kappa);
         const P2 mu = A * phi + B * phi * phi * phi - kp * lap;
         P2 fe[Q], ge[Q], F[Q];
-        f_equilibrium<!FORCING>(rho, ux, uy, phi, gx, gy, lap, A, B, kp, fe);
+        const P2 u[2] = {ux, uy}, gr[2] = {gx, gy};
+        f_equilibrium<D2Q9, !FORCING>(rho, u, phi, gr, lap, A, B, kp, fe);
         P2 vx = ux, vy = uy;
         if constexpr (FORCING) {
             // Eq. 28 from the 4 x 3 neighbourhoods of M'_xx - M'_yy and M'_xy
@@ -455,12 +342,14 @@ __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepA
             pair_stencil(dn, dDx, dDy, nullptr);
             pair_stencil(xn, dXx, dXy, nullptr);
             const P2 bfx = pp(-0.5f) * dDx - dXy, bfy = pp(0.5f) * dDy - dXx;
-            force_populations(ux, uy, bfx, bfy, F);
+            const P2 bf[2] = {bfx, bfy};
+            force_populations<D2Q9>(u, bf, F);
             const P2 hir = pp(0.5f) * ir;
             vx = ux + bfx * hir;   // Eq. 40
             vy = uy + bfy * hir;
         }
-        g_equilibrium(phi, vx, vy, mu, pp(a.Gamma), ge);
+        const P2 v[2] = {vx, vy};
+        g_equilibrium<D2Q9>(phi, v, mu, pp(a.Gamma), ge);
         const P2 om = pp(a.omega), omp = pp(a.omega_phi);
         const unsigned xm = unsigned(wrapc(x - 1, nx)), xp2 = unsigned(wrapc(x + 2, nx));
         const unsigned row[3] = {unsigned(wrapc(y - 1, ny)) * unsigned(nx), unsigned(y) * unsigned(nx),
@@ -512,8 +401,9 @@ __global__ void binary_init_kernel(const double* rho, const double* phi, const d
         const double mu = A * p[4] + B * p[4] * p[4] * p[4] - kappa * lap;
         const double u0 = ux ? ux[s] : 0.0, u1 = uy ? uy[s] : 0.0;
         double fe[Q], ge[Q];
-        f_equilibrium<!FORCING>(rho[s], u0, u1, p[4], gx, gy, lap, A, B, kappa, fe);
-        g_equilibrium(p[4], u0, u1, mu, Gamma, ge);
+        const double u[2] = {u0, u1}, gr[2] = {gx, gy};
+        f_equilibrium<D2Q9, !FORCING>(rho[s], u, p[4], gr, lap, A, B, kappa, fe);
+        g_equilibrium<D2Q9>(p[4], u, mu, Gamma, ge);
         for (int i = 0; i < Q; ++i) {
             dst[i * pitch + s] = real(fe[i]);
             dst[(Q + i) * pitch + s] = real(ge[i]);
@@ -584,9 +474,9 @@ __global__ void binary_velocity_kernel(const double* rho, const double* ux, cons
 }
 
 template <class real>
-__global__ void binary_convert_kernel(const real* src, double* out, long long pitch, long long n, int to_double,
-                                      const double* in, real* dst) {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * Q * n;
+__global__ void binary_convert_kernel(const real* src, double* out, long long pitch, long long n, int q2,
+                                      int to_double, const double* in, real* dst) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < q2 * n;
          t += (long long)gridDim.x * blockDim.x) {
         const long long k = t / n, s = t % n;
         if (to_double) out[t] = double(src[k * pitch + s]);
@@ -608,14 +498,16 @@ struct lb_binary {
     lb_binary_params p{};
     cudaStream_t stream = nullptr;       // the caller's stream (NULL: the legacy default stream)
     cudaStream_t cap_stream = nullptr;   // private stream the step graphs are captured on
+    int D = 2, Qn = 9;            // lattice dimension and velocities
     long long N = 0, pitch = 0;
     size_t esize = 8;
-    void* pop = nullptr;          // 2 sets x 18 populations x pitch elements
+    void* pop = nullptr;          // 2 sets x 2 Q populations x pitch elements
+    void* phi = nullptr;          // D3Q19: phi of the current set (one value per site, storage type)
     int cur = 0;                  // set holding the current populations
     bool initialised = false;
     long long step = 0;
     unsigned* d_status = nullptr;
-    double* work = nullptr;       // 9 float64 fields of N (observables)
+    double* work = nullptr;       // float64 observables: 9 fields of N (D2Q9), 15 (D3Q19)
     double* d_in = nullptr;       // staging of host float64 inputs (2 Q N)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
@@ -643,7 +535,7 @@ lb_status bcheck(lb_binary* c) {
 }
 
 char* set_ptr(lb_binary* c, int set) {
-    return static_cast<char*>(c->pop) + size_t(set) * 2 * Q * c->pitch * c->esize;
+    return static_cast<char*>(c->pop) + size_t(set) * 2 * c->Qn * c->pitch * c->esize;
 }
 
 template <class real>
@@ -651,9 +543,11 @@ cudaError_t launch_step(lb_binary* c, int from, cudaStream_t st) {
     StepArgs<real> a;
     a.src = reinterpret_cast<const real*>(set_ptr(c, from));
     a.dst = reinterpret_cast<real*>(set_ptr(c, 1 - from));
+    a.phi = nullptr;
     a.pitch = unsigned(c->pitch);
     a.nx = c->p.nx;
     a.ny = c->p.ny;
+    a.nz = c->p.nz;
     a.A = real(c->p.A);
     a.B = real(c->p.B);
     a.kappa = real(c->p.kappa);
@@ -662,6 +556,7 @@ cudaError_t launch_step(lb_binary* c, int from, cudaStream_t st) {
     a.omega_phi = real(1.0 / c->p.tau_phi);
     a.status = c->d_status;
     const bool forcing = c->p.scheme == LB_SCHEME_FORCING;
+    if (c->D == 3) return binary_step3(forcing, a, static_cast<real*>(c->phi), st);
     if constexpr (sizeof(real) == 4) {
         if (c->pair) {   // float32, even nx: two sites per thread
             const dim3 grid((c->p.nx + PTX_ - 1) / PTX_, (c->p.ny + PTY - 1) / PTY);
@@ -695,7 +590,7 @@ lb_status sync_status(lb_binary* c) {
 
 lb_status ensure_work(lb_binary* c) {
     if (c->work) return LB_OK;
-    cudaError_t e = cudaMalloc(&c->work, size_t(9) * c->N * sizeof(double));
+    cudaError_t e = cudaMalloc(&c->work, size_t(c->D == 3 ? 15 : 9) * c->N * sizeof(double));
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->work = nullptr;
@@ -706,7 +601,7 @@ lb_status ensure_work(lb_binary* c) {
 
 lb_status ensure_in(lb_binary* c) {
     if (c->d_in) return LB_OK;
-    cudaError_t e = cudaMalloc(&c->d_in, size_t(2) * Q * c->N * sizeof(double));
+    cudaError_t e = cudaMalloc(&c->d_in, size_t(2) * c->Qn * c->N * sizeof(double));
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->d_in = nullptr;
@@ -737,6 +632,13 @@ lb_status reset_after_set(lb_binary* c) {
 lb_status compute_fields(lb_binary* c) {
     lb_status s = ensure_work(c);
     if (s != LB_OK) return s;
+    if (c->D == 3) {
+        cudaError_t e = binary_fields3(c->p.scheme == LB_SCHEME_FORCING, c->p.storage == LB_F32, set_ptr(c, c->cur),
+                                       unsigned(c->pitch), c->p.nx, c->p.ny, c->p.nz, c->p.A, c->p.B, c->p.kappa,
+                                       c->work, c->stream);
+        if (e != cudaSuccess) return brecord(c, e, "binary fields");
+        return LB_OK;
+    }
     const long long N = c->N;
     double* w = c->work;
     double *rho = w, *phi = w + N, *ux = w + 2 * N, *uy = w + 3 * N, *vx = w + 4 * N, *vy = w + 5 * N,
@@ -773,8 +675,10 @@ extern "C" {
 lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** out) {
     if (!p || !out) return bfail(LB_EINVAL, "null argument");
     *out = nullptr;
-    if (p->nx < 1 || p->ny < 1) return bfail(LB_EINVAL, "nx and ny must be >= 1");
-    if ((long long)p->nx * p->ny > 0x7fffffffLL) return bfail(LB_EINVAL, "more than 2^31 - 1 sites");
+    if (p->lattice != LB_D2Q9 && p->lattice != LB_D3Q19) return bfail(LB_EINVAL, "lattice");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bfail(LB_EINVAL, "nx, ny and nz must be >= 1");
+    if (p->lattice == LB_D2Q9 && p->nz != 1) return bfail(LB_EINVAL, "D2Q9 needs nz = 1");
+    if ((long long)p->nx * p->ny * p->nz > 0x7fffffffLL) return bfail(LB_EINVAL, "more than 2^31 - 1 sites");
     if (!is_fin(p->A) || !is_fin(p->B) || !is_fin(p->kappa) || !is_fin(p->Gamma) || !is_fin(p->tau) ||
         !is_fin(p->tau_phi))
         return bfail(LB_EINVAL, "non-finite parameter");
@@ -786,18 +690,21 @@ lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** 
     lb_binary* c = new (std::nothrow) lb_binary;
     if (!c) return bfail(LB_ENOMEM, "context");
     c->p = *p;
-    c->N = (long long)p->nx * p->ny;
+    c->D = p->lattice == LB_D2Q9 ? 2 : 3;
+    c->Qn = p->lattice == LB_D2Q9 ? 9 : 19;
+    c->N = (long long)p->nx * p->ny * p->nz;
     c->esize = p->storage == LB_F64 ? 8 : 4;
     // LB_BINARY_SITE=1 keeps the one-site kernel for float32 (comparisons)
-    c->pair = p->storage == LB_F32 && p->nx % 2 == 0 && !std::getenv("LB_BINARY_SITE");
+    c->pair = c->D == 2 && p->storage == LB_F32 && p->nx % 2 == 0 && !std::getenv("LB_BINARY_SITE");
     c->pitch = (c->N + 63) / 64 * 64;
-    if (2 * Q * c->pitch >= (1LL << 32)) {
+    if (2 * c->Qn * c->pitch >= (1LL << 32)) {
         delete c;
         return bfail(LB_EINVAL, "lattice too large: element offsets of a population set must fit 32 bits "
-                                "(at most 238,609,280 sites)");
+                                "(at most 238,609,280 sites for D2Q9, 113,025,408 for D3Q19)");
     }
     c->stream = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMalloc(&c->pop, size_t(2) * 2 * Q * c->pitch * c->esize);
+    cudaError_t e = cudaMalloc(&c->pop, size_t(2) * 2 * c->Qn * c->pitch * c->esize);
+    if (e == cudaSuccess && c->D == 3) e = cudaMalloc(&c->phi, size_t(c->N) * c->esize);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -816,6 +723,7 @@ lb_status lb_binary_destroy(lb_binary* c) {
     else cudaDeviceSynchronize();
     drop_graphs(c);
     cudaFree(c->pop);
+    cudaFree(c->phi);
     cudaFree(c->d_status);
     cudaFree(c->work);
     cudaFree(c->d_in);
@@ -836,8 +744,15 @@ lb_status lb_binary_init_fields(lb_binary* c, const double* rho, const double* p
     const size_t nb = size_t(N) * sizeof(double);
     cudaError_t e = cudaMemcpyAsync(d, rho, nb, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d + N, phi, nb, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && u) e = cudaMemcpyAsync(d + 2 * N, u, 2 * nb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(d + 2 * N, u, c->D * nb, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return brecord(c, e, "field upload");
+    if (c->D == 3) {
+        e = binary_init3(c->p.scheme == LB_SCHEME_FORCING, c->p.storage == LB_F32, d, d + N, u ? d + 2 * N : nullptr,
+                         set_ptr(c, 0), unsigned(c->pitch), c->p.nx, c->p.ny, c->p.nz, c->p.A, c->p.B, c->p.kappa,
+                         c->p.Gamma, c->stream);
+        if (e != cudaSuccess) return brecord(c, e, "binary init");
+        return reset_after_set(c);
+    }
     const double* ux = u ? d + 2 * N : nullptr;
     const double* uy = u ? d + 3 * N : nullptr;
     const unsigned nbk = blocks_for(N);
@@ -862,16 +777,16 @@ lb_status lb_binary_set_populations(lb_binary* c, const double* f, const double*
     if (s != LB_OK) return s;
     if (!f || !g) return bfail(LB_EINVAL, "null populations");
     if ((s = ensure_in(c)) != LB_OK) return s;
-    const size_t half = size_t(Q) * c->N;
+    const size_t half = size_t(c->Qn) * c->N;
     cudaError_t e = cudaMemcpyAsync(c->d_in, f, half * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_in + half, g, half * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return brecord(c, e, "population upload");
     const unsigned nb = blocks_for(2 * half);
     if (c->p.storage == LB_F64)
-        binary_convert_kernel<double><<<nb, 256, 0, c->stream>>>(nullptr, nullptr, c->pitch, c->N, 0, c->d_in,
+        binary_convert_kernel<double><<<nb, 256, 0, c->stream>>>(nullptr, nullptr, c->pitch, c->N, 2 * c->Qn, 0, c->d_in,
                                                                   reinterpret_cast<double*>(set_ptr(c, 0)));
     else
-        binary_convert_kernel<float><<<nb, 256, 0, c->stream>>>(nullptr, nullptr, c->pitch, c->N, 0, c->d_in,
+        binary_convert_kernel<float><<<nb, 256, 0, c->stream>>>(nullptr, nullptr, c->pitch, c->N, 2 * c->Qn, 0, c->d_in,
                                                                  reinterpret_cast<float*>(set_ptr(c, 0)));
     e = cudaGetLastError();
     if (e != cudaSuccess) return brecord(c, e, "set populations");
@@ -884,14 +799,14 @@ lb_status lb_binary_get_populations(lb_binary* c, double* f, double* g) {
     if (!f || !g) return bfail(LB_EINVAL, "null output");
     if (!c->initialised) return bfail(LB_ESTATE, "state not initialised");
     if ((s = ensure_in(c)) != LB_OK) return s;
-    const size_t half = size_t(Q) * c->N;
+    const size_t half = size_t(c->Qn) * c->N;
     const unsigned nb = blocks_for(2 * half);
     if (c->p.storage == LB_F64)
         binary_convert_kernel<double><<<nb, 256, 0, c->stream>>>(
-            reinterpret_cast<const double*>(set_ptr(c, c->cur)), c->d_in, c->pitch, c->N, 1, nullptr, nullptr);
+            reinterpret_cast<const double*>(set_ptr(c, c->cur)), c->d_in, c->pitch, c->N, 2 * c->Qn, 1, nullptr, nullptr);
     else
         binary_convert_kernel<float><<<nb, 256, 0, c->stream>>>(
-            reinterpret_cast<const float*>(set_ptr(c, c->cur)), c->d_in, c->pitch, c->N, 1, nullptr, nullptr);
+            reinterpret_cast<const float*>(set_ptr(c, c->cur)), c->d_in, c->pitch, c->N, 2 * c->Qn, 1, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, c->d_in, half * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g, c->d_in + half, half * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -961,9 +876,10 @@ lb_status lb_binary_fields(lb_binary* c, double* rho, double* phi, double* u, do
     cudaError_t e = cudaSuccess;
     if (rho) e = cudaMemcpyAsync(rho, w, nb, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && phi) e = cudaMemcpyAsync(phi, w + N, nb, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, w + 2 * N, 2 * nb, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, w + 4 * N, 2 * nb, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && mu) e = cudaMemcpyAsync(mu, w + 6 * N, nb, cudaMemcpyDeviceToHost, c->stream);
+    const int D = c->D;   // workspace: rho, phi, u [D], v [D], mu, ...
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, w + 2 * N, D * nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, w + (2 + D) * N, D * nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && mu) e = cudaMemcpyAsync(mu, w + (2 + 2 * D) * N, nb, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return brecord(c, e, "field download");
     return sync_status(c);
 }
@@ -974,26 +890,32 @@ lb_status lb_binary_stats_get(lb_binary* c, lb_binary_stats* out) {
     if (!out) return bfail(LB_EINVAL, "null output");
     if (!c->initialised) return bfail(LB_ESTATE, "state not initialised");
     const long long N = c->N;
+    const int D = c->D;
     std::vector<double> h;
     try {
-        h.resize(size_t(6) * N);
+        h.resize(size_t(2 + 2 * D) * N);
     } catch (...) {
         return bfail(LB_ENOMEM, "host buffer");
     }
-    s = lb_binary_fields(c, h.data(), h.data() + N, h.data() + 2 * N, h.data() + 4 * N, nullptr);
+    const double* hu = h.data() + 2 * N;
+    const double* hv = h.data() + (2 + D) * N;
+    s = lb_binary_fields(c, h.data(), h.data() + N, h.data() + 2 * N, h.data() + (2 + D) * N, nullptr);
     if (s != LB_OK && s != LB_EUNSTABLE) return s;
     lb_binary_stats r{};
     r.min_phi = h[N];
     r.max_phi = h[N];
     for (long long i = 0; i < N; ++i) {
-        const double rh = h[i], ph = h[N + i], ux = h[2 * N + i], uy = h[3 * N + i];
-        const double vx = h[4 * N + i], vy = h[5 * N + i];
+        const double rh = h[i], ph = h[N + i];
+        double u2 = 0, v2 = 0;
+        for (int d = 0; d < D; ++d) {
+            r.momentum[d] += rh * hu[d * N + i];
+            u2 += hu[d * N + i] * hu[d * N + i];
+            v2 += hv[d * N + i] * hv[d * N + i];
+        }
         r.mass += rh;
         r.phi_total += ph;
-        r.momentum[0] += rh * ux;
-        r.momentum[1] += rh * uy;
-        r.max_u = std::fmax(r.max_u, std::sqrt(ux * ux + uy * uy));
-        r.max_v = std::fmax(r.max_v, std::sqrt(vx * vx + vy * vy));
+        r.max_u = std::fmax(r.max_u, std::sqrt(u2));
+        r.max_v = std::fmax(r.max_v, std::sqrt(v2));
         r.min_phi = std::fmin(r.min_phi, ph);
         r.max_phi = std::fmax(r.max_phi, ph);
     }

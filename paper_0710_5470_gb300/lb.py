@@ -56,13 +56,14 @@ class lb_instance(C.Structure):
 
 
 class lb_binary_params(C.Structure):
-    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("A", C.c_double), ("B", C.c_double), ("kappa", C.c_double),
+    _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("A", C.c_double),
+                ("B", C.c_double), ("kappa", C.c_double),
                 ("Gamma", C.c_double), ("tau", C.c_double), ("tau_phi", C.c_double), ("scheme", C.c_int),
                 ("storage", C.c_int)]
 
 
 class lb_binary_stats(C.Structure):
-    _fields_ = [("mass", C.c_double), ("phi_total", C.c_double), ("momentum", C.c_double * 2),
+    _fields_ = [("mass", C.c_double), ("phi_total", C.c_double), ("momentum", C.c_double * 3),
                 ("max_u", C.c_double), ("max_v", C.c_double), ("min_phi", C.c_double), ("max_phi", C.c_double),
                 ("step", C.c_longlong), ("status", C.c_int)]
 
@@ -686,17 +687,22 @@ def ws_decode(rho_tanh: np.ndarray, rho_l: float, rho_g: float, y: np.ndarray):
 
 
 class BinaryContext:
-    """One D2Q9 binary-fluid lattice (lb_binary_create ... lb_binary_destroy).
+    """One binary-fluid lattice (lb_binary_create ... lb_binary_destroy).
 
-    shape is (nx, ny); fields are (ny, nx) arrays, populations (9, ny, nx)."""
+    shape (nx, ny) selects D2Q9, (nx, ny, nz) D3Q19; fields are (ny, nx) or
+    (nz, ny, nx) arrays, populations (Q, ...)."""
 
     def __init__(self, shape, A: float, B: float, kappa: float, Gamma: float, tau: float, tau_phi: float,
                  scheme: int = EQUILIBRIUM, storage: int = F64, stream=None):
         lib = load_library()
-        nx, ny = (int(v) for v in shape)
-        self.params = lb_binary_params(nx, ny, A, B, kappa, Gamma, tau, tau_phi, scheme, storage)
-        self.shape = (ny, nx)
-        self.n = nx * ny
+        dims = [int(v) for v in shape]
+        self.dim = len(dims)
+        nx, ny, nz = (dims + [1])[:3]
+        self.q = 9 if self.dim == 2 else 19
+        self.params = lb_binary_params(D2Q9 if self.dim == 2 else D3Q19, nx, ny, nz, A, B, kappa, Gamma, tau,
+                                       tau_phi, scheme, storage)
+        self.shape = (ny, nx) if self.dim == 2 else (nz, ny, nx)
+        self.n = nx * ny * nz
         h = C.c_void_p()
         st = C.c_void_p(int(stream)) if stream else None
         _check(lib.lb_binary_create(C.byref(self.params), st, C.byref(h)))
@@ -724,18 +730,18 @@ class BinaryContext:
         rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
         phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
-        assert rho.size == self.n and phi.size == self.n and (uu is None or uu.size == 2 * self.n)
+        assert rho.size == self.n and phi.size == self.n and (uu is None or uu.size == self.dim * self.n)
         _check(self._lib.lb_binary_init_fields(self._h, _dptr(rho), _dptr(phi), _dptr(uu)))
 
     def set_populations(self, f: np.ndarray, g: np.ndarray):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
-        assert f.size == 9 * self.n and g.size == 9 * self.n
+        assert f.size == self.q * self.n and g.size == self.q * self.n
         _check(self._lib.lb_binary_set_populations(self._h, _dptr(f), _dptr(g)))
 
     def get_populations(self):
-        f = np.empty((9,) + self.shape, dtype=np.float64)
-        g = np.empty((9,) + self.shape, dtype=np.float64)
+        f = np.empty((self.q,) + self.shape, dtype=np.float64)
+        g = np.empty((self.q,) + self.shape, dtype=np.float64)
         _check(self._lib.lb_binary_get_populations(self._h, _dptr(f), _dptr(g)))
         return f, g
 
@@ -746,11 +752,11 @@ class BinaryContext:
         _check(self._lib.lb_binary_synchronize(self._h))
 
     def fields(self):
-        """rho, phi, u (2, ny, nx), v (2, ny, nx), mu."""
+        """rho, phi, u (D, ...), v (D, ...), mu."""
         rho = np.empty(self.shape)
         phi = np.empty(self.shape)
-        u = np.empty((2,) + self.shape)
-        v = np.empty((2,) + self.shape)
+        u = np.empty((self.dim,) + self.shape)
+        v = np.empty((self.dim,) + self.shape)
         mu = np.empty(self.shape)
         _check(self._lib.lb_binary_fields(self._h, _dptr(rho), _dptr(phi), _dptr(u), _dptr(v), _dptr(mu)))
         return rho, phi, u, v, mu
