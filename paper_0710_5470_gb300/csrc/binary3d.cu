@@ -25,7 +25,13 @@
 namespace lbb {
 
 constexpr int Q3 = 19;
-constexpr int BX = 32, BY = 4, BZ = 2, NT3 = BX * BY * BZ;
+constexpr int BX = 32, BY = 4;
+// Brick depth: 2 planes (256 threads).  Measured on GB300 at 128^3, float32:
+// forcing 8.7 GLUPS (1711 instructions per update), equilibrium 11.2; 4 planes
+// (512 threads, one CTA of 16 warps per SM; less halo and ring per site) ran
+// 7.8 / 9.6.  float64 (238 registers a thread) has room for 256 threads only.
+template <class real>
+constexpr int brick_z() { return 2; }
 
 template <class real>
 __global__ void binary_phi_kernel(const real* src, unsigned pitch, unsigned n, real* phi) {
@@ -89,13 +95,14 @@ __device__ __forceinline__ void body_force3(const real* mt, int sn, int k, real 
 template <bool FORCING, class real>
 struct Step3Layout {
     static constexpr int H = FORCING ? 2 : 1;
+    static constexpr int BZ = brick_z<real>(), NT = BX * BY * BZ;
     static constexpr int RX = BX + 2 * H, RY = BY + 2 * H, RZ = BZ + 2 * H, RN = RX * RY * RZ;
     static constexpr int SX = BX + 2, SY = BY + 2, SZ = BZ + 2, SN = SX * SY * SZ;
     static constexpr size_t BYTES = sizeof(real) * (RN + (FORCING ? 6 * SN : 0));
 };
 
 template <bool FORCING, class real>
-__global__ void __launch_bounds__(NT3) binary_step_kernel3(const StepArgs<real> a) {
+__global__ void __launch_bounds__(BX * BY * brick_z<real>()) binary_step_kernel3(const StepArgs<real> a) {
     using Lay = Step3Layout<FORCING, real>;
     constexpr int H = Lay::H, RX = Lay::RX, RY = Lay::RY, RN = Lay::RN;
     constexpr int SX = Lay::SX, SY = Lay::SY, SN = Lay::SN;
@@ -106,6 +113,7 @@ __global__ void __launch_bounds__(NT3) binary_step_kernel3(const StepArgs<real> 
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const unsigned pitch = a.pitch;
     const int tx = threadIdx.x % BX, ty = (threadIdx.x / BX) % BY, tz = threadIdx.x / (BX * BY);
+    constexpr int BZ = Lay::BZ, NT3 = Lay::NT;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
     const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
     const bool own = x < nx && y < ny && z < nz;
@@ -119,11 +127,21 @@ __global__ void __launch_bounds__(NT3) binary_step_kernel3(const StepArgs<real> 
             g[i] = a.src[(Q3 + i) * pitch + s];
         }
     }
-    for (int k = threadIdx.x; k < RN; k += NT3) {
-        const int rx = k % RX, ry = (k / RX) % RY, rz = k / (RX * RY);
-        const unsigned s = (unsigned(wrapc(z0 - H + rz, nz)) * unsigned(ny) + unsigned(wrapc(y0 - H + ry, ny))) *
-                               unsigned(nx) + unsigned(wrapc(x0 - H + rx, nx));
-        phs[k] = a.phi[s];
+    {
+        // a warp per region row (y, z), its lanes along x: row offsets and wraps
+        // once per row, the x wrap per element
+        const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+        constexpr int NW = NT3 / 32;
+        static_assert(RX <= 64, "two elements per lane cover a region row");
+        const unsigned xa = unsigned(wrapc(x0 - H + lane, nx));
+        const unsigned xb = lane + 32 < RX ? unsigned(wrapc(x0 - H + lane + 32, nx)) : 0u;
+        for (int row = warp; row < RY * Lay::RZ; row += NW) {
+            const int ry = row % RY, rz = row / RY;
+            const unsigned base = (unsigned(wrapc(z0 - H + rz, nz)) * unsigned(ny) + unsigned(wrapc(y0 - H + ry, ny))) *
+                                  unsigned(nx);
+            phs[row * RX + lane] = a.phi[base + xa];
+            if (lane + 32 < RX) phs[row * RX + lane + 32] = a.phi[base + xb];
+        }
     }
     __syncthreads();
 
@@ -311,8 +329,8 @@ cudaError_t step3_impl(const StepArgs<real>& a, real* phi_buf, cudaStream_t st) 
     binary_phi_kernel<real><<<blocks3(n), 256, 0, st>>>(a.src, a.pitch, n, phi_buf);
     StepArgs<real> b = a;
     b.phi = phi_buf;
-    const dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + BZ - 1) / BZ);
-    binary_step_kernel3<FORCING, real><<<grid, NT3, Lay::BYTES, st>>>(b);
+    const dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + Lay::BZ - 1) / Lay::BZ);
+    binary_step_kernel3<FORCING, real><<<grid, Lay::NT, Lay::BYTES, st>>>(b);
     return cudaGetLastError();
 }
 }  // namespace
