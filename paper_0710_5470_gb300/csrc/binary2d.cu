@@ -140,32 +140,25 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
         const real ir = real(1) / rho;
         const real ux = jx * ir, uy = jy * ir;
         const real mu = a.A * phi + a.B * phi * phi * phi - a.kappa * lap;
-        real fe[Q], ge[Q], F[Q];
         const real u[2] = {ux, uy}, gr[2] = {gx, gy};
-        f_equilibrium<D2Q9, !FORCING>(rho, u, phi, gr, lap, a.A, a.B, a.kappa, fe);
-        real vx = ux, vy = uy;
+        real bf[2] = {real(0), real(0)}, v[2] = {ux, uy};
         if constexpr (FORCING) {
             // Eq. 28: g_x = -1/2 d_x (M'_xx - M'_yy) - d_y M'_xy, g_y = 1/2 d_y (M'_xx - M'_yy) - d_x M'_xy
             const int k = (ty + 1) * SX + tx + 1;
             real dDx, dDy, dXx, dXy;
             stencil<SX>(mdiff, k, dDx, dDy);
             stencil<SX>(mxy_s, k, dXx, dXy);
-            const real bfx = real(-0.5) * dDx - dXy, bfy = real(0.5) * dDy - dXx;
-            const real bf[2] = {bfx, bfy};
-            force_populations<D2Q9>(u, bf, F);
-            vx = ux + bfx * (real(0.5) * ir);   // Eq. 40
-            vy = uy + bfy * (real(0.5) * ir);
+            bf[0] = real(-0.5) * dDx - dXy;
+            bf[1] = real(0.5) * dDy - dXx;
+            v[0] = ux + bf[0] * (real(0.5) * ir);   // Eq. 40
+            v[1] = uy + bf[1] * (real(0.5) * ir);
         }
-        const real v[2] = {vx, vy};
-        g_equilibrium<D2Q9>(phi, v, mu, a.Gamma, ge);
         const int xw[3] = {wrapc(x - 1, nx), x, wrapc(x + 1, nx)};
         const int yw[3] = {wrapc(y - 1, ny), y, wrapc(y + 1, ny)};
-        static_for<0, Q>([&](auto K) {
+        collide_stream<D2Q9, FORCING>(f, g, rho, u, phi, gr, lap, bf, v, mu, a.A, a.B, a.kappa, a.Gamma, a.omega,
+                                      a.omega_phi, [&](auto K, real fs, real gs) {
             constexpr int i = decltype(K)::value;
             constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
-            real fs = f[i] + a.omega * (fe[i] - f[i]);
-            if constexpr (FORCING) fs += F[i];
-            const real gs = g[i] + a.omega_phi * (ge[i] - g[i]);
             const unsigned d = unsigned(yw[1 + ey]) * unsigned(nx) + unsigned(xw[1 + ex]);
             a.dst[i * pitch + d] = fs;
             a.dst[(Q + i) * pitch + d] = gs;
@@ -180,11 +173,12 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
 // instructions.  CTA: a 32 x 8 tile, 128 threads; the phi halo is 2 sites in
 // x (one pair) and 1 (equilibrium) or 2 (forcing) rows in y.
 constexpr int PTX_ = 32, PTY = 8, PTXP = PTX_ / 2, PNT = PTXP * PTY;
-// Five resident CTAs per SM (at most 96 registers; the forcing form spills 28
-// bytes): measured on GB300 at 2048^2 against the unbounded form (118 / 94
-// registers, four CTAs): forcing 36.7 against 34.0 GLUPS, equilibrium 35.8
-// against 33.4-36.0.
-constexpr int PAIR_MINB = 5;
+// Six resident CTAs per SM (at most 80 registers; the forcing form spills 20
+// bytes): with the collision streamed population by population, measured on
+// GB300 at 2048^2: forcing 38.8 GLUPS against 37.2 at five CTAs, equilibrium
+// 38.1 against 35.7 (the array form at five CTAs: 36.7 / 35.8; unbounded,
+// 118 registers and four CTAs: 34.0 / 33.4-36.0).
+constexpr int PAIR_MINB = 6;
 
 // Gradient (Eq. 10) and Laplacian (Eq. 11) of both sites of a pair from the
 // 4 x 3 neighbourhood columns x-1 .. x+2 (c[r][0..3]) of rows y-1, y, y+1
@@ -323,10 +317,8 @@ __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepA
         const P2 ux = jx * ir, uy = jy * ir;
         const P2 A = pp(a.A), B = pp(a.B), kp = pp(a.kappa);
         const P2 mu = A * phi + B * phi * phi * phi - kp * lap;
-        P2 fe[Q], ge[Q], F[Q];
         const P2 u[2] = {ux, uy}, gr[2] = {gx, gy};
-        f_equilibrium<D2Q9, !FORCING>(rho, u, phi, gr, lap, A, B, kp, fe);
-        P2 vx = ux, vy = uy;
+        P2 bf[2] = {pp(0.0f), pp(0.0f)}, v[2] = {ux, uy};
         if constexpr (FORCING) {
             // Eq. 28 from the 4 x 3 neighbourhoods of M'_xx - M'_yy and M'_xy
             float dn[3][4], xn[3][4];
@@ -341,25 +333,19 @@ __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepA
             P2 dDx, dDy, dXx, dXy;
             pair_stencil(dn, dDx, dDy, nullptr);
             pair_stencil(xn, dXx, dXy, nullptr);
-            const P2 bfx = pp(-0.5f) * dDx - dXy, bfy = pp(0.5f) * dDy - dXx;
-            const P2 bf[2] = {bfx, bfy};
-            force_populations<D2Q9>(u, bf, F);
+            bf[0] = pp(-0.5f) * dDx - dXy;
+            bf[1] = pp(0.5f) * dDy - dXx;
             const P2 hir = pp(0.5f) * ir;
-            vx = ux + bfx * hir;   // Eq. 40
-            vy = uy + bfy * hir;
+            v[0] = ux + bf[0] * hir;   // Eq. 40
+            v[1] = uy + bf[1] * hir;
         }
-        const P2 v[2] = {vx, vy};
-        g_equilibrium<D2Q9>(phi, v, mu, pp(a.Gamma), ge);
-        const P2 om = pp(a.omega), omp = pp(a.omega_phi);
         const unsigned xm = unsigned(wrapc(x - 1, nx)), xp2 = unsigned(wrapc(x + 2, nx));
         const unsigned row[3] = {unsigned(wrapc(y - 1, ny)) * unsigned(nx), unsigned(y) * unsigned(nx),
                                  unsigned(wrapc(y + 1, ny)) * unsigned(nx)};
-        static_for<0, Q>([&](auto K) {
+        collide_stream<D2Q9, FORCING>(f, g, rho, u, phi, gr, lap, bf, v, mu, A, B, kp, pp(a.Gamma), pp(a.omega),
+                                      pp(a.omega_phi), [&](auto K, P2 fs, P2 gs) {
             constexpr int i = decltype(K)::value;
             constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
-            P2 fs = f[i] + om * (fe[i] - f[i]);
-            if constexpr (FORCING) fs += F[i];
-            const P2 gs = g[i] + omp * (ge[i] - g[i]);
             const unsigned r = row[1 + ey];
             float* df = a.dst + i * pitch + r;
             float* dg = a.dst + (Q + i) * pitch + r;

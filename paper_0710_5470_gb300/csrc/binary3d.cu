@@ -192,16 +192,6 @@ __global__ void __launch_bounds__(BX * BY * brick_z<real>(), sizeof(real) == 4 ?
 #pragma unroll
             for (int d = 0; d < 3; ++d) v[d] = u[d] + bf[d] * hir;   // Eq. 40
         }
-        // f^eq, F and g^eq population by population (the same arithmetic as
-        // f_equilibrium, force_populations and g_equilibrium), each pushed as
-        // soon as it is formed; the i = 0 terms from the running sums last
-        const real phi2 = phi * phi;
-        const real iso = rho * real(1.0 / 3.0) + real(0.5) * a.A * phi2 + real(0.75) * a.B * phi2 * phi2 -
-                         a.kappa * phi * lap;
-        const real usq3 = dot<D3Q19>(u, u) * real(1.0 / 3.0);
-        const real vsq3 = dot<D3Q19>(v, v) * real(1.0 / 3.0);
-        const real ug23 = dot<D3Q19>(u, bf) * real(2.0 / 3.0);
-        const real gm = a.Gamma * mu;
         const int xw[3] = {wrapc(x - 1, nx), x, wrapc(x + 1, nx)};
         const unsigned yz[3][3] = {
             {(unsigned(wrapc(z - 1, nz)) * ny + unsigned(wrapc(y - 1, ny))) * unsigned(nx),
@@ -212,45 +202,14 @@ __global__ void __launch_bounds__(BX * BY * brick_z<real>(), sizeof(real) == 4 ?
             {(unsigned(wrapc(z + 1, nz)) * ny + unsigned(wrapc(y - 1, ny))) * unsigned(nx),
              (unsigned(wrapc(z + 1, nz)) * ny + unsigned(y)) * unsigned(nx),
              (unsigned(wrapc(z + 1, nz)) * ny + unsigned(wrapc(y + 1, ny))) * unsigned(nx)}};
-        real sfe = 0, sF = 0, sge = 0;
-        static_for<1, Q3>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            constexpr int ex = D3Q19::ex(i), ey = D3Q19::ey(i), ez = D3Q19::ez(i);
-            real pr = real(W<D3Q19, i>()) * iso;
-            if constexpr (!FORCING) {
-                static_for<0, 3>([&](auto AA) {
-                    constexpr int a_ = decltype(AA)::value;
-                    static_for<a_, 3>([&](auto BB) {
-                        constexpr int b_ = decltype(BB)::value;
-                        constexpr double wab = lbk::w_m<D3Q19>(i, a_, b_);
-                        if constexpr (wab != 0.0) pr += real(wab) * (a.kappa * gr[a_] * gr[b_]);
-                    });
-                });
-            }
-            const real fe = velocity_part<D3Q19, i>(rho, u, usq3) + pr;
-            sfe += fe;
-            real fs = f[i] + a.omega * (fe - f[i]);
-            if constexpr (FORCING) {
-                const real eg = edot<D3Q19, i>(bf), eu = edot<D3Q19, i>(u);
-                const real Fi = real(W<D3Q19, i>()) * (eg + real(1.5) * (real(2.0) * eu * eg - ug23));
-                sF += Fi;
-                fs += Fi;
-            }
-            const real ge = velocity_part<D3Q19, i>(phi, v, vsq3) + real(W<D3Q19, i>()) * gm;
-            sge += ge;
-            const real gs = g[i] + a.omega_phi * (ge - g[i]);
-            const unsigned d = yz[1 + ez][1 + ey] + unsigned(xw[1 + ex]);
-            a.dst[i * pitch + d] = fs;
-            a.dst[(Q3 + i) * pitch + d] = gs;
-        });
-        {
-            real fs = f[0] + a.omega * ((rho - sfe) - f[0]);
-            if constexpr (FORCING) fs += -sF;
-            const real gs = g[0] + a.omega_phi * ((phi - sge) - g[0]);
-            const unsigned d = yz[1][1] + unsigned(x);
-            a.dst[d] = fs;
-            a.dst[Q3 * pitch + d] = gs;
-        }
+        collide_stream<D3Q19, FORCING>(f, g, rho, u, phi, gr, lap, bf, v, mu, a.A, a.B, a.kappa, a.Gamma, a.omega,
+                                       a.omega_phi, [&](auto K, real fs, real gs) {
+                                           constexpr int i = decltype(K)::value;
+                                           constexpr int ex = D3Q19::ex(i), ey = D3Q19::ey(i), ez = D3Q19::ez(i);
+                                           const unsigned d = yz[1 + ez][1 + ey] + unsigned(xw[1 + ex]);
+                                           a.dst[i * pitch + d] = fs;
+                                           a.dst[(Q3 + i) * pitch + d] = gs;
+                                       });
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x % 32) == 0) atomicOr(a.status, 1u);
 }

@@ -159,4 +159,58 @@ __device__ __forceinline__ void force_populations(const real (&u)[L::D], const r
     F[0] = -sum;
 }
 
+// The collision of one site (or a packed pair) streamed population by
+// population: for i = 1 .. Q-1 it forms f^eq_i, (forcing) F_i and g^eq_i with
+// the arithmetic of f_equilibrium, force_populations and g_equilibrium,
+// relaxes f_i with omega and g_i with omega_phi and hands f*_i, g*_i to
+// push(integral_constant<int, i>, f*_i, g*_i) at once; i = 0 follows from the
+// running sums (f^eq_0 = rho - sum, Eq. 6; F_0 = -sum, reading R8; g^eq_0 =
+// phi - sum).  No population array beyond f and g is ever live, which keeps a
+// thread's registers low enough for more resident CTAs.
+template <class L, bool FORCING, class real, class Push>
+__device__ __forceinline__ void collide_stream(const real (&f)[L::Q], const real (&g)[L::Q], real rho,
+                                               const real (&u)[L::D], real phi, const real (&gr)[L::D], real lap,
+                                               const real (&bf)[L::D], const real (&v)[L::D], real mu, real A,
+                                               real B, real kappa, real Gamma, real omega, real omega_phi,
+                                               Push&& push) {
+    const real phi2 = phi * phi;
+    const real p0 = rho * cst<real>(1.0 / 3.0) + cst<real>(0.5) * A * phi2 + cst<real>(0.75) * B * phi2 * phi2;
+    const real iso = p0 - kappa * phi * lap;
+    const real usq3 = dot<L>(u, u) * cst<real>(1.0 / 3.0);
+    const real vsq3 = dot<L>(v, v) * cst<real>(1.0 / 3.0);
+    const real gm = Gamma * mu;
+    real ug23 = cst<real>(0.0);
+    if constexpr (FORCING) ug23 = dot<L>(u, bf) * cst<real>(2.0 / 3.0);
+    real sfe = cst<real>(0.0), sF = cst<real>(0.0), sge = cst<real>(0.0);
+    static_for<1, L::Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        real pr = cst<real>(W<L, i>()) * iso;
+        if constexpr (!FORCING) {
+            static_for<0, L::D>([&](auto AA) {
+                constexpr int a = decltype(AA)::value;
+                static_for<a, L::D>([&](auto BB) {
+                    constexpr int b = decltype(BB)::value;
+                    constexpr double wab = lbk::w_m<L>(i, a, b);
+                    if constexpr (wab != 0.0) pr += cst<real>(wab) * (kappa * gr[a] * gr[b]);
+                });
+            });
+        }
+        const real fe = velocity_part<L, i>(rho, u, usq3) + pr;
+        sfe += fe;
+        real fs = f[i] + omega * (fe - f[i]);
+        if constexpr (FORCING) {
+            const real eg = edot<L, i>(bf), eu = edot<L, i>(u);
+            const real Fi = cst<real>(W<L, i>()) * (eg + cst<real>(1.5) * (cst<real>(2.0) * eu * eg - ug23));
+            sF += Fi;
+            fs += Fi;
+        }
+        const real ge = velocity_part<L, i>(phi, v, vsq3) + cst<real>(W<L, i>()) * gm;
+        sge += ge;
+        push(K, fs, g[i] + omega_phi * (ge - g[i]));
+    });
+    real fs0 = f[0] + omega * ((rho - sfe) - f[0]);
+    if constexpr (FORCING) fs0 += -sF;
+    push(std::integral_constant<int, 0>{}, fs0, g[0] + omega_phi * ((phi - sge) - g[0]));
+}
+
 }  // namespace lbb
