@@ -544,6 +544,10 @@ lb_status lb_binary_synchronize(lb_binary* ctx);
  * rho [N], phi [N], u [D][N] (Eq. 3), v [D][N] (Eq. 40; = u in the equilibrium
  * scheme), mu [N]. */
 lb_status lb_binary_fields(lb_binary* ctx, double* rho, double* phi, double* u, double* v, double* mu);
+/* Totals and extremes of the current state: the float64 fields of
+ * lb_binary_fields (computed on the device), summed in site order on the host;
+ * allocates (2 + 2 D) N doubles of host memory per call.  Returns
+ * LB_EUNSTABLE (with out filled) once a density became non-finite. */
 lb_status lb_binary_stats_get(lb_binary* ctx, lb_binary_stats* out);
 
 #ifdef __cplusplus
