@@ -453,7 +453,8 @@ def binary_block(lb, stream, peak, dist, world, warmup, cpu: bool):
                        f"{w:g}), rho=1, A={b['A']}, B={b['B']}, kappa={b['kappa']}, Gamma={b['Gamma']}, "
                        f"tau=tau_phi=1", "runs": {}}
     for scheme in ("forcing", "equilibrium"):
-        for sname, st_code, bpl, steps in (("f32", lb.F32, 144, 400), ("f64", lb.F64, 288, 100)):
+        for sname, st_code, bpl, steps in (("f32", lb.F32, 144, 400), ("f16dev", lb.F16DEV, 80, 400),
+                                           ("f64", lb.F64, 288, 100)):
             ctx = lb.BinaryContext((n, n), b["A"], b["B"], b["kappa"], b["Gamma"], b["tau"], b["tau_phi"],
                                    scheme=lb.FORCING if scheme == "forcing" else lb.EQUILIBRIUM, storage=st_code,
                                    stream=stream.cuda_stream)

@@ -492,7 +492,10 @@ lb_status lb_fma_peak(int precision, int iters, double* tflops);
  * Stencils: the gradient and Laplacian of phi by Eqs. 10 and 11 at the
  * optimum (B = 1/12, D = 1/6), the force stencil with F = 1/12; in 3D
  * Eq. 29 with A = 1/6, B = 1/12, C = 1/3, D = 1/6 and the weights of Eq. 31.
- * Storage: LB_F64 (float64 arithmetic) or LB_F32 (float32 arithmetic).
+ * Storage: LB_F64 (float64 arithmetic), LB_F32 (float32 arithmetic), or for
+ * D2Q9 with an even nx LB_F16DEV (float32 arithmetic; f_0 and g_0 stored in
+ * float32, f_i - w_i p_ref and g_i (i >= 1) in fp16, p_ref = p0 of a bulk
+ * phase at rho = 1: 1/3 + A^2 / (4 B) for A < 0 < B, else 1/3).
  * Populations exchanged with the host: float64 [i][z][y][x] for f and for g,
  * i in the paper's order (Sec. II, Sec. VII), after streaming.  Conventions otherwise as
  * above (caller-owned host arrays, status codes, sticky device errors). */
@@ -507,7 +510,7 @@ typedef struct {
     double tau;           /* relaxation time of f, > 1/2 */
     double tau_phi;       /* relaxation time of g, > 1/2 */
     int scheme;           /* lb_scheme */
-    int storage;          /* LB_F64 or LB_F32 */
+    int storage;          /* LB_F64, LB_F32, or LB_F16DEV (D2Q9, even nx) */
 } lb_binary_params;
 
 typedef struct {

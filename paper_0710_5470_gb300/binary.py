@@ -110,7 +110,9 @@ def throughput(n: int, steps: int, scheme: str = "forcing", storage: str = "f32"
         ms = e0.elapsed_time(e1)
         st = c.stats()
     q = 9 if dim == 2 else 19
-    bpl = 2 * 2 * q * (4 if storage == "f32" else 8)     # f and g read and written
+    # f and g read and written: every population in float32 / float64; with fp16
+    # deviations f_0 and g_0 in float32 and the other 2 Q - 2 in fp16
+    bpl = {"f32": 2 * 2 * q * 4, "f64": 2 * 2 * q * 8, "f16dev": 2 * (2 * 4 + (2 * q - 2) * 2)}[storage]
     sites = n ** dim
     return {"n": n, "dim": dim, "scheme": scheme, "storage": storage, "steps": steps, "ms_per_step": ms / steps,
             "glups": sites * steps / (ms / 1e3) / 1e9, "gbs": bpl * sites * steps / (ms / 1e3) / 1e9,
@@ -125,7 +127,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=12)
     ap.add_argument("--radius", type=float, default=None)
     ap.add_argument("--scheme", choices=["forcing", "equilibrium"], default="forcing")
-    ap.add_argument("--storage", choices=["f64", "f32"], default="f32")
+    ap.add_argument("--storage", choices=["f64", "f32", "f16dev"], default="f32")
     ap.add_argument("--dim", type=int, choices=[2, 3], default=2, help="2: D2Q9, 3: D3Q19")
     a = ap.parse_args(argv)
     build.build()

@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lb.h"
@@ -172,6 +173,51 @@ __global__ void __launch_bounds__(NT) binary_step_kernel(const StepArgs<real> a)
 // and every arithmetic step of stage C runs as packed float32 pair
 // instructions.  CTA: a 32 x 8 tile, 128 threads; the phi halo is 2 sites in
 // x (one pair) and 1 (equilibrium) or 2 (forcing) rows in y.
+// Population k of a set (0 .. Q-1: f_k, Q .. 2Q-1: g_{k-Q}).  A float32 set holds
+// 2Q float arrays of `pitch` elements.  A 16-bit set (fp16 deviations) holds
+// f_0 and g_0 as float32 (at 0 and 4 pitch bytes) and the other 2Q - 2 as fp16
+// arrays from 8 pitch bytes on: f_i - w_i pref (i >= 1; w_i pref is the rest
+// equilibrium of a bulk phase) and g_i (i >= 1; zero at rest in a bulk phase).
+__host__ __device__ constexpr unsigned set16_half_offset(int k, unsigned pitch) {
+    return 8u * pitch + unsigned(k < Q ? k - 1 : Q - 1 + (k - Q - 1)) * 2u * pitch;
+}
+__host__ __device__ constexpr size_t set16_bytes(size_t pitch) { return 8 * pitch + size_t(2 * Q - 2) * 2 * pitch; }
+
+// The pair of sites at pair index s2 (site 2 s2, x even) of population k, as
+// float32 values; fref = w_k pref for f_k of a 16-bit set, else 0.
+template <bool F16>
+__device__ __forceinline__ P2 ld_pair(const char* set, unsigned pitch, int k, unsigned s2, float fref) {
+    if constexpr (!F16) {
+        return P2{reinterpret_cast<const float2*>(set)[unsigned(k) * (pitch >> 1) + s2]};
+    } else {
+        if (k == 0 || k == Q) return P2{reinterpret_cast<const float2*>(set + (k == 0 ? 0u : 4u * pitch))[s2]};
+        const float2 v = __half22float2(reinterpret_cast<const __half2*>(set + set16_half_offset(k, pitch))[s2]);
+        return pp(v.x + fref, v.y + fref);
+    }
+}
+// Stores the pair v at sites idx, idx + 1 (idx even) / one value at site idx.
+template <bool F16>
+__device__ __forceinline__ void st_pair(char* set, unsigned pitch, int k, unsigned idx, P2 v, float fref) {
+    if constexpr (!F16) {
+        *reinterpret_cast<float2*>(reinterpret_cast<float*>(set) + (unsigned(k) * pitch + idx)) = v.v;
+    } else if (k == 0 || k == Q) {
+        *reinterpret_cast<float2*>(reinterpret_cast<float*>(set + (k == 0 ? 0u : 4u * pitch)) + idx) = v.v;
+    } else {
+        *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(set + set16_half_offset(k, pitch)) + idx) =
+            __floats2half2_rn(v.v.x - fref, v.v.y - fref);
+    }
+}
+template <bool F16>
+__device__ __forceinline__ void st_one(char* set, unsigned pitch, int k, unsigned idx, float v, float fref) {
+    if constexpr (!F16) {
+        reinterpret_cast<float*>(set)[unsigned(k) * pitch + idx] = v;
+    } else if (k == 0 || k == Q) {
+        reinterpret_cast<float*>(set + (k == 0 ? 0u : 4u * pitch))[idx] = v;
+    } else {
+        reinterpret_cast<__half*>(set + set16_half_offset(k, pitch))[idx] = __float2half_rn(v - fref);
+    }
+}
+
 constexpr int PTX_ = 32, PTY = 8, PTXP = PTX_ / 2, PNT = PTXP * PTY;
 // Six resident CTAs per SM (at most 80 registers; the forcing form spills 20
 // bytes): with the collision streamed population by population, measured on
@@ -179,6 +225,8 @@ constexpr int PTX_ = 32, PTY = 8, PTXP = PTX_ / 2, PNT = PTXP * PTY;
 // 38.1 against 35.7 (the array form at five CTAs: 36.7 / 35.8; unbounded,
 // 118 registers and four CTAs: 34.0 / 33.4-36.0).
 constexpr int PAIR_MINB = 6;
+// 16-bit storage: five (at six its fp16 decodes spilled 32-68 bytes).
+constexpr int PAIR_MINB16 = 5;
 
 // Gradient (Eq. 10) and Laplacian (Eq. 11) of both sites of a pair from the
 // 4 x 3 neighbourhood columns x-1 .. x+2 (c[r][0..3]) of rows y-1, y, y+1
@@ -199,7 +247,7 @@ __device__ __forceinline__ void pair_stencil(const float (&c)[3][4], P2& gx, P2&
                pp(10.0f / 3.0f) * M[1];
 }
 
-template <bool FORCING, int MINB>
+template <bool FORCING, int MINB, bool F16 = false>
 __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepArgs<float> a) {
     constexpr int H = FORCING ? 2 : 1, HX = 2;
     constexpr int RX = PTX_ + 2 * HX, RY = PTY + 2 * H, RN = RX * RY, RXP = RX / 2;
@@ -217,22 +265,29 @@ __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepA
     const int x0 = blockIdx.x * PTX_, y0 = blockIdx.y * PTY;
     const int x = x0 + 2 * px, y = y0 + py;
     const bool own = x < nx && y < ny;
-    const float2* src = reinterpret_cast<const float2*>(a.src);
+    const char* srcb = reinterpret_cast<const char*>(a.src);
+    // w_i pref of the 16-bit deviations (f_i, i >= 1), formed where used
+    auto fref = [&](int i) { return F16 && i > 0 ? float(lbk::w_vel<D2Q9>(i)) * a.pref : 0.0f; };
 
     // ---- stage A: the own pair's populations; phi pairs on the tile and halo
     P2 f[Q], g[Q];
     {
         const int sx = own ? x : wrapc(x, nx), sy = own ? y : wrapc(y, ny);
         const unsigned s2 = (unsigned(sy) * unsigned(nx) + unsigned(sx)) >> 1;   // pair index (x even)
+        const float2* src = reinterpret_cast<const float2*>(a.src);
         const unsigned p2 = pitch >> 1;
         if (own) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) f[i].v = src[i * p2 + s2];
+            for (int i = 0; i < Q; ++i) {
+                if constexpr (F16) f[i] = ld_pair<F16>(srcb, pitch, i, s2, fref(i));
+                else f[i].v = src[i * p2 + s2];
+            }
         }
         P2 phi = pp(0.0f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            g[i].v = src[(Q + i) * p2 + s2];
+            if constexpr (F16) g[i] = ld_pair<F16>(srcb, pitch, Q + i, s2, 0.0f);
+            else g[i].v = src[(Q + i) * p2 + s2];
             phi += g[i];
         }
         *reinterpret_cast<float2*>(&phs[(py + H) * RX + 2 * px + HX]) = phi.v;
@@ -251,7 +306,10 @@ __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepA
                                  unsigned(wrapc(x0 - HX + 2 * rxp, nx))) >> 1;
             P2 ph = pp(0.0f);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) ph += P2{src[(Q + i) * p2 + h2]};
+            for (int i = 0; i < Q; ++i) {
+                if constexpr (F16) ph += ld_pair<F16>(srcb, pitch, Q + i, h2, 0.0f);
+                else ph += P2{reinterpret_cast<const float2*>(a.src)[(Q + i) * (pitch >> 1) + h2]};
+            }
             *reinterpret_cast<float2*>(&phs[ry * RX + 2 * rxp]) = ph.v;
         }
     }
@@ -347,21 +405,39 @@ __global__ void __launch_bounds__(PNT, MINB) binary_step_kernel_pair(const StepA
             constexpr int i = decltype(K)::value;
             constexpr int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
             const unsigned r = row[1 + ey];
-            float* df = a.dst + i * pitch + r;
-            float* dg = a.dst + (Q + i) * pitch + r;
+            if constexpr (!F16) {
+                float* df = a.dst + i * pitch + r;
+                float* dg = a.dst + (Q + i) * pitch + r;
+                if constexpr (ex == 0) {
+                    *reinterpret_cast<float2*>(df + x) = fs.v;
+                    *reinterpret_cast<float2*>(dg + x) = gs.v;
+                } else if constexpr (ex > 0) {
+                    df[x + 1] = fs.v.x;
+                    df[xp2] = fs.v.y;
+                    dg[x + 1] = gs.v.x;
+                    dg[xp2] = gs.v.y;
+                } else {
+                    df[xm] = fs.v.x;
+                    df[x] = fs.v.y;
+                    dg[xm] = gs.v.x;
+                    dg[x] = gs.v.y;
+                }
+                return;
+            }
+            char* db = reinterpret_cast<char*>(a.dst);
             if constexpr (ex == 0) {
-                *reinterpret_cast<float2*>(df + x) = fs.v;
-                *reinterpret_cast<float2*>(dg + x) = gs.v;
+                st_pair<F16>(db, pitch, i, r + x, fs, fref(i));
+                st_pair<F16>(db, pitch, Q + i, r + x, gs, 0.0f);
             } else if constexpr (ex > 0) {
-                df[x + 1] = fs.v.x;
-                df[xp2] = fs.v.y;
-                dg[x + 1] = gs.v.x;
-                dg[xp2] = gs.v.y;
+                st_one<F16>(db, pitch, i, r + x + 1, fs.v.x, fref(i));
+                st_one<F16>(db, pitch, i, r + xp2, fs.v.y, fref(i));
+                st_one<F16>(db, pitch, Q + i, r + x + 1, gs.v.x, 0.0f);
+                st_one<F16>(db, pitch, Q + i, r + xp2, gs.v.y, 0.0f);
             } else {
-                df[xm] = fs.v.x;
-                df[x] = fs.v.y;
-                dg[xm] = gs.v.x;
-                dg[x] = gs.v.y;
+                st_one<F16>(db, pitch, i, r + xm, fs.v.x, fref(i));
+                st_one<F16>(db, pitch, i, r + x, fs.v.y, fref(i));
+                st_one<F16>(db, pitch, Q + i, r + xm, gs.v.x, 0.0f);
+                st_one<F16>(db, pitch, Q + i, r + x, gs.v.y, 0.0f);
             }
         });
     }
@@ -470,6 +546,47 @@ __global__ void binary_convert_kernel(const real* src, double* out, long long pi
     }
 }
 
+// Conversion between a 16-bit set and float64 populations [2Q][n] (f then g);
+// to_double: set -> buf, else buf -> set (deviations rounded to fp16 from float64).
+__global__ void binary_convert16_kernel(char* set, unsigned pitch, unsigned n, int to_double, double* buf, float pref) {
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < 2u * Q * n; t += gridDim.x * blockDim.x) {
+        const int k = int(t / n);
+        const unsigned s = t % n;
+        if (k == 0 || k == Q) {
+            float* p = reinterpret_cast<float*>(set + (k == 0 ? 0u : 4u * pitch));
+            if (to_double) buf[t] = double(p[s]);
+            else p[s] = float(buf[t]);
+        } else {
+            __half* h = reinterpret_cast<__half*>(set + set16_half_offset(k, pitch));
+            const double fref = k < Q ? lbk::w_vel<D2Q9>(k) * double(pref) : 0.0;
+            if (to_double) buf[t] = double(__half2float(h[s])) + fref;
+            else h[s] = __float2half_rn(float(buf[t] - fref));
+        }
+    }
+}
+
+// rho, phi, u of a 16-bit set in float64.
+__global__ void binary_moments16_kernel(const char* set, unsigned pitch, unsigned n, float pref, double* rho,
+                                        double* phi, double* ux, double* uy) {
+    for (unsigned s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double r = double(reinterpret_cast<const float*>(set)[s]);
+        double p = double(reinterpret_cast<const float*>(set + 4u * pitch)[s]);
+        double jx = 0, jy = 0;
+        for (int i = 1; i < Q; ++i) {
+            const double fi = double(__half2float(reinterpret_cast<const __half*>(set + set16_half_offset(i, pitch))[s])) +
+                              lbk::w_vel<D2Q9>(i) * double(pref);
+            r += fi;
+            jx += D2Q9::ex(i) * fi;
+            jy += D2Q9::ey(i) * fi;
+            p += double(__half2float(reinterpret_cast<const __half*>(set + set16_half_offset(Q + i, pitch))[s]));
+        }
+        rho[s] = r;
+        phi[s] = p;
+        ux[s] = jx / r;
+        uy[s] = jy / r;
+    }
+}
+
 inline unsigned blocks_for(long long n) {
     long long b = (n + 255) / 256;
     if (b > 8192) b = 8192;
@@ -497,7 +614,10 @@ struct lb_binary {
     double* d_in = nullptr;       // staging of host float64 inputs (2 Q N)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
-    bool pair = false;            // float32 with an even nx: the two-sites-per-thread kernel
+    bool pair = false;            // float32 / 16-bit with an even nx: the two-sites-per-thread kernel
+    bool f16 = false;             // LB_F16DEV: f_0, g_0 float32, the rest fp16 (f_i as deviations)
+    float pref = 0.0f;            // the deviations' reference p0 of a bulk phase at rho = 1
+    size_t set_bytes = 0;         // bytes of one population set
     lb_status sticky = LB_OK;
 };
 
@@ -521,7 +641,7 @@ lb_status bcheck(lb_binary* c) {
 }
 
 char* set_ptr(lb_binary* c, int set) {
-    return static_cast<char*>(c->pop) + size_t(set) * 2 * c->Qn * c->pitch * c->esize;
+    return static_cast<char*>(c->pop) + size_t(set) * c->set_bytes;
 }
 
 template <class real>
@@ -541,13 +661,19 @@ cudaError_t launch_step(lb_binary* c, int from, cudaStream_t st) {
     a.omega = real(1.0 / c->p.tau);
     a.omega_phi = real(1.0 / c->p.tau_phi);
     a.status = c->d_status;
+    a.pref = c->pref;
     const bool forcing = c->p.scheme == LB_SCHEME_FORCING;
     if (c->D == 3) return binary_step3(forcing, a, static_cast<real*>(c->phi), st);
     if constexpr (sizeof(real) == 4) {
-        if (c->pair) {   // float32, even nx: two sites per thread
+        if (c->pair) {   // float32 or 16-bit, even nx: two sites per thread
             const dim3 grid((c->p.nx + PTX_ - 1) / PTX_, (c->p.ny + PTY - 1) / PTY);
-            if (forcing) binary_step_kernel_pair<true, PAIR_MINB><<<grid, PNT, 0, st>>>(a);
-            else binary_step_kernel_pair<false, PAIR_MINB><<<grid, PNT, 0, st>>>(a);
+            if (c->f16) {
+                if (forcing) binary_step_kernel_pair<true, PAIR_MINB16, true><<<grid, PNT, 0, st>>>(a);
+                else binary_step_kernel_pair<false, PAIR_MINB16, true><<<grid, PNT, 0, st>>>(a);
+            } else {
+                if (forcing) binary_step_kernel_pair<true, PAIR_MINB><<<grid, PNT, 0, st>>>(a);
+                else binary_step_kernel_pair<false, PAIR_MINB><<<grid, PNT, 0, st>>>(a);
+            }
             return cudaGetLastError();
         }
     }
@@ -631,7 +757,10 @@ lb_status compute_fields(lb_binary* c) {
            *mu = w + 6 * N, *md = w + 7 * N, *mx = w + 8 * N;
     const unsigned nb = blocks_for(N);
     const int nx = c->p.nx, ny = c->p.ny;
-    if (c->p.storage == LB_F64)
+    if (c->f16)
+        binary_moments16_kernel<<<nb, 256, 0, c->stream>>>(set_ptr(c, c->cur), unsigned(c->pitch), unsigned(N), c->pref,
+                                                           rho, phi, ux, uy);
+    else if (c->p.storage == LB_F64)
         binary_moments_kernel<double><<<nb, 256, 0, c->stream>>>(
             reinterpret_cast<const double*>(set_ptr(c, c->cur)), c->pitch, nx, ny, rho, phi, ux, uy);
     else
@@ -672,7 +801,10 @@ lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** 
     if (!(p->Gamma > 0)) return bfail(LB_EINVAL, "Gamma must be > 0");
     if (!(p->tau > 0.5) || !(p->tau_phi > 0.5)) return bfail(LB_EINVAL, "tau and tau_phi must be > 1/2");
     if (p->scheme != LB_SCHEME_EQUILIBRIUM && p->scheme != LB_SCHEME_FORCING) return bfail(LB_EINVAL, "scheme");
-    if (p->storage != LB_F64 && p->storage != LB_F32) return bfail(LB_EINVAL, "storage must be LB_F64 or LB_F32");
+    if (p->storage != LB_F64 && p->storage != LB_F32 && p->storage != LB_F16DEV)
+        return bfail(LB_EINVAL, "storage must be LB_F64, LB_F32 or LB_F16DEV");
+    if (p->storage == LB_F16DEV && (p->lattice != LB_D2Q9 || p->nx % 2 != 0))
+        return bfail(LB_EINVAL, "LB_F16DEV binary storage needs D2Q9 and an even nx");
     lb_binary* c = new (std::nothrow) lb_binary;
     if (!c) return bfail(LB_ENOMEM, "context");
     c->p = *p;
@@ -680,16 +812,22 @@ lb_status lb_binary_create(const lb_binary_params* p, void* stream, lb_binary** 
     c->Qn = p->lattice == LB_D2Q9 ? 9 : 19;
     c->N = (long long)p->nx * p->ny * p->nz;
     c->esize = p->storage == LB_F64 ? 8 : 4;
+    c->f16 = p->storage == LB_F16DEV;
     // LB_BINARY_SITE=1 keeps the one-site kernel for float32 (comparisons)
-    c->pair = c->D == 2 && p->storage == LB_F32 && p->nx % 2 == 0 && !std::getenv("LB_BINARY_SITE");
+    c->pair = c->f16 || (c->D == 2 && p->storage == LB_F32 && p->nx % 2 == 0 && !std::getenv("LB_BINARY_SITE"));
     c->pitch = (c->N + 63) / 64 * 64;
-    if (2 * c->Qn * c->pitch >= (1LL << 32)) {
+    if (2 * c->Qn * c->pitch >= (1LL << 32) || (c->f16 && set16_bytes(size_t(c->pitch)) >= (1ULL << 32))) {
         delete c;
-        return bfail(LB_EINVAL, "lattice too large: element offsets of a population set must fit 32 bits "
-                                "(at most 238,609,280 sites for D2Q9, 113,025,408 for D3Q19)");
+        return bfail(LB_EINVAL, "lattice too large: offsets within a population set must fit 32 bits "
+                                "(at most 238,609,280 sites for D2Q9, 107,374,144 with LB_F16DEV, "
+                                "113,025,408 for D3Q19)");
     }
+    c->set_bytes = c->f16 ? set16_bytes(size_t(c->pitch)) : size_t(2) * c->Qn * c->pitch * c->esize;
+    // the rest equilibrium w_i p0 of a bulk phase at rho = 1, phi = +-phi* (the same in both)
+    const double ps2 = (p->A < 0 && p->B > 0) ? -p->A / p->B : 0.0;
+    c->pref = float(1.0 / 3.0 + 0.5 * p->A * ps2 + 0.75 * p->B * ps2 * ps2);
     c->stream = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMalloc(&c->pop, size_t(2) * 2 * c->Qn * c->pitch * c->esize);
+    cudaError_t e = cudaMalloc(&c->pop, 2 * c->set_bytes);
     if (e == cudaSuccess && c->D == 3) e = cudaMalloc(&c->phi, size_t(c->N) * c->esize);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
@@ -744,6 +882,24 @@ lb_status lb_binary_init_fields(lb_binary* c, const double* rho, const double* p
     const unsigned nbk = blocks_for(N);
     const bool forcing = c->p.scheme == LB_SCHEME_FORCING;
     const lb_binary_params& p = c->p;
+    if (c->f16) {   // float64 equilibria into a staging array, then rounded into the 16-bit set
+        double* tmp = nullptr;
+        e = cudaMalloc(&tmp, size_t(2) * Q * N * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(LB_ENOMEM, "init staging");
+        }
+        if (forcing) binary_init_kernel<true, double><<<nbk, 256, 0, c->stream>>>(d, d + N, ux, uy, tmp, N, p.nx, p.ny, p.A, p.B, p.kappa, p.Gamma);
+        else binary_init_kernel<false, double><<<nbk, 256, 0, c->stream>>>(d, d + N, ux, uy, tmp, N, p.nx, p.ny, p.A, p.B, p.kappa, p.Gamma);
+        binary_convert16_kernel<<<blocks_for(2 * Q * N), 256, 0, c->stream>>>(set_ptr(c, 0), unsigned(c->pitch),
+                                                                            unsigned(N), 0, tmp, c->pref);
+        e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return brecord(c, e, "binary init");
+        return reset_after_set(c);
+    }
     if (p.storage == LB_F64) {
         double* dst = reinterpret_cast<double*>(set_ptr(c, 0));
         if (forcing) binary_init_kernel<true, double><<<nbk, 256, 0, c->stream>>>(d, d + N, ux, uy, dst, c->pitch, p.nx, p.ny, p.A, p.B, p.kappa, p.Gamma);
@@ -768,7 +924,10 @@ lb_status lb_binary_set_populations(lb_binary* c, const double* f, const double*
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_in + half, g, half * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return brecord(c, e, "population upload");
     const unsigned nb = blocks_for(2 * half);
-    if (c->p.storage == LB_F64)
+    if (c->f16)
+        binary_convert16_kernel<<<nb, 256, 0, c->stream>>>(set_ptr(c, 0), unsigned(c->pitch), unsigned(c->N), 0, c->d_in,
+                                                           c->pref);
+    else if (c->p.storage == LB_F64)
         binary_convert_kernel<double><<<nb, 256, 0, c->stream>>>(nullptr, nullptr, c->pitch, c->N, 2 * c->Qn, 0, c->d_in,
                                                                   reinterpret_cast<double*>(set_ptr(c, 0)));
     else
@@ -787,7 +946,10 @@ lb_status lb_binary_get_populations(lb_binary* c, double* f, double* g) {
     if ((s = ensure_in(c)) != LB_OK) return s;
     const size_t half = size_t(c->Qn) * c->N;
     const unsigned nb = blocks_for(2 * half);
-    if (c->p.storage == LB_F64)
+    if (c->f16)
+        binary_convert16_kernel<<<nb, 256, 0, c->stream>>>(set_ptr(c, c->cur), unsigned(c->pitch), unsigned(c->N), 1,
+                                                           c->d_in, c->pref);
+    else if (c->p.storage == LB_F64)
         binary_convert_kernel<double><<<nb, 256, 0, c->stream>>>(
             reinterpret_cast<const double*>(set_ptr(c, c->cur)), c->d_in, c->pitch, c->N, 2 * c->Qn, 1, nullptr, nullptr);
     else

@@ -42,6 +42,7 @@ struct StepArgs {
     unsigned pitch;      // 2 Q pitch < 2^32: element offsets within a set are 32-bit
     int nx, ny, nz;
     real A, B, kappa, Gamma, omega, omega_phi;   // omega = 1/tau, omega_phi = 1/tau_phi
+    float pref;          // 16-bit sets: f_i (i >= 1) are stored as f_i - w_i pref
     unsigned* status;
 };
 

@@ -105,6 +105,57 @@ def test_f32_parity(scheme, shape):
     assert ef < 2e-6 and eg < 2e-6
 
 
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("shape", [(48, 20), (36, 10), (6, 3)])
+def test_f16dev_parity(scheme, shape):
+    """fp16 deviations (f_0, g_0 float32; f_i - w_i p0(bulk) and g_i in fp16): one step from
+    the stored state against the oracle stepping it in float64 within 3e-5 of max |f|, and
+    20 steps from the rounded start within 1e-4 (measured on GB300: 4e-6 - 8e-6 and at most
+    1.0e-5; one rounding of the deviations, below 0.02 here, to 11 significant bits is at
+    most 1e-5 absolute per step, 2.5e-5 of max |f|)."""
+    m = _model(scheme)
+    nx, ny = shape
+    rho0, phi0, u0 = _fields(m, nx, ny)
+    f, g = BO.init_equilibrium(rho0, phi0, m, u0)
+    with _ctx(library(), m, (nx, ny), storage=2) as c:
+        c.set_populations(f[:, 0], g[:, 0])
+        fs, gs = c.get_populations()
+        c.step(1)
+        f1, g1 = c.get_populations()
+        c.step(19)
+        f20, g20 = c.get_populations()
+    fo, go = BO.step(fs[:, None], gs[:, None], m)
+    e1 = max(rel_inf(f1, fo[:, 0]), rel_inf(g1, go[:, 0]))
+    fo, go = BO.run(fs[:, None], gs[:, None], m, 20)
+    e20 = max(rel_inf(f20, fo[:, 0]), rel_inf(g20, go[:, 0]))
+    print(f"binary f16dev {scheme} {shape}: 1 step {e1:.2e}, 20 steps {e20:.2e}")
+    assert e1 < 3e-5 and e20 < 1e-4
+
+
+def test_f16dev_laplace_law():
+    """Laplace's law and the forcing scheme's smaller spurious velocity hold with fp16 deviations."""
+    lb = library()
+    n, R = 96, 20.0
+    res = {}
+    for scheme in SCHEMES:
+        m = _model(scheme, tau=1.0, tau_phi=1.0, Gamma=1.0)
+        phi0 = BO.drop_phi((1, n, n), [(n / 2, n / 2)], [R], 1.0, -1.0, BO.interface_width(A_BIN, K_BIN))
+        with _ctx(lb, m, (n, n), storage=2) as c:
+            c.init_fields(np.ones((n, n)), phi0[0])
+            c.step(20000)
+            rho, phi, u, v, mu = c.fields()
+            st = c.stats()
+        pin, pout = phi[n // 2, n // 2], phi[0, 0]
+        R_e = np.sqrt((phi.sum() - pout * n * n) / (np.pi * (pin - pout)))
+        dP = BO.p0(rho[n // 2, n // 2], pin, A_BIN, B_BIN) - BO.p0(rho[0, 0], pout, A_BIN, B_BIN)
+        res[scheme] = (dP * R_e / BO.surface_tension(A_BIN, B_BIN, K_BIN), float(np.hypot(v[0], v[1]).max()))
+        assert st["status"] == 0
+    print("binary f16dev Laplace", res)
+    for scheme in SCHEMES:
+        assert abs(res[scheme][0] - 1) < 0.06, (scheme, res)
+    assert res["forcing"][1] < res["equilibrium"][1], res
+
+
 @pytest.mark.parametrize("storage", [0, 1])
 def test_graph_replay_equals_single_launches(storage):
     m = _model("forcing")

@@ -121,7 +121,8 @@ def test_binary_parameters_rejected_before_device_work():
         with pytest.raises(lb.LBError) as e:
             lb.BinaryContext((16, 8), **kw)
         assert e.value.status == 1, b
-    for shape, extra in (((0, 8), {}), ((8, 8), dict(scheme=2)), ((8, 8), dict(storage=2))):
+    for shape, extra in (((0, 8), {}), ((8, 8), dict(scheme=2)), ((8, 8), dict(storage=3)),
+                         ((9, 8), dict(storage=2)), ((8, 8, 4), dict(storage=2))):
         with pytest.raises(lb.LBError) as e:
             lb.BinaryContext(shape, **ok, **extra)
         assert e.value.status == 1
