@@ -4,7 +4,9 @@ the binary oracle.
 float64: every population, rho, phi, u, v and mu to 1e-12 after 100 steps on
 ragged, odd and tiny lattices, both schemes; the initial state to 1e-14; one
 step at 1024^2.  float32 (two sites per thread for even nx): the same comparison
-at float32 rounding, and one step at the bench's 2048^2.  The graph
+at float32 rounding, and one step at the bench's 2048^2.  fp16 deviations (D2Q9,
+even nx): one and 20 steps against the oracle from the stored state, and
+Laplace's law.  The graph
 replay path equals single launches bit for bit; mass, order parameter and
 momentum stay conserved; Laplace's law holds on the device.  D3Q19: the same
 float64 parity after 30 steps, the initial state, float32, graph replay,
