@@ -11,7 +11,7 @@ import pytest
 from oracle import binary_oracle as BO
 from oracle import lb_oracle as O
 from tests.test_binary_oracle import _model, thermodynamic_residual, A_BIN, K_BIN
-from tests.test_oracle_pins import A_VDW, B_VDW, _pressure_tensor, _random_state, galilean_errors
+from tests.test_oracle_pins import A_VDW, B_VDW, _pressure_tensor, _random_state, eq28_error, galilean_errors
 
 
 def _second_moment_error(weights, cs2_sign=1.0):
@@ -113,3 +113,9 @@ def test_order_parameter_advected_with_u_in_the_forcing_scheme_is_caught():
         f, g = step_u(f, g, m)
     mu = BO.observables(f, g, m)[4]
     assert np.abs(mu).max() > 1e-3      # the pin asks |mu| < 1e-4
+
+
+def test_wrong_sign_or_transposed_body_force_is_caught():
+    """g = +div M' instead of -div M' (Eq. 28), or its components exchanged."""
+    assert eq28_error(lambda rho, m: [-c for c in O.body_force(rho, m)]) > 1e-6
+    assert eq28_error(lambda rho, m: O.body_force(rho, m)[::-1]) > 1e-6

@@ -253,13 +253,16 @@ def test_force_population_moments(lat):
             assert np.allclose(got, u[a_] * g[b_] + u[b_] * g[a_], rtol=1e-12, atol=1e-16)
 
 
-def test_force_2d_matches_eq28_stencil_form():
-    """Eq. 28 written as the printed (E, F) stencils on (M_xx - M_yy)/2 and M_xy,
-    with E = 1/3, F = 1/12, evaluated directly with the matrices as printed."""
+def eq28_error(body_force=None):
+    """Largest difference between the body force (the oracle's by default) and Eq. 28
+    written as the printed (E, F) stencils on (M_xx - M_yy)/2 and M_xy with E = 1/3,
+    F = 1/12, evaluated directly with the matrices as printed; g_y by interchanging the
+    labels x and y, as Sec. VI says."""
+    body_force = body_force or O.body_force
     rng = np.random.default_rng(2)
     m = O.Model("D2Q9", A_VDW, B_VDW, 0.55, 0.02, 1.0, scheme="forcing")
     rho = rng.uniform(2, 5, (1, 6, 7))
-    g = O.body_force(rho, m)
+    g = body_force(rho, m)
     gx_, gy_ = O.gradient(rho, m.stencils)
     Mxx, Myy, Mxy = m.kappa * gx_ * gx_, m.kappa * gy_ * gy_, m.kappa * gx_ * gy_
     E, F = 1 / 3, 1 / 12
@@ -269,7 +272,17 @@ def test_force_2d_matches_eq28_stencil_form():
              - F * s(h, -1, -1) + F * s(h, 1, -1))
     second = (F * s(Mxy, -1, 1) + E * s(Mxy, 0, 1) + F * s(Mxy, 1, 1)
               - F * s(Mxy, -1, -1) - E * s(Mxy, 0, -1) - F * s(Mxy, 1, -1))
-    assert np.allclose(g[0], -first - second, rtol=1e-13, atol=1e-15)
+    hy = -h   # (M_yy - M_xx)/2
+    first_y = (-F * s(hy, 1, -1) + F * s(hy, 1, 1) - E * s(hy, 0, -1) + E * s(hy, 0, 1)
+               - F * s(hy, -1, -1) + F * s(hy, -1, 1))
+    second_y = (F * s(Mxy, 1, -1) + E * s(Mxy, 1, 0) + F * s(Mxy, 1, 1)
+                - F * s(Mxy, -1, -1) - E * s(Mxy, -1, 0) - F * s(Mxy, -1, 1))
+    return max(float(np.abs(g[0] + first + second).max()), float(np.abs(g[1] + first_y + second_y).max()))
+
+
+def test_force_2d_matches_eq28_stencil_form():
+    """Eq. 28 as printed (both components) against the oracle's body force."""
+    assert eq28_error() < 1e-14
 
 
 # ---------------------------------------------------------- dynamics pins
