@@ -17,3 +17,10 @@ def test_drop_matches_oracle_drop():
     A, B, k = -0.04, 0.04, 0.08
     want = BO.drop_phi((1, n, n), [(n / 2, n / 2)], [R], 1.0, -1.0, BO.interface_width(A, k))[0]
     assert np.abs(binary.drop_phi(n, R, A, k, B) - want).max() < 1e-14
+
+
+def test_drop_3d_matches_oracle_drop():
+    n, R = 20, 5.5
+    A, B, k = -0.04, 0.04, 0.08
+    want = BO.drop_phi((n, n, n), [(n / 2, n / 2, n / 2)], [R], 1.0, -1.0, BO.interface_width(A, k))
+    assert np.abs(binary.drop_phi(n, R, A, k, B, dim=3) - want).max() < 1e-14
